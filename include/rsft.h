@@ -1,0 +1,206 @@
+/*
+ * rsft.h -- C ABI of the GB300 (sm_103a) RSFT hot path.
+ *
+ * The Realistic Sparse Fourier Transform of Wang, Patel and Petropulu ("An
+ * Efficient High-Dimensional Sparse Fourier Transform"), Algorithm 1: over L
+ * random loops, a windowed N-D complex cube is permuted per dimension by an
+ * odd multiplier sigma (Def. 1, tau = 0 as in §III), multiplied by a flat
+ * window, aliased into a B-bucket grid (Def. 2, §III-C.3), transformed by a
+ * B-point N-D FFT (eq. (f)), thresholded on bucket power (first-stage
+ * Neyman-Pearson detection, §IV-B eq. (tpd)), reverse-mapped into candidate
+ * frequencies (Def. 4) whose votes are accumulated over loops (eq. (a_i)), and
+ * thresholded again on the vote count (second stage, §III-C.5, eq. (opt)).
+ * Located frequencies get a median amplitude estimate (the estimation
+ * paragraph of §III).
+ *
+ * Conventions used by every call below:
+ *  - Sizes: ndim in [1, 4]; every N_d and B_d is a power of two (§II-A
+ *    notation), B_d divides N_d, N_d >= 2; M_d = N_d / B_d (the paper's L of
+ *    Def. 2).  L = number of loops (the paper's T), 1..255.
+ *  - Cube: complex64 (interleaved re, im float32), row-major N_0 x ... x
+ *    N_{D-1}, last dimension contiguous, device memory, 16-byte aligned,
+ *    owned by the caller and only read.
+ *  - Linear frequency index i = sum_d i_d prod_{e>d} N_e (row-major).
+ *  - Bucket index k = sum_d k_d prod_{e>d} B_e (row-major); bucket k of loop l
+ *    holds the permuted bins [k_d M_d, (k_d + 1) M_d) of every dimension
+ *    (the floor mapping of Def. 3).
+ *  - DFTs are forward (kernel e^{-j 2 pi k n / B}) and unnormalised (eq. (f)).
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *    default stream).  Calls are stream-ordered unless stated otherwise.
+ *  - Errors: every call returns an rsft_status; on failure nothing is
+ *    guaranteed about the outputs and rsft_last_error() holds a message.
+ *    The library never traps, never spins on device flags, and never falls
+ *    back to the CPU: without a usable CUDA device, calls that need one
+ *    return RSFT_ERR_CUDA.
+ */
+#ifndef RSFT_H
+#define RSFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rsft_status {
+  RSFT_OK = 0,
+  RSFT_ERR_INVALID_ARG = 1,   /* bad descriptor, pointer or size              */
+  RSFT_ERR_UNSUPPORTED = 2,   /* valid but not implemented (e.g. ndim > 4)    */
+  RSFT_ERR_OOM = 3,           /* device or host allocation failed             */
+  RSFT_ERR_CAPACITY = 4,      /* output truncated; required size returned     */
+  RSFT_ERR_CUDA = 5,          /* CUDA runtime error (message in last_error)   */
+  RSFT_ERR_TIMEOUT = 6,       /* a bounded device wait gave up                */
+  RSFT_ERR_DESIGN = 7         /* threshold design (eq. (opt)) has no solution */
+} rsft_status;
+
+enum { RSFT_WIN_RECT = 0, RSFT_WIN_CHEB = 1 };       /* pre-permutation window (§III-A) */
+enum { RSFT_FLAT_IDEAL = 0, RSFT_FLAT_CHEB = 1 };    /* flat window (§IV-B)             */
+enum { RSFT_BETA_EXACT = 0, RSFT_BETA_MEAN = 1 };    /* beta(sigma_l) or beta-bar in gamma */
+
+/* Warning bits reported by rsft_plan_get(RSFT_GET_WARNINGS). */
+enum { RSFT_WARN_SPARSITY_LIMIT = 1 };  /* K_max * eta_m >= B: Remark 2, RSFT cannot separate H0/H1 */
+
+/*
+ * Plan descriptor (Problem 1 of §IV-A: sizes, loop count, window, P_fa; the
+ * Algorithm 1 inputs).  Fill with rsft_desc_init() and override fields.
+ */
+typedef struct rsft_desc {
+  int32_t ndim;              /* D, 1..4                                               */
+  int64_t n[4];              /* N_d, powers of two >= 2                               */
+  int64_t b[4];              /* B_d, powers of two, B_d | N_d                          */
+  int32_t loops;             /* L (paper T), 1..255                                   */
+  int32_t window;            /* RSFT_WIN_CHEB (default) or RSFT_WIN_RECT              */
+  double atten_db;           /* Chebyshev side-lobe attenuation in dB (default 60)    */
+  int32_t flat;              /* RSFT_FLAT_CHEB (default) or RSFT_FLAT_IDEAL           */
+  int64_t flat_support[4];   /* taper support S_d (even, 2..N_d); 0 = N_d             */
+  double p_fa;               /* system per-bin false-alarm probability (§IV-A)       */
+  double p_d;                /* system detection probability of the weakest tone     */
+  int32_t k_max;             /* sparsity budget K used by the design (Claim 3)       */
+  double eta_p;              /* calibration eta_p >= 1 (Claim 3); <= 0 = 1/Pd-bar     */
+  double p_fa1_override;     /* > 0: first-stage Pfa1-bar; else from eq. (opt)        */
+  int32_t mu_override;       /* >= 0: second-stage threshold mu; else from eq. (opt)  */
+  double noise_var;          /* sigma_n^2 > 0 (known noise, §IV-A)                    */
+  uint64_t seed;             /* SplitMix64 seed of the sigma draws                    */
+  const int64_t* sigma;      /* optional [loops][ndim] odd multipliers; NULL = draw   */
+  int32_t beta_mode;         /* RSFT_BETA_EXACT (default) or RSFT_BETA_MEAN           */
+  int64_t max_located;       /* capacity of the located list (default 65536)          */
+  int32_t device;            /* CUDA device ordinal; -1 = host-only plan (tables only) */
+} rsft_desc;
+
+typedef struct rsft_plan rsft_plan;
+
+/* Fill *desc with defaults: ndim 0 (must be set), Chebyshev 60 dB windows,
+ * p_fa 1e-6, p_d 0.9, k_max 8, eta_p 1, no overrides, noise_var 1, seed 0,
+ * max_located 65536, device 0.  desc must not be NULL. */
+void rsft_desc_init(rsft_desc* desc);
+
+/*
+ * Build a plan: draw sigma (Def. 1; odd values, §V-E), build the windows
+ * (§III-C.1, §IV-B), per-loop beta(sigma_l) (eq. (alpha_beta)), solve eq.
+ * (opt) for (mu, Pfa1-bar) unless overridden, set gamma_l = -sigma_n^2
+ * beta(sigma_l) ln Pfa1-bar (eq. (tpd)), upload the tables and allocate the
+ * workspace on desc->device.  With device = -1 only the host tables are
+ * built (for rsft_plan_get); such a plan cannot execute.
+ * Ownership: *plan is owned by the caller and released by rsft_plan_destroy.
+ * Errors: INVALID_ARG (sizes, loops, windows), UNSUPPORTED (ndim > 4),
+ * DESIGN (no feasible mu), OOM, CUDA.  On error *plan is set to NULL.
+ */
+rsft_status rsft_plan_create(const rsft_desc* desc, rsft_plan** plan);
+
+/* Release a plan and its device memory (synchronises its device).  NULL is a no-op. */
+void rsft_plan_destroy(rsft_plan* plan);
+
+/*
+ * Run the whole hot path on one cube (Algorithm 1 plus second-stage
+ * detection and estimation) and wait for it.
+ *   d_cube          device complex64 cube (see conventions).
+ *   stream          cudaStream_t or NULL.
+ *   d_located       device uint64 [max_located]: located linear indices,
+ *                   ascending (second-stage output o of Algorithm 1).
+ *   d_located_votes device uint8 [max_located] or NULL: vote count of each.
+ *   d_amp           device complex64 [max_located] or NULL: median estimate of
+ *                   each located amplitude (§III estimation paragraph).
+ *   d_votes_out     device uint8 [N] or NULL: the accumulated votes a-bar
+ *                   (eq. (a_i)) before they are cleared for the next call.
+ *   n_located       host: number of located frequencies (may exceed
+ *                   max_located, then RSFT_ERR_CAPACITY and the first
+ *                   max_located, in ascending order, are written).
+ * The plan's workspace is reused: calls on one plan must not overlap.
+ */
+rsft_status rsft_execute(rsft_plan* plan, const void* d_cube, void* stream,
+                         uint64_t* d_located, uint8_t* d_located_votes,
+                         void* d_amp, uint8_t* d_votes_out, int64_t* n_located);
+
+/*
+ * As rsft_execute, but does not wait: the located count (int64, possibly
+ * above max_located) is written to device memory *d_n_located in stream
+ * order, and capacity overflow is not reported as an error.
+ */
+rsft_status rsft_execute_async(rsft_plan* plan, const void* d_cube, void* stream,
+                               uint64_t* d_located, uint8_t* d_located_votes,
+                               void* d_amp, uint8_t* d_votes_out,
+                               int64_t* d_n_located);
+
+/*
+ * End-to-end call on HOST buffers: copies h_cube (N complex64, preferably
+ * pinned) to a plan-owned device staging buffer on `stream`, runs the hot
+ * path, and copies the located list back.  h_located (uint64), h_amp
+ * (complex64, may be NULL) hold max_located entries.  Synchronous.
+ */
+rsft_status rsft_execute_host(rsft_plan* plan, const void* h_cube, void* stream,
+                              uint64_t* h_located, void* h_amp, int64_t* n_located);
+
+/* Items of rsft_plan_get (host copies; `bytes` must be at least the size given). */
+enum {
+  RSFT_GET_SIGMA = 1,       /* int64 [L][D]  sigma_{l,d}                                  */
+  RSFT_GET_SIGMA_INV = 2,   /* int64 [L][D]  sigma^{-1} mod N_d (eq. (mod_inv))           */
+  RSFT_GET_GAMMA = 3,       /* double [L]    first-stage thresholds gamma_l               */
+  RSFT_GET_BETA = 4,        /* double [L]    beta(sigma_l) (eq. (alpha_beta))            */
+  RSFT_GET_MU = 5,          /* int32 [1]     second-stage threshold (votes > mu)         */
+  RSFT_GET_PFA1 = 6,        /* double [1]    first-stage Pfa1-bar                        */
+  RSFT_GET_ETA_M = 7,       /* double [1]    prod_d 6-dB bandwidth of w_d in bins        */
+  RSFT_GET_PD_BAR = 8,      /* double [1]    Pd-bar of the design (0 if overridden)      */
+  RSFT_GET_WINDOW = 9,      /* double [sum_d N_d]    pre-window taps w_d, d = 0..D-1      */
+  RSFT_GET_FLAT = 10,       /* double [2 sum_d N_d]  flat-window taps (re, im) per d      */
+  RSFT_GET_WARNINGS = 11,   /* int32 [1]     RSFT_WARN_* bits                            */
+  RSFT_GET_SNR_DB = 12,     /* double [1]    SNR*_min of eq. (opt) in dB (half-bin tone) */
+  RSFT_GET_WORKSPACE_BYTES = 13 /* int64 [1] device bytes owned by the plan               */
+};
+rsft_status rsft_plan_get(const rsft_plan* plan, int32_t what, void* out, size_t bytes);
+
+/* Bucket arrays of the last execute, for inspection (stream-ordered device copy). */
+enum {
+  RSFT_BUCKETS_FOLDED = 0,    /* f_l = Aliasing(W-bar P_sigma W r) (Algorithm 1, eq. (l)) */
+  RSFT_BUCKETS_SPECTRUM = 1   /* f-hat_l = NDFFT(f_l) (eq. (f))                           */
+};
+/* d_out: device complex64 [L][B] (bucket k of loop l at l * B + k). */
+rsft_status rsft_copy_buckets(rsft_plan* plan, int32_t which, void* d_out, void* stream);
+
+/* First-stage detections c_l of the last execute (§IV-C): d_out device uint32
+ * [L][ceil(B/32)], bit (k mod 32) of word k / 32 set iff |f-hat_l[k]|^2 > gamma_l. */
+rsft_status rsft_copy_detections(rsft_plan* plan, void* d_out, void* stream);
+
+/*
+ * Gradient refinement of located tones (beyond the paper, which recovers only
+ * grid locations, §I): minimises the bucket-domain residual between the
+ * cube's folded buckets and those of K synthesised tones over `steps`
+ * gradient steps of size lr.  d_freq: device float [K][D] in cycles/sample
+ * (in/out); d_amp: device complex64 [K] (in/out).  Requires a prior execute
+ * on the same cube.
+ */
+rsft_status rsft_refine(rsft_plan* plan, const void* d_cube, int64_t k,
+                        float* d_freq, void* d_amp, int32_t steps, float lr,
+                        void* stream);
+
+/* Static description of a status code (never NULL). */
+const char* rsft_status_string(rsft_status status);
+
+/* Message of the last failing call on this thread ("" if none; never NULL). */
+const char* rsft_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSFT_H */

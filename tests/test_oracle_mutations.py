@@ -1,0 +1,89 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that a pin fails.
+
+Each case swaps one oracle function for a subtly wrong version (a transposed
+operand, a dropped term, a wrong sign or index) and runs the pin that must
+catch it.  This shows the pins are sharp enough to notice such slips.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.pipeline as orsft
+import oracle.windows as owin
+import oracle.design as odes
+import tests.test_oracle_pins as pins
+
+
+def _perm_inverse(y, sigma_row):
+    idx = [(O.inverse_mod(int(s), nd) * np.arange(nd)) % nd for s, nd in zip(sigma_row, y.shape)]
+    return y[np.ix_(*idx)]
+
+
+def _alias_wrong_axis(z, b):
+    shape = []
+    for nd, bd in zip(z.shape, b):
+        shape += [bd, nd // bd]
+    return z.reshape(shape).sum(axis=tuple(range(0, 2 * z.ndim, 2)))
+
+
+def _reverse_with_sigma(plan, l, j):
+    return [(int(plan.sigma[l, d]) * (int(j[d]) * plan.m[d] + np.arange(plan.m[d]))) % plan.n[d]
+            for d in range(plan.ndim)]
+
+
+def _flat_conj(n, m, kind, atten_db, support=None):
+    return np.conj(_ORIG_FLAT(n, m, kind, atten_db, support))
+
+
+def _beta_no_square(wbars, ws, sigma_row):
+    out = 1.0
+    for wbar, w, s in zip(wbars, ws, sigma_row):
+        n = len(w)
+        out *= float(np.sum(np.abs(wbar) * w[(int(s) * np.arange(n)) % n] ** 2))
+    return out
+
+
+def _median_no_wsum(plan, spectra, located):
+    saved = plan.wsum
+    plan.wsum = 1.0
+    try:
+        return _ORIG_EST(plan, spectra, located)
+    finally:
+        plan.wsum = saved
+
+
+def _mapping_off_by_one(plan, l, i):
+    return tuple(((int(plan.sigma[l, d]) * int(i[d]) + 1) % plan.n[d]) // plan.m[d]
+                 for d in range(plan.ndim))
+
+
+_ORIG_FLAT = owin.flat_window
+_ORIG_EST = orsft.estimate_amplitudes
+
+CASES = [
+    ("permute with sigma^-1", [(orsft, "permute", _perm_inverse), (O, "permute", _perm_inverse)],
+     lambda: pins.test_permutation_property((16, 8), (3, 7))),
+    ("alias over the wrong axis", [(orsft, "alias", _alias_wrong_axis), (O, "alias", _alias_wrong_axis)],
+     lambda: pins.test_aliasing_property((16, 32), (4, 8))),
+    ("reverse map with sigma", [(orsft, "reverse_map", _reverse_with_sigma), (O, "reverse_map", _reverse_with_sigma)],
+     lambda: pins.test_reversibility_and_distinctiveness_exhaustive(16)),
+    ("conjugated flat window", [(orsft, "flat_window", _flat_conj), (owin, "flat_window", _flat_conj),
+                                (O, "flat_window", _flat_conj)],
+     lambda: pins.test_ideal_flat_window_is_boxcar(64, 8)),
+    ("beta without the square", [(orsft, "beta_sigma", _beta_no_square), (odes, "beta_sigma", _beta_no_square)],
+     pins.test_noise_only_power_is_exponential),
+    ("estimate without the pre-window gain", [(orsft, "estimate_amplitudes", _median_no_wsum)],
+     lambda: pins.test_exact_recovery_noise_free((64, 32), (8, 8), 6, 4)),
+    ("mapping off by one", [(orsft, "mapping", _mapping_off_by_one), (O, "mapping", _mapping_off_by_one)],
+     lambda: pins.test_reversibility_and_distinctiveness_exhaustive(16)),
+]
+
+
+@pytest.mark.parametrize("name,patches,check", CASES, ids=[c[0] for c in CASES])
+def test_planted_mistake_is_caught(monkeypatch, name, patches, check):
+    for mod, attr, fn in patches:
+        monkeypatch.setattr(mod, attr, fn)
+    with pytest.raises(AssertionError):
+        check()
