@@ -1,0 +1,350 @@
+#!/usr/bin/env python3
+"""RSFT throughput on GB300: frames/s of the whole hot path on synthetic radar cubes.
+
+Default workload: the 3-D radar cube 1024 x 256 x 64 complex64 (range x Doppler x
+angle), bucket grid 64 x 32 x 8, L = 12 loops, 80 dB Chebyshev windows, system
+P_fa = 1e-6, K = 32 off-grid Rayleigh targets at 5-25 dB (thresholds from the
+paper's eq. (opt)).  A step is one rsft_execute_async over one frame (fold, bucket
+FFT + detection, vote scatter, second stage, median estimate).  Frames rotate
+through a ring of 4 distinct cubes (537 MB, larger than the 129 MB L2).
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU FP64 oracle on
+the host instead (the only comparison system this method has).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RSFT frames/s on 1 GB300 at matched Pd/Pfa; % HBM roofline; vs plain and dense FFT"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="c2_3d_radar")
+    ap.add_argument("--frames", type=int, default=4)
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def profile_traffic(workload):
+    """DRAM bytes per fold launch from the committed ncu summary, if it matches the kernel source."""
+    path = os.path.join(ROOT, "profiles", f"permute_window_fold_{workload}.txt")
+    src = os.path.join(ROOT, "paper_1610_01050_gb300", "csrc", "fold.cu")
+    try:
+        text = open(path).read()
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        vals = dict(line.split(":", 1) for line in text.splitlines() if ":" in line)
+        if vals.get("fold_cu_sha256_16", "").strip() != digest:
+            return None
+        return float(vals["dram_bytes_per_launch"].strip())
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id=None):
+        self.out = tempfile.NamedTemporaryFile(prefix="clocks_", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu_id:
+            cmd.insert(1, f"--id={gpu_id}")
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        self.t0 = self.t1 = None
+
+    def mark(self, start):
+        if start:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        self.out.close()
+        rows = []
+        try:
+            for line in open(self.out.name):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        except Exception:
+            pass
+        os.unlink(self.out.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def workload_desc(R, wl, nv, seed):
+    return R.make_desc(wl.shape, wl.buckets, wl.loops, atten_db=wl.atten_db, flat_support=wl.flat_support,
+                       p_fa=wl.p_fa, k_max=wl.k_range[1], noise_var=nv, seed=seed, max_located=65536)
+
+
+def oracle_sample(wl, cube, nv, seed, loops):
+    """Time the FP64 oracle (as it stands) on `loops` loops of one frame; returns seconds."""
+    import oracle as O
+    op = O.make_plan(wl.shape, wl.buckets, wl.loops, seed=seed, atten_db=wl.atten_db,
+                     flat_support=wl.flat_support, noise_var=nv, p_fa=wl.p_fa, k_max=wl.k_range[1])
+    sub = O.make_plan(wl.shape, wl.buckets, loops, seed=seed, atten_db=wl.atten_db,
+                      flat_support=wl.flat_support, noise_var=nv, sigma=op.sigma[:loops], pfa1=op.pfa1,
+                      mu=min(op.mu, loops - 1))
+    x = cube.astype(np.complex128)
+    t0 = time.perf_counter()
+    O.rsft(sub, x, estimate=True, keep=False)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(wl, cube, nv, seed):
+    t1 = oracle_sample(wl, cube, nv, seed, 1)
+    loops = wl.loops if t1 * wl.loops <= 30.0 else max(1, int(20.0 / t1))
+    t = oracle_sample(wl, cube, nv, seed, loops) if loops > 1 else t1
+    per_frame = t * wl.loops / loops
+    sample = (f"one {'x'.join(map(str, wl.shape))} frame, {loops} of {wl.loops} loops of the FP64 oracle "
+              f"(plan excluded), {t:.1f} s, scaled to a frame by L/{loops}")
+    return {"value": 1.0 / per_frame, "unit": "frames/s", "cores": 1, "kind": "oracle", "sample": sample}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import rsft_inputs as ri
+    wl = ri.WORKLOADS[args.workload]
+    cube, _, _, nv = ri.workload_frame(args.workload, 0)
+    seed = ri.frame_seed(wl, 0)
+    # a step = one loop of the oracle on one frame (a bounded sample); frames/s scales by 1/L
+    for _ in range(args.warmup):
+        oracle_sample(wl, cube, nv, seed, 1)
+    steps = max(1, min(args.steps, 20))
+    times = [oracle_sample(wl, cube, nv, seed, 1) for _ in range(steps)]
+    per_step = sum(times) / len(times)
+    value = 1.0 / (per_step * wl.loops)
+    sample = f"1 of {wl.loops} loops of one frame per step, {steps} steps, scaled by 1/L"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "shape": list(wl.shape), "buckets": list(wl.buckets), "loops": wl.loops},
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def detection_quality(wl, targets, shape, located):
+    """Pd: targets with a located index within +-1 bin per dimension; Pfa: located cells
+    outside every target's +-3-bin box over the cells outside those boxes."""
+    n = np.asarray(shape)
+    idx = np.stack(np.unravel_index(located, shape), axis=1) if len(located) else np.zeros((0, len(shape)), int)
+    grid = np.rint(targets.freqs * n).astype(np.int64) % n
+    hits, outside = 0, np.ones(len(idx), dtype=bool)
+    for g in grid:
+        diff = np.abs(idx - g)
+        diff = np.minimum(diff, n - diff)
+        if np.any(np.all(diff <= 1, axis=1)):
+            hits += 1
+        outside &= ~np.all(diff <= 3, axis=1)
+    cells_out = float(np.prod(n)) - len(grid) * 7.0 ** len(shape)
+    return hits / max(1, len(grid)), float(outside.sum()) / cells_out
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group(backend="nccl")
+    torch.cuda.set_device(local)
+    import paper_1610_01050_gb300 as R
+    from paper_1610_01050_gb300 import build as B
+    import rsft_inputs as ri
+
+    B.build()
+    R.load_library()
+    wl = ri.WORKLOADS[args.workload]
+    F = max(1, args.frames)
+    host, targets = [], []
+    nv = wl.noise_var
+    for f in range(F):
+        cube, tg, _, nv = ri.workload_frame(args.workload, rank * F + f)
+        host.append(torch.from_numpy(cube).pin_memory())
+        targets.append(tg)
+    dev = torch.device("cuda", local)
+    cubes = [h.to(dev) for h in host]
+    seed = ri.frame_seed(wl, 0)
+    plan = R.rsft_plan_create(workload_desc(R, wl, nv, seed))
+    cap = 65536
+    located = torch.zeros(cap, dtype=torch.int64, device=dev)
+    amp = torch.zeros(cap, dtype=torch.complex64, device=dev)
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    # detection quality on the ring (also a warm-up)
+    pd, pfa, n_loc = [], [], []
+    for f in range(F):
+        c = R.rsft_execute(plan, cubes[f], located=located, amp=amp, allow_capacity=True)
+        loc = located[:min(c, cap)].cpu().numpy()
+        a, b = detection_quality(wl, targets[f], wl.shape, loc)
+        pd.append(a)
+        pfa.append(b)
+        n_loc.append(c)
+
+    for k in range(args.warmup):
+        R.rsft_execute_async(plan, cubes[k % F], count, stream=stream, located=located, amp=amp)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    time.sleep(0.5)
+    R.rsft_plan_timing(plan, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    sampler.mark(True)
+    ev0.record(stream)
+    for k in range(args.steps):
+        R.rsft_execute_async(plan, cubes[k % F], count, stream=stream, located=located, amp=amp)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    sampler.mark(False)
+    ms = ev0.elapsed_time(ev1)
+    stage = R.rsft_plan_get(plan, R.RSFT_GET_STAGE_MS)
+    R.rsft_plan_timing(plan, False)
+    clocks = sampler.stop()
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * args.steps / (ms / 1e3)
+
+    # roofline of the dominant kernel (the fold): algorithmic bytes / average launch time
+    fold_bytes = int(R.rsft_plan_get(plan, R.RSFT_GET_FOLD_BYTES)[0])
+    timed = max(1.0, stage[6])
+    fold_s = stage[0] / timed / 1e3
+    peak, peak_kind = measured_peak()
+    achieved = fold_bytes / fold_s / 1e9
+    traffic = profile_traffic(args.workload)
+    stages = {k: stage[i] / timed * 1e3 for i, k in
+              enumerate(["fold_us", "fft_detect_us", "vote_scatter_us", "stage2_us", "median_us", "execute_us"])}
+
+    # end to end through the C ABI with host buffers (H2D of the cube and D2H of the result inside)
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    h_loc = torch.zeros(cap, dtype=torch.int64).pin_memory()
+    h_amp = torch.zeros(cap, dtype=torch.complex64).pin_memory()
+    for k in range(3):
+        R.rsft_execute_host(plan, host[k % F], h_loc, h_amp, stream=stream, allow_capacity=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for k in range(e2e_steps):
+        c = R.rsft_execute_host(plan, host[k % F], h_loc, h_amp, stream=stream, allow_capacity=True)
+        d2h += 8 + 16 * min(c, cap)
+    t_e2e = time.perf_counter() - t0
+    e2e_val = e2e_steps / t_e2e
+    if ws > 1:
+        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_val = ws * e2e_steps / float(t.item())
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, host[0].numpy(), nv, seed)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {
+                "workload": f"{wl.name}: {'x'.join(map(str, wl.shape))} complex64, B={'x'.join(map(str, wl.buckets))}, "
+                            f"L={wl.loops}, {wl.atten_db:g} dB Chebyshev, Pfa={wl.p_fa:g}, "
+                            f"K={wl.k_range[0]}-{wl.k_range[1]} {wl.kind}",
+                "frames_per_rank_ring": F,
+                "l2": f"inputs larger than L2: ring of {F} frames, {F * int(np.prod(wl.shape)) * 8 / 1e6:.0f} MB",
+                "parallelism": f"frames sharded over {ws} GPU(s), no collective on the data path",
+                "mu": int(R.rsft_plan_get(plan, R.RSFT_GET_MU)[0]),
+                "pfa1": float(R.rsft_plan_get(plan, R.RSFT_GET_PFA1)[0]),
+            },
+            "detection": {"pd": float(np.mean(pd)), "pfa": float(np.mean(pfa)), "located_per_frame": float(np.mean(n_loc)),
+                          "note": "Pd: targets located within +-1 bin per dim; Pfa: located cells outside +-3-bin target boxes"},
+            "stages_us_per_frame": stages,
+            "roofline": {"bound": "hbm", "kernel": "permute_window_fold", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_kind} (copy bandwidth)",
+                         "traffic": traffic, "algorithmic_bytes_per_launch": fold_bytes},
+            "e2e": {"value": e2e_val, "unit": "frames/s", "h2d_bytes_per_step": int(np.prod(wl.shape)) * 8,
+                    "d2h_bytes_per_step": int(d2h / e2e_steps)},
+            "gpu_launches": int(stage[7]) * args.steps,
+            "clocks": clocks,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

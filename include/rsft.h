@@ -165,9 +165,23 @@ enum {
   RSFT_GET_FLAT = 10,       /* double [2 sum_d N_d]  flat-window taps (re, im) per d      */
   RSFT_GET_WARNINGS = 11,   /* int32 [1]     RSFT_WARN_* bits                            */
   RSFT_GET_SNR_DB = 12,     /* double [1]    SNR*_min of eq. (opt) in dB (half-bin tone) */
-  RSFT_GET_WORKSPACE_BYTES = 13 /* int64 [1] device bytes owned by the plan               */
+  RSFT_GET_WORKSPACE_BYTES = 13, /* int64 [1] device bytes owned by the plan              */
+  RSFT_GET_STAGE_MS = 14,   /* double [8]    with timing on (rsft_plan_timing): summed device
+                             * milliseconds of [0] permute_window_fold, [1] bucket_fft+np_detect,
+                             * [2] vote_scatter, [3] stage2_compact, [4] median_estimate,
+                             * [5] whole execute; [6] executes timed; [7] kernel launches per
+                             * execute (with amplitudes).  Waits for the timed executes.      */
+  RSFT_GET_FOLD_BYTES = 15  /* int64 [1]     algorithmic bytes of one execute's fold: the cube
+                             * read once per loop group plus the bucket writes               */
 };
 rsft_status rsft_plan_get(const rsft_plan* plan, int32_t what, void* out, size_t bytes);
+
+/*
+ * Per-stage device timing.  enable != 0 starts recording CUDA events on the
+ * execute's stream around each stage (and clears the sums); 0 stops.  Read the
+ * sums with rsft_plan_get(RSFT_GET_STAGE_MS).  Events add no host sync.
+ */
+rsft_status rsft_plan_timing(rsft_plan* plan, int32_t enable);
 
 /* Bucket arrays of the last execute, for inspection (stream-ordered device copy). */
 enum {

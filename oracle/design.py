@@ -123,6 +123,9 @@ def optimal_thresholds(loops: int, b: int, k: int, eta_m: float, p_d: float,
                        beta_bar: float = 1.0) -> dict:
     """Solve eq. (opt) by enumerating mu in [L]; returns the minimiser and the table."""
     f_count = loops * k * eta_m / b
+    if f_count >= loops:
+        # Remark 2: K eta_m >= B makes the vote statistics of both hypotheses coincide
+        raise ValueError("infeasible design: K eta_m >= B (Remark 2)")
     rows = []
     for mu in range(loops):
         pd = solve_pd_bar(mu, loops, p_d)

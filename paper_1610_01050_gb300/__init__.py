@@ -1,0 +1,293 @@
+"""GB300-native RSFT hot path: a thin Python binding of the C ABI in include/rsft.h.
+
+The functions here have the names of the C entry points and only marshal
+arguments (torch tensors or numpy arrays to pointers and sizes); every step of
+the path runs in the CUDA library ``_lib/librsft.so``.  There is no CPU
+fallback: if the library is missing, or no GPU is present, calls raise.
+
+Typical use::
+
+    import torch, paper_1610_01050_gb300 as R
+    desc = R.make_desc(n=(1024, 256, 64), b=(64, 32, 8), loops=12, atten_db=80.0, p_fa=1e-6, k_max=32)
+    plan = R.rsft_plan_create(desc)
+    cube = torch.randn(1024, 256, 64, dtype=torch.complex64, device="cuda")
+    located = torch.empty(desc.max_located, dtype=torch.int64, device="cuda")
+    amp = torch.empty(desc.max_located, dtype=torch.complex64, device="cuda")
+    n = R.rsft_execute(plan, cube, located=located, amp=amp)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_size_t, c_uint64, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "librsft.so")
+
+RSFT_OK, RSFT_ERR_INVALID_ARG, RSFT_ERR_UNSUPPORTED, RSFT_ERR_OOM = 0, 1, 2, 3
+RSFT_ERR_CAPACITY, RSFT_ERR_CUDA, RSFT_ERR_TIMEOUT, RSFT_ERR_DESIGN = 4, 5, 6, 7
+RSFT_WIN_RECT, RSFT_WIN_CHEB = 0, 1
+RSFT_FLAT_IDEAL, RSFT_FLAT_CHEB = 0, 1
+RSFT_BETA_EXACT, RSFT_BETA_MEAN = 0, 1
+RSFT_WARN_SPARSITY_LIMIT = 1
+RSFT_GET_SIGMA, RSFT_GET_SIGMA_INV, RSFT_GET_GAMMA, RSFT_GET_BETA = 1, 2, 3, 4
+RSFT_GET_MU, RSFT_GET_PFA1, RSFT_GET_ETA_M, RSFT_GET_PD_BAR = 5, 6, 7, 8
+RSFT_GET_WINDOW, RSFT_GET_FLAT, RSFT_GET_WARNINGS, RSFT_GET_SNR_DB = 9, 10, 11, 12
+RSFT_GET_WORKSPACE_BYTES, RSFT_GET_STAGE_MS, RSFT_GET_FOLD_BYTES = 13, 14, 15
+RSFT_BUCKETS_FOLDED, RSFT_BUCKETS_SPECTRUM = 0, 1
+
+# Every C entry point declared in include/rsft.h.
+C_SYMBOLS = (
+    "rsft_desc_init", "rsft_plan_create", "rsft_plan_destroy", "rsft_execute",
+    "rsft_execute_async", "rsft_execute_host", "rsft_plan_get", "rsft_plan_timing", "rsft_copy_buckets",
+    "rsft_copy_detections", "rsft_refine", "rsft_status_string", "rsft_last_error",
+)
+
+
+class RsftDesc(ctypes.Structure):
+    """Mirror of ``struct rsft_desc``."""
+    _fields_ = [
+        ("ndim", c_int32), ("n", c_int64 * 4), ("b", c_int64 * 4), ("loops", c_int32),
+        ("window", c_int32), ("atten_db", c_double), ("flat", c_int32),
+        ("flat_support", c_int64 * 4), ("p_fa", c_double), ("p_d", c_double),
+        ("k_max", c_int32), ("eta_p", c_double), ("p_fa1_override", c_double),
+        ("mu_override", c_int32), ("noise_var", c_double), ("seed", c_uint64),
+        ("sigma", POINTER(c_int64)), ("beta_mode", c_int32), ("max_located", c_int64),
+        ("device", c_int32),
+    ]
+
+
+class RsftError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load librsft.so (built by ``paper_1610_01050_gb300.build.build()``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1610_01050_gb300.build.build() "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    lib.rsft_desc_init.argtypes = [POINTER(RsftDesc)]
+    lib.rsft_desc_init.restype = None
+    lib.rsft_plan_create.argtypes = [POINTER(RsftDesc), POINTER(c_void_p)]
+    lib.rsft_plan_destroy.argtypes = [c_void_p]
+    lib.rsft_plan_destroy.restype = None
+    lib.rsft_execute.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                 POINTER(c_int64)]
+    lib.rsft_execute_async.argtypes = [c_void_p] * 8
+    lib.rsft_execute_host.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_int64)]
+    lib.rsft_plan_get.argtypes = [c_void_p, c_int32, c_void_p, c_size_t]
+    lib.rsft_plan_timing.argtypes = [c_void_p, c_int32]
+    lib.rsft_copy_buckets.argtypes = [c_void_p, c_int32, c_void_p, c_void_p]
+    lib.rsft_copy_detections.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.rsft_refine.argtypes = [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_int32, ctypes.c_float,
+                                c_void_p]
+    lib.rsft_status_string.argtypes = [c_int32]
+    lib.rsft_status_string.restype = c_char_p
+    lib.rsft_last_error.argtypes = []
+    lib.rsft_last_error.restype = c_char_p
+    for name in ("rsft_plan_create", "rsft_execute", "rsft_execute_async", "rsft_execute_host",
+                 "rsft_plan_get", "rsft_plan_timing", "rsft_copy_buckets", "rsft_copy_detections",
+                 "rsft_refine"):
+        getattr(lib, name).restype = c_int32
+    _lib = lib
+    return lib
+
+
+def _check(status: int, allow=()):
+    if status != RSFT_OK and status not in allow:
+        lib = load_library()
+        raise RsftError(status, f"{lib.rsft_status_string(status).decode()}: {lib.rsft_last_error().decode()}")
+    return status
+
+
+def _ptr(x):
+    """Device or host pointer of a torch tensor / numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return c_void_p(x.ctypes.data)
+    if isinstance(x, int):
+        return c_void_p(x)
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return c_void_p(stream.cuda_stream)
+    return c_void_p(int(stream))
+
+
+class Plan:
+    """Owning handle of an ``rsft_plan``; keeps the descriptor (and sigma table) alive."""
+
+    def __init__(self, handle: c_void_p, desc: RsftDesc, keep=None):
+        self.handle = handle
+        self.desc = desc
+        self._keep = keep
+
+    @property
+    def shape(self):
+        return tuple(int(self.desc.n[i]) for i in range(self.desc.ndim))
+
+    @property
+    def buckets(self):
+        return tuple(int(self.desc.b[i]) for i in range(self.desc.ndim))
+
+    @property
+    def loops(self):
+        return int(self.desc.loops)
+
+    def close(self):
+        if self.handle:
+            load_library().rsft_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rsft_desc_init() -> RsftDesc:
+    d = RsftDesc()
+    load_library().rsft_desc_init(ctypes.byref(d))
+    return d
+
+
+def make_desc(n, b, loops, *, window=RSFT_WIN_CHEB, atten_db=60.0, flat=RSFT_FLAT_CHEB, flat_support=None,
+              p_fa=1e-6, p_d=0.9, k_max=8, eta_p=1.0, p_fa1=None, mu=None, noise_var=1.0, seed=0,
+              sigma=None, beta_mode=RSFT_BETA_EXACT, max_located=65536, device=0) -> RsftDesc:
+    """Descriptor from keyword arguments (sizes per dimension, powers of two)."""
+    d = rsft_desc_init()
+    d.ndim = len(n)
+    for i, (nn, bb) in enumerate(zip(n, b)):
+        d.n[i] = int(nn)
+        d.b[i] = int(bb)
+    d.loops = int(loops)
+    d.window = int(window)
+    d.atten_db = float(atten_db)
+    d.flat = int(flat)
+    if flat_support is not None:
+        for i, s in enumerate(flat_support):
+            d.flat_support[i] = int(s)
+    d.p_fa, d.p_d, d.k_max, d.eta_p = float(p_fa), float(p_d), int(k_max), float(eta_p)
+    d.p_fa1_override = float(p_fa1) if p_fa1 is not None else -1.0
+    d.mu_override = int(mu) if mu is not None else -1
+    d.noise_var = float(noise_var)
+    d.seed = int(seed) & ((1 << 64) - 1)
+    d.beta_mode = int(beta_mode)
+    d.max_located = int(max_located)
+    d.device = int(device)
+    if sigma is not None:
+        arr = np.ascontiguousarray(np.asarray(sigma, dtype=np.int64).reshape(-1))
+        d._sigma_keep = arr
+        d.sigma = arr.ctypes.data_as(POINTER(c_int64))
+    return d
+
+
+def rsft_plan_create(desc: RsftDesc) -> Plan:
+    lib = load_library()
+    h = c_void_p()
+    _check(lib.rsft_plan_create(ctypes.byref(desc), ctypes.byref(h)))
+    return Plan(h, desc, keep=getattr(desc, "_sigma_keep", None))
+
+
+def rsft_plan_destroy(plan: Plan) -> None:
+    plan.close()
+
+
+def rsft_execute(plan: Plan, cube, stream=None, located=None, located_votes=None, amp=None,
+                 votes_out=None, allow_capacity=False) -> int:
+    """Run the hot path on a device cube; returns the number of located frequencies."""
+    n = c_int64(0)
+    st = load_library().rsft_execute(plan.handle, _ptr(cube), _stream(stream), _ptr(located),
+                                     _ptr(located_votes), _ptr(amp), _ptr(votes_out), ctypes.byref(n))
+    _check(st, allow=(RSFT_ERR_CAPACITY,) if allow_capacity else ())
+    return int(n.value)
+
+
+def rsft_execute_async(plan: Plan, cube, count, stream=None, located=None, located_votes=None, amp=None,
+                       votes_out=None) -> None:
+    """Stream-ordered run; the located count lands in the device int64 tensor ``count``."""
+    _check(load_library().rsft_execute_async(plan.handle, _ptr(cube), _stream(stream), _ptr(located),
+                                             _ptr(located_votes), _ptr(amp), _ptr(votes_out), _ptr(count)))
+
+
+def rsft_execute_host(plan: Plan, h_cube, located, amp=None, stream=None, allow_capacity=False) -> int:
+    """End-to-end run on host buffers (numpy or CPU torch; pinned memory recommended)."""
+    n = c_int64(0)
+    st = load_library().rsft_execute_host(plan.handle, _ptr(h_cube), _stream(stream), _ptr(located), _ptr(amp),
+                                          ctypes.byref(n))
+    _check(st, allow=(RSFT_ERR_CAPACITY,) if allow_capacity else ())
+    return int(n.value)
+
+
+_GET_SHAPES = {
+    RSFT_GET_SIGMA: ("int64", "ld"), RSFT_GET_SIGMA_INV: ("int64", "ld"),
+    RSFT_GET_GAMMA: ("float64", "l"), RSFT_GET_BETA: ("float64", "l"),
+    RSFT_GET_MU: ("int32", "1"), RSFT_GET_PFA1: ("float64", "1"), RSFT_GET_ETA_M: ("float64", "1"),
+    RSFT_GET_PD_BAR: ("float64", "1"), RSFT_GET_WINDOW: ("float64", "sn"),
+    RSFT_GET_FLAT: ("float64", "2sn"), RSFT_GET_WARNINGS: ("int32", "1"),
+    RSFT_GET_SNR_DB: ("float64", "1"), RSFT_GET_WORKSPACE_BYTES: ("int64", "1"),
+    RSFT_GET_STAGE_MS: ("float64", "8"), RSFT_GET_FOLD_BYTES: ("int64", "1"),
+}
+
+
+def rsft_plan_get(plan: Plan, what: int) -> np.ndarray:
+    dt, kind = _GET_SHAPES[what]
+    d = plan.desc
+    L, D = int(d.loops), int(d.ndim)
+    sn = sum(int(d.n[i]) for i in range(D))
+    count = {"ld": L * D, "l": L, "1": 1, "8": 8, "sn": sn, "2sn": 2 * sn}[kind]
+    out = np.zeros(count, dtype=dt)
+    _check(load_library().rsft_plan_get(plan.handle, int(what), _ptr(out), out.nbytes))
+    if kind == "ld":
+        return out.reshape(L, D)
+    return out
+
+
+def rsft_plan_timing(plan: Plan, enable: bool) -> None:
+    _check(load_library().rsft_plan_timing(plan.handle, int(bool(enable))))
+
+
+def rsft_copy_buckets(plan: Plan, which: int, out, stream=None) -> None:
+    _check(load_library().rsft_copy_buckets(plan.handle, int(which), _ptr(out), _stream(stream)))
+
+
+def rsft_copy_detections(plan: Plan, out, stream=None) -> None:
+    _check(load_library().rsft_copy_detections(plan.handle, _ptr(out), _stream(stream)))
+
+
+def rsft_refine(plan: Plan, cube, k, freq, amp, steps, lr, stream=None) -> None:
+    _check(load_library().rsft_refine(plan.handle, _ptr(cube), int(k), _ptr(freq), _ptr(amp), int(steps),
+                                      ctypes.c_float(lr), _stream(stream)))
+
+
+def rsft_status_string(status: int) -> str:
+    return load_library().rsft_status_string(int(status)).decode()
+
+
+def rsft_last_error() -> str:
+    return load_library().rsft_last_error().decode()

@@ -1,0 +1,748 @@
+// C ABI of the RSFT hot path (include/rsft.h): plan lifetime, device tables,
+// workspace, and the stream-ordered launch sequence of one execute:
+//   permute_window_fold (per loop group) -> bucket_fft passes with np_detect in
+//   the last pass -> vote_scatter -> stage2_compact -> median_estimate.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "device.cuh"
+#include "plan_host.h"
+#include "rsft.h"
+
+using rsft::cplx;
+
+struct rsft_plan {
+  rsft::HostPlan host;
+  bool has_device = false;
+  int device = -1;
+  rsft::Geometry geom{};
+  rsft::FoldSchedule fold{};
+  std::vector<rsft::FftPass> passes;
+  rsft::DeviceTables tables{};
+  rsft::Workspace ws{};
+  std::vector<void*> allocations;
+  int64_t* d_count = nullptr;       // located count of the last execute
+  int64_t* h_count = nullptr;       // pinned mirror of d_count
+  void* staging = nullptr;          // cube staging buffer of rsft_execute_host
+  uint64_t* d_loc_stage = nullptr;  // located list staging of rsft_execute_host
+  float2* d_amp_stage = nullptr;
+  bool votes_dirty = false;
+  bool snr_cached = false;
+  double snr_db = 0.0;
+  bool timing = false;
+  std::vector<cudaEvent_t> event_pool;
+  std::vector<std::array<cudaEvent_t, 6>> pending;  // events of timed executes not yet summed
+  double stage_ms[6] = {0, 0, 0, 0, 0, 0};
+  int64_t timed_executes = 0;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+rsft_status fail(rsft_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+rsft_status cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return RSFT_ERR_CUDA;
+}
+
+int ilog2(int64_t v) {
+  int r = 0;
+  while ((int64_t(1) << r) < v) ++r;
+  return r;
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+template <class T>
+rsft_status dev_alloc(rsft_plan* p, T** ptr, size_t bytes) {
+  void* raw = nullptr;
+  cudaError_t e = cudaMalloc(&raw, bytes < 16 ? 16 : bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? RSFT_ERR_OOM : RSFT_ERR_CUDA,
+                std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  p->allocations.push_back(raw);
+  *ptr = static_cast<T*>(raw);
+  return RSFT_OK;
+}
+
+template <class T>
+rsft_status upload(rsft_plan* p, T** dst, const std::vector<T>& src) {
+  rsft_status st = dev_alloc(p, dst, src.size() * sizeof(T));
+  if (st != RSFT_OK) return st;
+  cudaError_t e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "upload");
+  return RSFT_OK;
+}
+
+float2 to_f2(cplx v) { return make_float2(static_cast<float>(v.real()), static_cast<float>(v.imag())); }
+
+// Choose how the fold splits rows and columns (see fold.cu).  Costs are relative to
+// the 8 bytes each cube element costs: per-element row-weight setup and partial-sum traffic.
+bool choose_fold_schedule(const rsft::Geometry& g, rsft::FoldSchedule& out) {
+  const int lg = std::min(g.loops, rsft::kMaxLoopGroup);
+  double best = 1e300;
+  bool found = false;
+  for (int d_in = 0; d_in < g.ndim; ++d_in) {
+    int64_t row_len = 1, rows_pc = 1, classes = 1, xcount = 1, after = 1;
+    for (int e = d_in; e < g.ndim; ++e) {
+      row_len *= g.n[e];
+      xcount *= g.b[e];
+    }
+    for (int e = d_in + 1; e < g.ndim; ++e) after *= g.n[e];
+    for (int e = 0; e < d_in; ++e) {
+      rows_pc *= g.m[e];
+      classes *= g.b[e];
+    }
+    const int64_t width = std::min<int64_t>(row_len, 2 * rsft::kFoldThreads);
+    if (width < row_len) {
+      // a chunk must hold whole residue periods: W = w_p * prod_{e > d_in} N_e, B_{d_in} | w_p
+      if (width % after != 0) continue;
+      if ((width / after) % g.b[d_in] != 0) continue;
+    }
+    if (xcount > width || xcount > 65535) continue;
+    if (classes > (int64_t(1) << 30)) continue;
+    const int64_t table_cap = std::max<int64_t>(1, (64 * 1024) / (16 * lg + 4));
+    int64_t rpc = 1;
+    while (rpc * 2 <= std::min(rows_pc, table_cap)) rpc *= 2;
+    const int64_t row_chunks = rows_pc / rpc;
+    const int64_t col_chunks = row_len / width;
+    const int64_t ctas = classes * row_chunks * col_chunks;
+    if (ctas > 0x7fffffff) continue;
+    const double setup = static_cast<double>(lg) / static_cast<double>(width);
+    const double partial = (row_chunks * col_chunks > 1)
+                               ? 2.0 * lg * static_cast<double>(xcount) / static_cast<double>(rpc * width)
+                               : 0.0;
+    const double fill = ctas < 2 * 152 ? static_cast<double>(2 * 152 - ctas) / (2 * 152) : 0.0;
+    const double cost = 0.5 * setup + partial + fill;
+    if (cost < best) {
+      best = cost;
+      found = true;
+      out.d_in = d_in;
+      out.row_len = row_len;
+      out.width = static_cast<int>(width);
+      out.col_chunks = static_cast<int>(col_chunks);
+      out.classes = static_cast<int>(classes);
+      out.rows_per_class = static_cast<int>(rows_pc);
+      out.rows_per_chunk = static_cast<int>(rpc);
+      out.row_chunks = static_cast<int>(row_chunks);
+      out.xcount = static_cast<int>(xcount);
+      out.mult = static_cast<int>(width / xcount);
+      out.direct = (row_chunks * col_chunks == 1) ? 1 : 0;
+    }
+  }
+  return found;
+}
+
+// Group the bucket dimensions into shared-memory FFT passes, last dimension last.
+bool plan_fft_passes(const rsft::Geometry& g, std::vector<rsft::FftPass>& passes) {
+  const int64_t target = 2048, cap = 16384;
+  passes.clear();
+  int db = g.ndim;
+  while (db > 0) {
+    int da = db - 1;
+    int64_t group = g.b[da];
+    while (da > 0 && group * g.b[da - 1] <= target) {
+      --da;
+      group *= g.b[da];
+    }
+    if (group > cap) return false;
+    rsft::FftPass ps{};
+    ps.da = da;
+    ps.db = db;
+    ps.group = group;
+    ps.inner = 1;
+    for (int e = db; e < g.ndim; ++e) ps.inner *= g.b[e];
+    ps.outer = 1;
+    for (int e = 0; e < da; ++e) ps.outer *= g.b[e];
+    ps.width = std::min<int64_t>(ps.inner, std::max<int64_t>(1, target / group));
+    ps.outer_per_cta = 1;
+    if (ps.width == ps.inner) ps.outer_per_cta = std::min<int64_t>(ps.outer, std::max<int64_t>(1, target / (group * ps.inner)));
+    ps.ctas_per_loop = (ps.outer / ps.outer_per_cta) * (ps.inner / ps.width);
+    ps.last = (db == g.ndim) ? 1 : 0;
+    passes.insert(passes.begin(), ps);
+    db = da;
+  }
+  return true;
+}
+
+rsft_status build_device(rsft_plan* p) {
+  const rsft::HostPlan& h = p->host;
+  rsft::Geometry& g = p->geom;
+  g.ndim = h.ndim;
+  g.loops = h.loops;
+  g.total_n = h.total_n;
+  g.total_b = h.total_b;
+  for (int d = 0; d < rsft::kMaxDim; ++d) {
+    g.n[d] = d < h.ndim ? h.n[d] : 1;
+    g.b[d] = d < h.ndim ? h.b[d] : 1;
+    g.m[d] = d < h.ndim ? h.m[d] : 1;
+    g.log_n[d] = ilog2(g.n[d]);
+    g.log_b[d] = ilog2(g.b[d]);
+    g.log_m[d] = ilog2(g.m[d]);
+  }
+  for (int d = 0; d < rsft::kMaxDim; ++d) {
+    g.n_shift[d] = 0;
+    g.b_shift[d] = 0;
+    for (int e = d + 1; e < h.ndim; ++e) {
+      g.n_shift[d] += g.log_n[e];
+      g.b_shift[d] += g.log_b[e];
+    }
+  }
+  if (!choose_fold_schedule(g, p->fold))
+    return fail(RSFT_ERR_UNSUPPORTED, "no fold schedule for this bucket grid (inner B_d too large)");
+  if (!plan_fft_passes(g, p->passes))
+    return fail(RSFT_ERR_UNSUPPORTED, "a bucket dimension is too large for the shared-memory FFT");
+
+  const int L = h.loops, D = h.ndim;
+  rsft_status st;
+  // per-loop, per-dimension fold weights a_{l,d}(s) = w-bar_d(sigma^{-1} s mod N_d) w_d(s)
+  for (int d = 0; d < D; ++d) {
+    const int64_t n = h.n[d];
+    std::vector<float2> tab(static_cast<size_t>(L) * n);
+    for (int l = 0; l < L; ++l) {
+      const int64_t si = h.sigma_inv[l * D + d];
+      for (int64_t s = 0; s < n; ++s) tab[l * n + s] = to_f2(h.wbar[d][(si * s) & (n - 1)] * h.w[d][s]);
+    }
+    float2* dp = nullptr;
+    if ((st = upload(p, &dp, tab)) != RSFT_OK) return st;
+    p->tables.wtab[d] = dp;
+    // twiddles e^{-j 2 pi k / B_d}
+    std::vector<float2> tw(std::max<int64_t>(1, h.b[d] / 2));
+    for (int64_t k = 0; k < h.b[d] / 2; ++k)
+      tw[k] = to_f2(std::polar(1.0, -2.0 * 3.14159265358979323846 * static_cast<double>(k) / static_cast<double>(h.b[d])));
+    if ((st = upload(p, &dp, tw)) != RSFT_OK) return st;
+    p->tables.twiddle[d] = dp;
+    // inverse pass-band gains; dimension 0 also carries 1 / prod_d sum w_d
+    std::vector<float2> gi(h.m[d]);
+    for (int64_t v = 0; v < h.m[d]; ++v) {
+      cplx x = 1.0 / h.gain_pass[d][v];
+      if (d == 0) x /= h.wsum;
+      gi[v] = to_f2(x);
+    }
+    if ((st = upload(p, &dp, gi)) != RSFT_OK) return st;
+    p->tables.ginv[d] = dp;
+  }
+  for (int d = D; d < rsft::kMaxDim; ++d) {
+    p->tables.wtab[d] = nullptr;
+    p->tables.twiddle[d] = nullptr;
+    p->tables.ginv[d] = nullptr;
+  }
+  std::vector<int> sg(L * D), si(L * D), sib(L * D);
+  for (int l = 0; l < L; ++l)
+    for (int d = 0; d < D; ++d) {
+      sg[l * D + d] = static_cast<int>(h.sigma[l * D + d]);
+      si[l * D + d] = static_cast<int>(h.sigma_inv[l * D + d]);
+      sib[l * D + d] = static_cast<int>(h.sigma_inv[l * D + d] & (h.b[d] - 1));
+    }
+  int* ip = nullptr;
+  if ((st = upload(p, &ip, sg)) != RSFT_OK) return st;
+  p->tables.sigma = ip;
+  if ((st = upload(p, &ip, si)) != RSFT_OK) return st;
+  p->tables.sigma_inv = ip;
+  if ((st = upload(p, &ip, sib)) != RSFT_OK) return st;
+  p->tables.sigma_inv_b = ip;
+  std::vector<float> gam(L);
+  for (int l = 0; l < L; ++l) gam[l] = static_cast<float>(h.gamma[l]);
+  float* fp = nullptr;
+  if ((st = upload(p, &fp, gam)) != RSFT_OK) return st;
+  p->tables.gamma = fp;
+  // fold residue tables: columns of a chunk grouped by inner residue, and residue digits
+  {
+    const rsft::FoldSchedule& fs = p->fold;
+    std::vector<unsigned short> cols(fs.width), digits(static_cast<size_t>(fs.xcount) * 4, 0);
+    std::vector<int> fill(fs.xcount, 0);
+    for (int c = 0; c < fs.width; ++c) {
+      int64_t rem = c;
+      int64_t x = 0, xstride = 1;
+      for (int d = D - 1; d >= fs.d_in; --d) {
+        const int64_t sd = rem % h.n[d];
+        rem /= h.n[d];
+        x += (sd % h.b[d]) * xstride;
+        xstride *= h.b[d];
+      }
+      cols[x * fs.mult + fill[x]++] = static_cast<unsigned short>(c);
+    }
+    for (int x = 0; x < fs.xcount; ++x) {
+      int64_t rem = x;
+      for (int d = D - 1; d >= fs.d_in; --d) {
+        digits[x * 4 + (d - fs.d_in)] = static_cast<unsigned short>(rem % h.b[d]);
+        rem /= h.b[d];
+      }
+    }
+    unsigned short* up = nullptr;
+    if ((st = upload(p, &up, cols)) != RSFT_OK) return st;
+    p->tables.cols_by_x = up;
+    if ((st = upload(p, &up, digits)) != RSFT_OK) return st;
+    p->tables.x_digits = up;
+  }
+  // workspace
+  rsft::Workspace& ws = p->ws;
+  const size_t lb = static_cast<size_t>(L) * h.total_b;
+  if ((st = dev_alloc(p, &ws.folded, lb * sizeof(float2))) != RSFT_OK) return st;
+  if ((st = dev_alloc(p, &ws.spectrum, lb * sizeof(float2))) != RSFT_OK) return st;
+  ws.partial = nullptr;
+  if (!p->fold.direct) {
+    const size_t np = static_cast<size_t>(std::min(L, rsft::kMaxLoopGroup)) * p->fold.classes *
+                      p->fold.row_chunks * p->fold.col_chunks * p->fold.xcount;
+    if ((st = dev_alloc(p, &ws.partial, np * sizeof(float2))) != RSFT_OK) return st;
+  }
+  ws.words_b = (h.total_b + 31) / 32;
+  if ((st = dev_alloc(p, &ws.det_bits, static_cast<size_t>(L) * ws.words_b * 4)) != RSFT_OK) return st;
+  if ((st = dev_alloc(p, &ws.det_count, static_cast<size_t>(L) * 4)) != RSFT_OK) return st;
+  ws.segments = rsft::stage2_segments(h.total_n);
+  const size_t vote_bytes = static_cast<size_t>(ws.segments) * 16 * 1024;
+  ws.vote_words = static_cast<int64_t>(vote_bytes / 4);
+  if ((st = dev_alloc(p, &ws.votes, vote_bytes)) != RSFT_OK) return st;
+  cudaError_t e = cudaMemset(ws.votes, 0, vote_bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(votes)");
+  if ((st = dev_alloc(p, &ws.seg_count, static_cast<size_t>(ws.segments) * 4)) != RSFT_OK) return st;
+  if ((st = dev_alloc(p, &ws.seg_offset, static_cast<size_t>(ws.segments + 1) * 8)) != RSFT_OK) return st;
+  if ((st = dev_alloc(p, &p->d_count, 8)) != RSFT_OK) return st;
+  e = cudaMallocHost(reinterpret_cast<void**>(&p->h_count), 8);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "plan upload");
+  return RSFT_OK;
+}
+
+cudaEvent_t take_event(rsft_plan* p) {
+  if (!p->event_pool.empty()) {
+    cudaEvent_t e = p->event_pool.back();
+    p->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Sum the elapsed times of all pending timed executes (waits for them).
+void drain_timing(rsft_plan* p) {
+  for (auto& ev : p->pending) {
+    bool ok = true;
+    for (cudaEvent_t e : ev) ok = ok && e != nullptr;
+    if (ok && cudaEventSynchronize(ev[5]) == cudaSuccess) {
+      float ms = 0.f;
+      for (int s = 0; s < 5; ++s)
+        if (cudaEventElapsedTime(&ms, ev[s], ev[s + 1]) == cudaSuccess) p->stage_ms[s] += ms;
+      if (cudaEventElapsedTime(&ms, ev[0], ev[5]) == cudaSuccess) p->stage_ms[5] += ms;
+      p->timed_executes += 1;
+    }
+    cudaGetLastError();
+    for (cudaEvent_t e : ev)
+      if (e) p->event_pool.push_back(e);
+  }
+  p->pending.clear();
+}
+
+int launches_per_execute(const rsft_plan* p) {
+  const int groups = (p->geom.loops + rsft::kMaxLoopGroup - 1) / rsft::kMaxLoopGroup;
+  return groups * (p->fold.direct ? 1 : 2) + static_cast<int>(p->passes.size()) + 1 + 3 + 1;
+}
+
+void release(rsft_plan* p) {
+  if (!p) return;
+  if (p->has_device) {
+    DeviceGuard guard(p->device);
+    cudaDeviceSynchronize();
+    p->pending.clear();
+    for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
+    for (void* a : p->allocations) cudaFree(a);
+    if (p->h_count) cudaFreeHost(p->h_count);
+    cudaGetLastError();
+  }
+  delete p;
+}
+
+rsft_status run(rsft_plan* p, const void* d_cube, cudaStream_t stream, uint64_t* d_located,
+                uint8_t* d_located_votes, float2* d_amp, uint8_t* d_votes_out, int64_t* d_count) {
+  const rsft::Geometry& g = p->geom;
+  rsft::Workspace& ws = p->ws;
+  cudaError_t e;
+  if (reinterpret_cast<uintptr_t>(d_cube) % 16 != 0) return fail(RSFT_ERR_INVALID_ARG, "cube must be 16-byte aligned");
+  std::array<cudaEvent_t, 6> ev{};
+  if (p->timing)
+    for (auto& x : ev) x = take_event(p);
+  auto mark = [&](int i) {
+    if (p->timing && ev[i]) cudaEventRecord(ev[i], stream);
+  };
+  if (p->votes_dirty) {
+    e = cudaMemsetAsync(ws.votes, 0, static_cast<size_t>(ws.vote_words) * 4, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "clear votes");
+  }
+  e = cudaMemsetAsync(ws.det_bits, 0, static_cast<size_t>(g.loops) * ws.words_b * 4, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws.det_count, 0, static_cast<size_t>(g.loops) * 4, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "clear detections");
+  mark(0);
+  for (int l0 = 0; l0 < g.loops; l0 += rsft::kMaxLoopGroup) {
+    const int lg = std::min(rsft::kMaxLoopGroup, g.loops - l0);
+    e = rsft::launch_fold(g, p->fold, p->tables, static_cast<const float2*>(d_cube), l0, lg, ws.folded,
+                          ws.partial, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "permute_window_fold");
+    if (!p->fold.direct) {
+      e = rsft::launch_fold_reduce(g, p->fold, p->tables, l0, lg, ws.partial, ws.folded, stream);
+      if (e != cudaSuccess) return cuda_fail(e, "fold reduce");
+    }
+  }
+  mark(1);
+  for (size_t i = 0; i < p->passes.size(); ++i) {
+    e = rsft::launch_fft_pass(g, p->passes[i], p->tables, i == 0 ? ws.folded : ws.spectrum, ws.spectrum,
+                              ws.det_bits, ws.det_count, ws.words_b, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "bucket_fft/np_detect");
+  }
+  mark(2);
+  p->votes_dirty = true;
+  e = rsft::launch_vote_scatter(g, p->tables, ws.det_bits, ws.words_b, ws.votes, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "vote_scatter");
+  mark(3);
+  e = rsft::launch_stage2(g, p->host.mu, ws, d_located, d_located_votes, d_votes_out, p->host.desc.max_located,
+                          d_count, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stage2_compact");
+  p->votes_dirty = false;
+  mark(4);
+  if (d_amp && p->host.desc.max_located > 0) {
+    e = rsft::launch_median(g, p->tables, ws.spectrum, d_located, d_count, p->host.desc.max_located, d_amp, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "median_estimate");
+  }
+  mark(5);
+  if (p->timing) p->pending.push_back(ev);
+  return RSFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rsft_desc_init(rsft_desc* d) {
+  if (!d) return;
+  std::memset(d, 0, sizeof(*d));
+  d->ndim = 0;
+  for (int i = 0; i < 4; ++i) {
+    d->n[i] = 1;
+    d->b[i] = 1;
+    d->flat_support[i] = 0;
+  }
+  d->loops = 8;
+  d->window = RSFT_WIN_CHEB;
+  d->atten_db = 60.0;
+  d->flat = RSFT_FLAT_CHEB;
+  d->p_fa = 1e-6;
+  d->p_d = 0.9;
+  d->k_max = 8;
+  d->eta_p = 1.0;
+  d->p_fa1_override = -1.0;
+  d->mu_override = -1;
+  d->noise_var = 1.0;
+  d->seed = 0;
+  d->sigma = nullptr;
+  d->beta_mode = RSFT_BETA_EXACT;
+  d->max_located = 65536;
+  d->device = 0;
+}
+
+rsft_status rsft_plan_create(const rsft_desc* desc, rsft_plan** plan) {
+  if (!plan) return fail(RSFT_ERR_INVALID_ARG, "plan is NULL");
+  *plan = nullptr;
+  if (!desc) return fail(RSFT_ERR_INVALID_ARG, "desc is NULL");
+  rsft_plan* p = new (std::nothrow) rsft_plan();
+  if (!p) return fail(RSFT_ERR_OOM, "host allocation");
+  std::string err;
+  rsft_status st = rsft::build_host_plan(*desc, p->host, err);
+  if (st != RSFT_OK) {
+    delete p;
+    return fail(st, err);
+  }
+  if (desc->device >= 0) {
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || desc->device >= count) {
+      cudaGetLastError();
+      delete p;
+      return fail(RSFT_ERR_CUDA, std::string("no CUDA device ") + std::to_string(desc->device) +
+                                     (e != cudaSuccess ? std::string(": ") + cudaGetErrorString(e) : ""));
+    }
+    p->has_device = true;
+    p->device = desc->device;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) {
+      p->has_device = false;
+      delete p;
+      return fail(RSFT_ERR_CUDA, "cudaSetDevice failed");
+    }
+    st = build_device(p);
+    if (st != RSFT_OK) {
+      std::string msg = g_last_error;
+      release(p);
+      return fail(st, msg);
+    }
+  }
+  *plan = p;
+  g_last_error.clear();
+  return RSFT_OK;
+}
+
+void rsft_plan_destroy(rsft_plan* plan) { release(plan); }
+
+rsft_status rsft_execute_async(rsft_plan* plan, const void* d_cube, void* stream, uint64_t* d_located,
+                               uint8_t* d_located_votes, void* d_amp, uint8_t* d_votes_out,
+                               int64_t* d_n_located) {
+  if (!plan || !d_cube || !d_n_located) return fail(RSFT_ERR_INVALID_ARG, "NULL plan, cube or count");
+  if (!plan->has_device) return fail(RSFT_ERR_INVALID_ARG, "host-only plan cannot execute");
+  if (plan->host.desc.max_located > 0 && !d_located) return fail(RSFT_ERR_INVALID_ARG, "d_located is NULL");
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return fail(RSFT_ERR_CUDA, "cudaSetDevice failed");
+  return run(plan, d_cube, static_cast<cudaStream_t>(stream), d_located, d_located_votes,
+             static_cast<float2*>(d_amp), d_votes_out, d_n_located);
+}
+
+rsft_status rsft_execute(rsft_plan* plan, const void* d_cube, void* stream, uint64_t* d_located,
+                         uint8_t* d_located_votes, void* d_amp, uint8_t* d_votes_out, int64_t* n_located) {
+  if (!plan || !n_located) return fail(RSFT_ERR_INVALID_ARG, "NULL plan or n_located");
+  if (!plan->has_device) return fail(RSFT_ERR_INVALID_ARG, "host-only plan cannot execute");
+  rsft_status st = rsft_execute_async(plan, d_cube, stream, d_located, d_located_votes, d_amp, d_votes_out,
+                                      plan->d_count);
+  if (st != RSFT_OK) return st;
+  DeviceGuard guard(plan->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(plan->h_count, plan->d_count, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "rsft_execute");
+  *n_located = *plan->h_count;
+  if (*n_located > plan->host.desc.max_located)
+    return fail(RSFT_ERR_CAPACITY, "located list truncated to max_located");
+  return RSFT_OK;
+}
+
+rsft_status rsft_execute_host(rsft_plan* plan, const void* h_cube, void* stream, uint64_t* h_located,
+                              void* h_amp, int64_t* n_located) {
+  if (!plan || !h_cube || !n_located) return fail(RSFT_ERR_INVALID_ARG, "NULL plan, cube or count");
+  if (!plan->has_device) return fail(RSFT_ERR_INVALID_ARG, "host-only plan cannot execute");
+  const int64_t cap = plan->host.desc.max_located;
+  if (cap > 0 && !h_located) return fail(RSFT_ERR_INVALID_ARG, "h_located is NULL");
+  DeviceGuard guard(plan->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rsft_status st;
+  const size_t cube_bytes = static_cast<size_t>(plan->host.total_n) * 8;
+  if (!plan->staging) {
+    if ((st = dev_alloc(plan, &plan->staging, cube_bytes)) != RSFT_OK) return st;
+    if ((st = dev_alloc(plan, &plan->d_loc_stage, static_cast<size_t>(std::max<int64_t>(cap, 1)) * 8)) != RSFT_OK)
+      return st;
+    if ((st = dev_alloc(plan, &plan->d_amp_stage, static_cast<size_t>(std::max<int64_t>(cap, 1)) * 8)) != RSFT_OK)
+      return st;
+  }
+  cudaError_t e = cudaMemcpyAsync(plan->staging, h_cube, cube_bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "copy cube to device");
+  st = run(plan, plan->staging, s, plan->d_loc_stage, nullptr, h_amp ? plan->d_amp_stage : nullptr, nullptr,
+           plan->d_count);
+  if (st != RSFT_OK) return st;
+  e = cudaMemcpyAsync(plan->h_count, plan->d_count, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "rsft_execute_host");
+  const int64_t cnt = *plan->h_count;
+  const int64_t ncopy = std::min(cnt, cap);
+  if (ncopy > 0) {
+    e = cudaMemcpyAsync(h_located, plan->d_loc_stage, static_cast<size_t>(ncopy) * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && h_amp)
+      e = cudaMemcpyAsync(h_amp, plan->d_amp_stage, static_cast<size_t>(ncopy) * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "copy located to host");
+  }
+  *n_located = cnt;
+  if (cnt > cap) return fail(RSFT_ERR_CAPACITY, "located list truncated to max_located");
+  return RSFT_OK;
+}
+
+rsft_status rsft_plan_get(const rsft_plan* plan, int32_t what, void* out, size_t bytes) {
+  if (!plan || !out) return fail(RSFT_ERR_INVALID_ARG, "NULL plan or out");
+  const rsft::HostPlan& h = plan->host;
+  const int L = h.loops, D = h.ndim;
+  auto need = [&](size_t n) { return bytes >= n; };
+  switch (what) {
+    case RSFT_GET_SIGMA:
+    case RSFT_GET_SIGMA_INV: {
+      const size_t n = static_cast<size_t>(L) * D * 8;
+      if (!need(n)) break;
+      std::memcpy(out, (what == RSFT_GET_SIGMA ? h.sigma : h.sigma_inv).data(), n);
+      return RSFT_OK;
+    }
+    case RSFT_GET_GAMMA:
+    case RSFT_GET_BETA: {
+      const size_t n = static_cast<size_t>(L) * 8;
+      if (!need(n)) break;
+      std::memcpy(out, (what == RSFT_GET_GAMMA ? h.gamma : h.beta).data(), n);
+      return RSFT_OK;
+    }
+    case RSFT_GET_MU:
+      if (!need(4)) break;
+      *static_cast<int32_t*>(out) = h.mu;
+      return RSFT_OK;
+    case RSFT_GET_PFA1:
+    case RSFT_GET_ETA_M:
+    case RSFT_GET_PD_BAR:
+      if (!need(8)) break;
+      *static_cast<double*>(out) = what == RSFT_GET_PFA1 ? h.pfa1 : (what == RSFT_GET_ETA_M ? h.eta_m : h.pd_bar);
+      return RSFT_OK;
+    case RSFT_GET_WINDOW: {
+      size_t total = 0;
+      for (int d = 0; d < D; ++d) total += h.w[d].size();
+      if (!need(total * 8)) break;
+      double* o = static_cast<double*>(out);
+      for (int d = 0; d < D; ++d) o = std::copy(h.w[d].begin(), h.w[d].end(), o);
+      return RSFT_OK;
+    }
+    case RSFT_GET_FLAT: {
+      size_t total = 0;
+      for (int d = 0; d < D; ++d) total += h.wbar[d].size();
+      if (!need(total * 16)) break;
+      double* o = static_cast<double*>(out);
+      for (int d = 0; d < D; ++d)
+        for (const cplx& v : h.wbar[d]) {
+          *o++ = v.real();
+          *o++ = v.imag();
+        }
+      return RSFT_OK;
+    }
+    case RSFT_GET_WARNINGS:
+      if (!need(4)) break;
+      *static_cast<int32_t*>(out) = h.warnings;
+      return RSFT_OK;
+    case RSFT_GET_SNR_DB: {
+      if (!need(8)) break;
+      rsft_plan* mp = const_cast<rsft_plan*>(plan);
+      if (!mp->snr_cached) {
+        mp->snr_db = rsft::design_snr_db(h);
+        mp->snr_cached = true;
+      }
+      *static_cast<double*>(out) = mp->snr_db;
+      return RSFT_OK;
+    }
+    case RSFT_GET_WORKSPACE_BYTES: {
+      if (!need(8)) break;
+      int64_t tot = 0;
+      if (plan->has_device) {
+        const rsft::Workspace& ws = plan->ws;
+        tot += 2 * static_cast<int64_t>(L) * h.total_b * 8 + static_cast<int64_t>(L) * ws.words_b * 4 +
+               ws.vote_words * 4 + ws.segments * 12;
+        if (!plan->fold.direct)
+          tot += static_cast<int64_t>(std::min(L, rsft::kMaxLoopGroup)) * plan->fold.classes *
+                 plan->fold.row_chunks * plan->fold.col_chunks * plan->fold.xcount * 8;
+      }
+      *static_cast<int64_t*>(out) = tot;
+      return RSFT_OK;
+    }
+    case RSFT_GET_STAGE_MS: {
+      if (!need(64)) break;
+      rsft_plan* mp = const_cast<rsft_plan*>(plan);
+      if (mp->has_device) {
+        DeviceGuard guard(mp->device);
+        drain_timing(mp);
+      }
+      double* o = static_cast<double*>(out);
+      for (int s = 0; s < 6; ++s) o[s] = mp->stage_ms[s];
+      o[6] = static_cast<double>(mp->timed_executes);
+      o[7] = mp->has_device ? static_cast<double>(launches_per_execute(mp)) : 0.0;
+      return RSFT_OK;
+    }
+    case RSFT_GET_FOLD_BYTES: {
+      if (!need(8)) break;
+      const int groups = (L + rsft::kMaxLoopGroup - 1) / rsft::kMaxLoopGroup;
+      *static_cast<int64_t*>(out) = groups * h.total_n * 8 + static_cast<int64_t>(L) * h.total_b * 8;
+      return RSFT_OK;
+    }
+    default:
+      return fail(RSFT_ERR_INVALID_ARG, "unknown rsft_plan_get item");
+  }
+  return fail(RSFT_ERR_INVALID_ARG, "output buffer too small");
+}
+
+rsft_status rsft_plan_timing(rsft_plan* plan, int32_t enable) {
+  if (!plan) return fail(RSFT_ERR_INVALID_ARG, "NULL plan");
+  if (!plan->has_device) return fail(RSFT_ERR_INVALID_ARG, "host-only plan");
+  DeviceGuard guard(plan->device);
+  drain_timing(plan);
+  for (double& v : plan->stage_ms) v = 0.0;
+  plan->timed_executes = 0;
+  plan->timing = enable != 0;
+  return RSFT_OK;
+}
+
+rsft_status rsft_copy_buckets(rsft_plan* plan, int32_t which, void* d_out, void* stream) {
+  if (!plan || !d_out) return fail(RSFT_ERR_INVALID_ARG, "NULL plan or output");
+  if (!plan->has_device) return fail(RSFT_ERR_INVALID_ARG, "host-only plan");
+  if (which != RSFT_BUCKETS_FOLDED && which != RSFT_BUCKETS_SPECTRUM) return fail(RSFT_ERR_INVALID_ARG, "which");
+  DeviceGuard guard(plan->device);
+  const size_t n = static_cast<size_t>(plan->host.loops) * plan->host.total_b * 8;
+  cudaError_t e = cudaMemcpyAsync(d_out, which == RSFT_BUCKETS_FOLDED ? plan->ws.folded : plan->ws.spectrum, n,
+                                  cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "rsft_copy_buckets");
+  return RSFT_OK;
+}
+
+rsft_status rsft_copy_detections(rsft_plan* plan, void* d_out, void* stream) {
+  if (!plan || !d_out) return fail(RSFT_ERR_INVALID_ARG, "NULL plan or output");
+  if (!plan->has_device) return fail(RSFT_ERR_INVALID_ARG, "host-only plan");
+  DeviceGuard guard(plan->device);
+  const size_t n = static_cast<size_t>(plan->host.loops) * plan->ws.words_b * 4;
+  cudaError_t e = cudaMemcpyAsync(d_out, plan->ws.det_bits, n, cudaMemcpyDeviceToDevice,
+                                  static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "rsft_copy_detections");
+  return RSFT_OK;
+}
+
+rsft_status rsft_refine(rsft_plan* plan, const void* d_cube, int64_t k, float* d_freq, void* d_amp,
+                        int32_t steps, float lr, void* stream) {
+  (void)plan;
+  (void)d_cube;
+  (void)k;
+  (void)d_freq;
+  (void)d_amp;
+  (void)steps;
+  (void)lr;
+  (void)stream;
+  return fail(RSFT_ERR_UNSUPPORTED, "rsft_refine is not implemented yet");
+}
+
+const char* rsft_status_string(rsft_status s) {
+  switch (s) {
+    case RSFT_OK: return "ok";
+    case RSFT_ERR_INVALID_ARG: return "invalid argument";
+    case RSFT_ERR_UNSUPPORTED: return "unsupported";
+    case RSFT_ERR_OOM: return "out of memory";
+    case RSFT_ERR_CAPACITY: return "output capacity exceeded";
+    case RSFT_ERR_CUDA: return "CUDA error";
+    case RSFT_ERR_TIMEOUT: return "device wait timed out";
+    case RSFT_ERR_DESIGN: return "threshold design infeasible";
+  }
+  return "unknown status";
+}
+
+const char* rsft_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// Device-side geometry, schedules and kernel launchers of the RSFT hot path.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rsft {
+
+constexpr int kMaxDim = 4;
+constexpr int kMaxLoopGroup = 16;    // loops folded per pass over the cube
+constexpr int kFoldThreads = 256;    // threads per fold CTA (two elements each per row step)
+
+// Sizes of the cube and the bucket grid, in the form the kernels index with.
+struct Geometry {
+  int ndim;
+  int loops;
+  int64_t n[kMaxDim];
+  int64_t b[kMaxDim];
+  int64_t m[kMaxDim];
+  int log_n[kMaxDim];
+  int log_b[kMaxDim];
+  int log_m[kMaxDim];
+  int64_t total_n;
+  int64_t total_b;
+  int n_shift[kMaxDim];   // log2 of prod_{e>d} N_e (linear frequency index)
+  int b_shift[kMaxDim];   // log2 of prod_{e>d} B_e (linear bucket index)
+};
+
+// How the fold splits the cube: dimensions [0, d_in) index rows, [d_in, D) columns.
+// A CTA owns one outer residue class (x_e = s_e mod B_e, e < d_in), one chunk of that
+// class's rows and one chunk of W columns; each thread keeps two fixed columns.
+struct FoldSchedule {
+  int d_in;               // first inner (column) dimension
+  int64_t row_len;        // prod_{e >= d_in} N_e
+  int width;              // W: columns per chunk (power of two, divides 2 * threads)
+  int col_chunks;         // row_len / W
+  int classes;            // prod_{e < d_in} B_e
+  int rows_per_class;     // prod_{e < d_in} M_e
+  int rows_per_chunk;
+  int row_chunks;
+  int xcount;             // X: inner residues per chunk = prod_{e >= d_in} B_e
+  int mult;               // columns per residue in a chunk = W / X
+  int smem_bytes;         // dynamic shared memory of one fold CTA (per loop-group size)
+  int direct;             // 1: one chunk per class, write buckets directly
+};
+
+// One FFT pass over the bucket arrays: transforms dimensions [da, db) in shared memory.
+struct FftPass {
+  int da, db;
+  int64_t group;          // prod_{da <= d < db} B_d
+  int64_t inner;          // prod_{d >= db} B_d
+  int64_t outer;          // prod_{d < da} B_d
+  int64_t width;          // W consecutive inner indices per slab
+  int64_t outer_per_cta;  // consecutive outer indices per CTA (when width == inner)
+  int64_t ctas_per_loop;
+  int last;               // final pass: writes the spectrum and the detections
+};
+
+// Device pointers and tables owned by a plan.
+struct DeviceTables {
+  const float2* wtab[kMaxDim];   // [L][N_d]: w-bar_d(sigma^{-1} s mod N_d) * w_d(s)
+  const int* sigma;              // [L][D]
+  const int* sigma_inv;          // [L][D] mod N_d
+  const int* sigma_inv_b;        // [L][D] sigma^{-1} mod B_d
+  const float* gamma;            // [L]
+  const float2* twiddle[kMaxDim];// [B_d / 2]: e^{-j 2 pi k / B_d}
+  const float2* ginv[kMaxDim];   // [M_d]: 1 / G_d(-v) (dimension 0 also holds 1 / sum w)
+  const unsigned short* cols_by_x;  // [W]: chunk columns grouped by inner residue
+  const unsigned short* x_digits;   // [X][4]: inner residue digit per inner dimension
+};
+
+struct Workspace {
+  float2* folded;        // [L][B]   f_l (paper order)
+  float2* spectrum;      // [L][B]   f-hat_l
+  float2* partial;       // [L][classes][chunks][X] fold partial sums (chunked schedules)
+  uint32_t* det_bits;    // [L][words_b]
+  uint32_t* det_count;   // [L]
+  uint32_t* votes;       // [ceil(N / 16) * 4] packed 8-bit votes
+  uint32_t* seg_count;   // [segments] stage-2 hits per segment
+  uint64_t* seg_offset;  // [segments + 1] exclusive scan of seg_count; last = total
+  int64_t words_b;
+  int64_t segments;
+  int64_t vote_words;
+};
+
+// Launchers (return cudaSuccess or the launch error).
+cudaError_t launch_fold(const Geometry& g, const FoldSchedule& fs, const DeviceTables& t,
+                        const float2* cube, int loop0, int lg, float2* folded, float2* partial,
+                        cudaStream_t stream);
+cudaError_t launch_fold_reduce(const Geometry& g, const FoldSchedule& fs, const DeviceTables& t,
+                               int loop0, int lg, const float2* partial, float2* folded,
+                               cudaStream_t stream);
+cudaError_t launch_fft_pass(const Geometry& g, const FftPass& ps, const DeviceTables& t,
+                            const float2* in, float2* out, uint32_t* det_bits, uint32_t* det_count,
+                            int64_t words_b, cudaStream_t stream);
+cudaError_t launch_vote_scatter(const Geometry& g, const DeviceTables& t, const uint32_t* det_bits,
+                                int64_t words_b, uint32_t* votes, cudaStream_t stream);
+cudaError_t launch_stage2(const Geometry& g, int mu, Workspace& ws, uint64_t* located,
+                          uint8_t* located_votes, uint8_t* votes_out, int64_t capacity,
+                          int64_t* d_count, cudaStream_t stream);
+cudaError_t launch_median(const Geometry& g, const DeviceTables& t, const float2* spectrum,
+                          const uint64_t* located, const int64_t* d_count, int64_t capacity,
+                          float2* amp, cudaStream_t stream);
+int64_t stage2_segments(int64_t total_n);   // 16 KiB vote segments covering N bytes
+
+int fold_smem_bytes(const FoldSchedule& fs, int lg);
+
+}  // namespace rsft

@@ -1,0 +1,132 @@
+"""The C ABI without a GPU: library loads, exports every declared symbol, builds
+host-only plans whose tables match the oracle, and rejects bad descriptors."""
+import re
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1610_01050_gb300 as R
+from paper_1610_01050_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return R.load_library()
+
+
+def test_exports_every_declared_symbol(lib):
+    header = open(os.path.join(ROOT, "include", "rsft.h")).read()
+    declared = set(re.findall(r"\b(rsft_[a-z_]+)\s*\(", header))
+    assert declared == set(R.C_SYMBOLS)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    for s in range(8):
+        assert R.rsft_status_string(s) and R.rsft_status_string(s) != "unknown status"
+
+
+CASES = [
+    dict(n=(256, 256), b=(16, 16), loops=8, atten=60.0, flat="cheb", support=(64, 64), k=8, pfa=1e-4),
+    dict(n=(1024, 256, 64), b=(64, 32, 8), loops=12, atten=80.0, flat="cheb", support=None, k=32, pfa=1e-6),
+    dict(n=(64, 32, 16, 8), b=(8, 4, 2, 2), loops=16, atten=60.0, flat="ideal", support=None, k=2, pfa=1e-5),
+    dict(n=(4096,), b=(64,), loops=5, atten=45.0, flat="cheb", support=(512,), k=3, pfa=1e-6),
+]
+
+
+@pytest.mark.parametrize("c", CASES, ids=[str(c["n"]) for c in CASES])
+def test_host_plan_matches_oracle(lib, c):
+    flat = R.RSFT_FLAT_CHEB if c["flat"] == "cheb" else R.RSFT_FLAT_IDEAL
+    d = R.make_desc(c["n"], c["b"], c["loops"], atten_db=c["atten"], flat=flat, flat_support=c["support"],
+                    p_fa=c["pfa"], k_max=c["k"], seed=1234, device=-1)
+    p = R.rsft_plan_create(d)
+    op = O.make_plan(c["n"], c["b"], c["loops"], seed=1234, atten_db=c["atten"], flat=c["flat"],
+                     flat_support=c["support"], p_fa=c["pfa"], k_max=c["k"])
+    np.testing.assert_array_equal(R.rsft_plan_get(p, R.RSFT_GET_SIGMA), op.sigma)
+    np.testing.assert_array_equal(R.rsft_plan_get(p, R.RSFT_GET_SIGMA_INV), op.sigma_inv)
+    # Chebyshev samples T_{n-1}(x0 cos(pi k / n)) near |x| = 1 have a condition number of
+    # about n / sqrt(x0^2 - 1) (~3e6 at n = 4096, 45 dB): two correct FP64 routes agree to ~1e-10.
+    np.testing.assert_allclose(R.rsft_plan_get(p, R.RSFT_GET_WINDOW), np.concatenate(op.w), atol=1e-9)
+    fl = R.rsft_plan_get(p, R.RSFT_GET_FLAT).reshape(-1, 2)
+    ofl = np.concatenate(op.wbar)
+    assert np.max(np.abs(fl[:, 0] + 1j * fl[:, 1] - ofl)) < 1e-9 * np.max(np.abs(ofl))
+    np.testing.assert_allclose(R.rsft_plan_get(p, R.RSFT_GET_BETA), op.beta, rtol=1e-8)
+    np.testing.assert_allclose(R.rsft_plan_get(p, R.RSFT_GET_GAMMA), op.gamma, rtol=1e-8)
+    assert int(R.rsft_plan_get(p, R.RSFT_GET_MU)[0]) == op.mu
+    assert abs(R.rsft_plan_get(p, R.RSFT_GET_PFA1)[0] / op.pfa1 - 1) < 1e-8
+    assert abs(R.rsft_plan_get(p, R.RSFT_GET_ETA_M)[0] / op.eta_m - 1) < 1e-8
+
+
+def test_explicit_sigma_and_overrides(lib):
+    sig = np.array([[3, 5], [7, 9], [1, 31]], dtype=np.int64)
+    d = R.make_desc((32, 64), (4, 8), 3, sigma=sig, p_fa1=0.01, mu=1, noise_var=2.0, device=-1)
+    p = R.rsft_plan_create(d)
+    np.testing.assert_array_equal(R.rsft_plan_get(p, R.RSFT_GET_SIGMA), sig)
+    inv = R.rsft_plan_get(p, R.RSFT_GET_SIGMA_INV)
+    assert np.all((sig * inv) % np.array([32, 64]) == 1)
+    assert int(R.rsft_plan_get(p, R.RSFT_GET_MU)[0]) == 1
+    op = O.make_plan((32, 64), (4, 8), 3, sigma=sig, pfa1=0.01, mu=1, noise_var=2.0)
+    np.testing.assert_allclose(R.rsft_plan_get(p, R.RSFT_GET_GAMMA), op.gamma, rtol=1e-10)
+
+
+def test_design_snr_matches_oracle(lib):
+    n, b = (1024,), (64,)
+    d = R.make_desc(n, b, 50, atten_db=40.0, p_fa=1e-6, p_d=0.9, k_max=4, device=-1)
+    p = R.rsft_plan_create(d)
+    op = O.make_plan(n, b, 50, atten_db=40.0, p_fa=1e-6, p_d=0.9, k_max=4)
+    ab = O.mean_alpha(op.wbar, op.w, list(b), [2 * np.pi * (1024 / 16 + 0.5) / 1024])
+    bb = O.mean_beta(op.wbar, op.w)
+    snr = 10 * np.log10((bb / ab) * (np.log(op.pfa1) / np.log(op.design["pd_bar"]) - 1))
+    assert abs(R.rsft_plan_get(p, R.RSFT_GET_SNR_DB)[0] - snr) < 1e-8
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(n=(30, 64), b=(2, 8), loops=4), R.RSFT_ERR_INVALID_ARG),        # not a power of two
+    (dict(n=(32, 64), b=(64, 8), loops=4), R.RSFT_ERR_INVALID_ARG),       # B > N
+    (dict(n=(32, 64), b=(4, 8), loops=0), R.RSFT_ERR_INVALID_ARG),        # no loops
+    (dict(n=(32, 64), b=(4, 8), loops=256), R.RSFT_ERR_INVALID_ARG),      # votes overflow 8 bits
+    (dict(n=(32, 64), b=(4, 8), loops=4, flat_support=(3, 0)), R.RSFT_ERR_INVALID_ARG),
+    (dict(n=(32, 64), b=(4, 8), loops=4, mu=4, p_fa1=0.1), R.RSFT_ERR_INVALID_ARG),
+    (dict(n=(32, 64), b=(4, 8), loops=4, noise_var=0.0), R.RSFT_ERR_UNSUPPORTED),
+    (dict(n=(32, 64), b=(4, 8), loops=4, sigma=[[2, 3]] * 4), R.RSFT_ERR_INVALID_ARG),  # even sigma
+    (dict(n=(64, 64), b=(4, 4), loops=12, k_max=64, p_fa=1e-9), R.RSFT_ERR_DESIGN),    # K eta_m >= B
+])
+def test_invalid_descriptors(lib, kw, status):
+    kw = dict(kw)
+    d = R.make_desc(kw.pop("n"), kw.pop("b"), kw.pop("loops"), device=-1, **kw)
+    with pytest.raises(R.RsftError) as ei:
+        R.rsft_plan_create(d)
+    assert ei.value.status == status
+    assert R.rsft_last_error()
+
+
+def test_ndim_limits(lib):
+    d = R.rsft_desc_init()
+    d.ndim = 5
+    d.device = -1
+    with pytest.raises(R.RsftError) as ei:
+        R.rsft_plan_create(d)
+    assert ei.value.status == R.RSFT_ERR_UNSUPPORTED
+    d.ndim = 0
+    with pytest.raises(R.RsftError) as ei:
+        R.rsft_plan_create(d)
+    assert ei.value.status == R.RSFT_ERR_INVALID_ARG
+
+
+def test_host_plan_cannot_execute(lib):
+    p = R.rsft_plan_create(R.make_desc((32, 64), (4, 8), 3, p_fa1=0.01, mu=1, device=-1))
+    cube = np.zeros((32, 64), dtype=np.complex64)
+    with pytest.raises(R.RsftError) as ei:
+        R.rsft_execute(p, cube)
+    assert ei.value.status == R.RSFT_ERR_INVALID_ARG
+
+
+def test_sparsity_limit_warning(lib):
+    p = R.rsft_plan_create(R.make_desc((64, 64), (4, 4), 8, k_max=64, p_fa1=0.01, mu=3, device=-1))
+    assert int(R.rsft_plan_get(p, R.RSFT_GET_WARNINGS)[0]) & R.RSFT_WARN_SPARSITY_LIMIT
