@@ -224,7 +224,7 @@ def run_ours(args):
     cubes = [h.to(dev) for h in host]
     seed = ri.frame_seed(wl, 0)
     plan = R.rsft_plan_create(workload_desc(R, wl, nv, seed))
-    cap = 65536
+    cap = 1 << 20
     located = torch.zeros(cap, dtype=torch.int64, device=dev)
     amp = torch.zeros(cap, dtype=torch.complex64, device=dev)
     count = torch.zeros(1, dtype=torch.int64, device=dev)

@@ -71,6 +71,7 @@ def test_parity_small(name, n, b, loops, extra):
     g = gpu_run(d, cube)
     ref = O.rsft(op, cube.astype(np.complex128))
     rep = compare_full(g, ref, op)
+    print(f"parity {name}: {rep}")
     assert rep["detected"] > 0
 
 
@@ -172,7 +173,7 @@ def _full_oracle_case(name, frame=0):
     cube, tg, wl, nv = ri.workload_frame(name, frame)
     d, op = make_pair(wl.shape, wl.buckets, wl.loops, seed=ri.frame_seed(wl, frame), atten=wl.atten_db,
                       support=wl.flat_support, noise_var=nv, p_fa=wl.p_fa,
-                      k_max=wl.k_range[1])
+                      k_max=wl.k_range[1], max_located=1 << 20)
     g = gpu_run(d, cube)
     ref = O.rsft(op, cube.astype(np.complex128))
     return compare_full(g, ref, op), g, ref, tg, wl
@@ -181,6 +182,7 @@ def _full_oracle_case(name, frame=0):
 @pytest.mark.parametrize("name", ["c2_3d_radar", "c3_large", "c4_2d_4096"])
 def test_parity_full_workload(name):
     rep, g, ref, tg, wl = _full_oracle_case(name)
+    print(f"parity {name}: {rep}")
     assert rep["detected"] > 0 and rep["located"] > 0
 
 
@@ -191,7 +193,7 @@ def test_parity_c5_sampled():
     name = "c5_4d"
     cube, tg, wl, nv = ri.workload_frame(name, 0)
     d, op = make_pair(wl.shape, wl.buckets, wl.loops, seed=ri.frame_seed(wl, 0), atten=wl.atten_db,
-                      noise_var=nv, p_fa=wl.p_fa, k_max=wl.k_range[1])
+                      noise_var=nv, p_fa=wl.p_fa, k_max=wl.k_range[1], max_located=1 << 22)
     g = gpu_run(d, cube, want_votes=True)
     compare_tables(g["plan"], op)
     rng = np.random.default_rng(5)
