@@ -207,6 +207,36 @@ rsft_status rsft_refine(rsft_plan* plan, const void* d_cube, int64_t k,
                         float* d_freq, void* d_amp, int32_t steps, float lr,
                         void* stream);
 
+/*
+ * Second-stage detection (o = {i : votes[i] > mu}, ascending) for callers that
+ * cannot allocate device memory.  The paper has no counterpart: this is the
+ * stage2_compact step of rsft_execute offered on its own, for code that must
+ * not call cudaMalloc or cudaFree when it runs (a real-time loop whose memory
+ * is fixed at start-up, a host framework that owns every allocation, code
+ * that cannot afford the device synchronisation those calls may cause).
+ *   d_votes          device uint8 [n], 16-byte aligned: the accumulated votes
+ *                    (eq. (a_i)), e.g. rsft_execute's d_votes_out.  Cleared to
+ *                    zero on return, as rsft_execute clears its own votes.
+ *   n                number of votes: a multiple of 16384, at most 2^28.
+ *   mu               second-stage threshold, 0..254.
+ *   d_located        device uint64 [capacity]: located indices, ascending.
+ *   d_located_votes  device uint8 [capacity] or NULL: their vote counts.
+ *   d_count          device int64 [1]: number located (may exceed capacity;
+ *                    then only the first `capacity` are written).
+ * Runs on the current device, stream-ordered.  It allocates nothing: its
+ * scratch (per-segment counts and offsets, about 192 KiB) is a fixed array in
+ * the library's device memory that every GPU loading the library holds until
+ * the process exits.  The first call on a device looks that array up
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls share the one array: calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.
+ * Errors: INVALID_ARG for NULL pointers, misalignment, n not a multiple of
+ * 16384 or above 2^28, mu out of range; CUDA for launch failures.
+ */
+rsft_status rsft_stage2_static(uint8_t* d_votes, int64_t n, int32_t mu, uint64_t* d_located,
+                               uint8_t* d_located_votes, int64_t capacity, int64_t* d_count,
+                               void* stream);
+
 /* Static description of a status code (never NULL). */
 const char* rsft_status_string(rsft_status status);
 

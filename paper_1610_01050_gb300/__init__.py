@@ -42,7 +42,8 @@ RSFT_BUCKETS_FOLDED, RSFT_BUCKETS_SPECTRUM = 0, 1
 C_SYMBOLS = (
     "rsft_desc_init", "rsft_plan_create", "rsft_plan_destroy", "rsft_execute",
     "rsft_execute_async", "rsft_execute_host", "rsft_plan_get", "rsft_plan_timing", "rsft_copy_buckets",
-    "rsft_copy_detections", "rsft_refine", "rsft_status_string", "rsft_last_error",
+    "rsft_copy_detections", "rsft_refine", "rsft_stage2_static", "rsft_status_string",
+    "rsft_last_error",
 )
 
 
@@ -92,13 +93,15 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rsft_copy_detections.argtypes = [c_void_p, c_void_p, c_void_p]
     lib.rsft_refine.argtypes = [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_int32, ctypes.c_float,
                                 c_void_p]
+    lib.rsft_stage2_static.argtypes = [c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_int64, c_void_p,
+                                       c_void_p]
     lib.rsft_status_string.argtypes = [c_int32]
     lib.rsft_status_string.restype = c_char_p
     lib.rsft_last_error.argtypes = []
     lib.rsft_last_error.restype = c_char_p
     for name in ("rsft_plan_create", "rsft_execute", "rsft_execute_async", "rsft_execute_host",
                  "rsft_plan_get", "rsft_plan_timing", "rsft_copy_buckets", "rsft_copy_detections",
-                 "rsft_refine"):
+                 "rsft_refine", "rsft_stage2_static"):
         getattr(lib, name).restype = c_int32
     _lib = lib
     return lib
@@ -283,6 +286,14 @@ def rsft_copy_detections(plan: Plan, out, stream=None) -> None:
 def rsft_refine(plan: Plan, cube, k, freq, amp, steps, lr, stream=None) -> None:
     _check(load_library().rsft_refine(plan.handle, _ptr(cube), int(k), _ptr(freq), _ptr(amp), int(steps),
                                       ctypes.c_float(lr), _stream(stream)))
+
+
+def rsft_stage2_static(votes, n, mu, located, count, located_votes=None, capacity=None, stream=None) -> None:
+    """Second-stage compaction into caller buffers, with library-owned fixed scratch
+    (no device allocation); ``votes`` is cleared.  See include/rsft.h."""
+    cap = int(located.numel()) if capacity is None else int(capacity)
+    _check(load_library().rsft_stage2_static(_ptr(votes), int(n), int(mu), _ptr(located), _ptr(located_votes),
+                                             cap, _ptr(count), _stream(stream)))
 
 
 def rsft_status_string(status: int) -> str:

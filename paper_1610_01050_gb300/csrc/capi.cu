@@ -438,6 +438,10 @@ rsft_status run(rsft_plan* p, const void* d_cube, cudaStream_t stream, uint64_t*
 
 }  // namespace
 
+namespace rsft {
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace rsft
+
 extern "C" {
 
 void rsft_desc_init(rsft_desc* d) {

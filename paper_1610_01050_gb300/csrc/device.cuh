@@ -105,4 +105,7 @@ int64_t stage2_segments(int64_t total_n);   // 16 KiB vote segments covering N b
 
 int fold_smem_bytes(const FoldSchedule& fs, int lg);
 
+// Message returned by rsft_last_error() on this thread.
+void set_last_error(const char* msg);
+
 }  // namespace rsft

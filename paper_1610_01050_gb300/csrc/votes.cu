@@ -19,7 +19,11 @@
 // tone's pass-band offset and by the pre-window's DC gain; the estimate is
 // the median of the real parts plus j times the median of the imaginary
 // parts over loops (the estimation paragraph of §III).
+#include <mutex>
+#include <string>
+
 #include "device.cuh"
+#include "rsft.h"
 
 namespace rsft {
 namespace {
@@ -368,3 +372,92 @@ cudaError_t launch_median(const Geometry& g, const DeviceTables& t, const float2
 }
 
 }  // namespace rsft
+
+// ---------------------------------------------------------------------------
+// Second-stage compaction that allocates nothing.
+//
+// Some callers cannot allocate device memory when they run the second stage:
+// a real-time radar loop whose memory is fixed at start-up, code that must not
+// call cudaMalloc/cudaFree while other work on the device is in flight (both
+// calls can synchronise the device), or a host framework that owns every
+// allocation itself.  rsft_stage2_static serves them: it runs the same three
+// kernels as the second stage of rsft_execute (count, scan, ordered write) on
+// a vote array the caller owns, and keeps its only scratch -- the per-segment
+// hit counts and their offsets -- in the fixed array below, which every GPU
+// that loads this library holds until the process exits.
+namespace rsft {
+namespace {
+
+constexpr int64_t kStaticSegments = 16384;  // 16384 segments of 16 KiB: at most 2^28 votes per call
+constexpr size_t kStaticOffsetBytes = static_cast<size_t>(kStaticSegments + 1) * sizeof(uint64_t);
+constexpr size_t kStaticScratchBytes = kStaticOffsetBytes + static_cast<size_t>(kStaticSegments) * sizeof(uint32_t);
+
+static __device__ __align__(256) unsigned char g_stage2_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mutex;
+void* g_static_addr[256] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once per device.
+cudaError_t static_scratch(int device, void** out) {
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (device < 0 || device >= 256) return cudaErrorInvalidDevice;
+  if (!g_static_addr[device]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_stage2_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_addr[device] = ptr;
+  }
+  *out = g_static_addr[device];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace rsft
+
+extern "C" rsft_status rsft_stage2_static(uint8_t* d_votes, int64_t n, int32_t mu, uint64_t* d_located,
+                                          uint8_t* d_located_votes, int64_t capacity, int64_t* d_count,
+                                          void* stream) {
+  using namespace rsft;
+  if (!d_votes || !d_count || n <= 0 || capacity < 0 || (capacity > 0 && !d_located)) {
+    set_last_error("rsft_stage2_static: NULL pointer or non-positive size");
+    return RSFT_ERR_INVALID_ARG;
+  }
+  if (reinterpret_cast<uintptr_t>(d_votes) % 16 != 0) {
+    set_last_error("rsft_stage2_static: d_votes must be 16-byte aligned");
+    return RSFT_ERR_INVALID_ARG;
+  }
+  if (n % (16 * 1024) != 0) {
+    set_last_error("rsft_stage2_static: n must be a multiple of 16384 votes");
+    return RSFT_ERR_INVALID_ARG;
+  }
+  if (n / (16 * 1024) > kStaticSegments) {
+    set_last_error("rsft_stage2_static: n exceeds the static scratch limit of 268435456 votes");
+    return RSFT_ERR_INVALID_ARG;
+  }
+  if (mu < 0 || mu > 254) {
+    set_last_error("rsft_stage2_static: mu must be in [0, 254]");
+    return RSFT_ERR_INVALID_ARG;
+  }
+  int device = 0;
+  cudaError_t e = cudaGetDevice(&device);
+  void* scratch = nullptr;
+  if (e == cudaSuccess) e = static_scratch(device, &scratch);
+  if (e != cudaSuccess) {
+    set_last_error((std::string("rsft_stage2_static: scratch lookup: ") + cudaGetErrorString(e)).c_str());
+    return RSFT_ERR_CUDA;
+  }
+  Geometry g{};
+  g.total_n = n;
+  Workspace ws{};
+  ws.votes = reinterpret_cast<uint32_t*>(d_votes);
+  ws.segments = n / (16 * 1024);
+  ws.seg_offset = static_cast<uint64_t*>(scratch);
+  ws.seg_count = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(scratch) + kStaticOffsetBytes);
+  e = launch_stage2(g, mu, ws, d_located, d_located_votes, nullptr, capacity, d_count,
+                    static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    set_last_error((std::string("rsft_stage2_static: ") + cudaGetErrorString(e)).c_str());
+    return RSFT_ERR_CUDA;
+  }
+  return RSFT_OK;
+}

@@ -21,7 +21,7 @@ def lib():
 
 def test_exports_every_declared_symbol(lib):
     header = open(os.path.join(ROOT, "include", "rsft.h")).read()
-    declared = set(re.findall(r"\b(rsft_[a-z_]+)\s*\(", header))
+    declared = set(re.findall(r"\b(rsft_[a-z0-9_]+)\s*\(", header))
     assert declared == set(R.C_SYMBOLS)
     for name in declared:
         assert hasattr(lib, name), name
