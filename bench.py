@@ -127,14 +127,14 @@ class ClockSampler:
 
 def workload_desc(R, wl, nv, seed):
     return R.make_desc(wl.shape, wl.buckets, wl.loops, atten_db=wl.atten_db, flat_support=wl.flat_support,
-                       p_fa=wl.p_fa, k_max=wl.k_range[1], noise_var=nv, seed=seed, max_located=65536)
+                       p_fa=wl.p_fa, k_max=wl.k_design, noise_var=nv, seed=seed, max_located=1 << 20)
 
 
 def oracle_sample(wl, cube, nv, seed, loops):
     """Time the FP64 oracle (as it stands) on `loops` loops of one frame; returns seconds."""
     import oracle as O
     op = O.make_plan(wl.shape, wl.buckets, wl.loops, seed=seed, atten_db=wl.atten_db,
-                     flat_support=wl.flat_support, noise_var=nv, p_fa=wl.p_fa, k_max=wl.k_range[1])
+                     flat_support=wl.flat_support, noise_var=nv, p_fa=wl.p_fa, k_max=wl.k_design)
     sub = O.make_plan(wl.shape, wl.buckets, loops, seed=seed, atten_db=wl.atten_db,
                       flat_support=wl.flat_support, noise_var=nv, sigma=op.sigma[:loops], pfa1=op.pfa1,
                       mu=min(op.mu, loops - 1))

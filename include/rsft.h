@@ -57,6 +57,10 @@ typedef enum rsft_status {
 enum { RSFT_WIN_RECT = 0, RSFT_WIN_CHEB = 1 };       /* pre-permutation window (§III-A) */
 enum { RSFT_FLAT_IDEAL = 0, RSFT_FLAT_CHEB = 1 };    /* flat window (§IV-B)             */
 enum { RSFT_BETA_EXACT = 0, RSFT_BETA_MEAN = 1 };    /* beta(sigma_l) or beta-bar in gamma */
+/* How votes are accumulated (same result): by output rows in shared memory with the
+ * second stage fused (default), or by scattering every candidate of every detected
+ * bucket with 8-bit atomic adds into an N-byte vote array followed by a compaction. */
+enum { RSFT_VOTES_ROWS = 0, RSFT_VOTES_SCATTER = 1 };
 
 /* Warning bits reported by rsft_plan_get(RSFT_GET_WARNINGS). */
 enum { RSFT_WARN_SPARSITY_LIMIT = 1 };  /* K_max * eta_m >= B: Remark 2, RSFT cannot separate H0/H1 */
@@ -86,6 +90,7 @@ typedef struct rsft_desc {
   int32_t beta_mode;         /* RSFT_BETA_EXACT (default) or RSFT_BETA_MEAN           */
   int64_t max_located;       /* capacity of the located list (default 65536)          */
   int32_t device;            /* CUDA device ordinal; -1 = host-only plan (tables only) */
+  int32_t vote_mode;         /* RSFT_VOTES_ROWS (default) or RSFT_VOTES_SCATTER        */
 } rsft_desc;
 
 typedef struct rsft_plan rsft_plan;
@@ -168,11 +173,14 @@ enum {
   RSFT_GET_WORKSPACE_BYTES = 13, /* int64 [1] device bytes owned by the plan              */
   RSFT_GET_STAGE_MS = 14,   /* double [8]    with timing on (rsft_plan_timing): summed device
                              * milliseconds of [0] permute_window_fold, [1] bucket_fft+np_detect,
-                             * [2] vote_scatter, [3] stage2_compact, [4] median_estimate,
+                             * [2] vote_scatter (RSFT_VOTES_SCATTER only), [3] stage2_compact
+                             * or, with RSFT_VOTES_ROWS, vote_rows, [4] median_estimate,
                              * [5] whole execute; [6] executes timed; [7] kernel launches per
                              * execute (with amplitudes).  Waits for the timed executes.      */
-  RSFT_GET_FOLD_BYTES = 15  /* int64 [1]     algorithmic bytes of one execute's fold: the cube
+  RSFT_GET_FOLD_BYTES = 15, /* int64 [1]     algorithmic bytes of one execute's fold: the cube
                              * read once per loop group plus the bucket writes               */
+  RSFT_GET_FOLD_COPY = 16   /* int32 [1]     how the last fold streamed the cube: 0 one bulk copy
+                             * per row, 3 or 5 one tensor-map box per stage (rank), -1 none yet */
 };
 rsft_status rsft_plan_get(const rsft_plan* plan, int32_t what, void* out, size_t bytes);
 

@@ -31,11 +31,12 @@ RSFT_ERR_CAPACITY, RSFT_ERR_CUDA, RSFT_ERR_TIMEOUT, RSFT_ERR_DESIGN = 4, 5, 6, 7
 RSFT_WIN_RECT, RSFT_WIN_CHEB = 0, 1
 RSFT_FLAT_IDEAL, RSFT_FLAT_CHEB = 0, 1
 RSFT_BETA_EXACT, RSFT_BETA_MEAN = 0, 1
+RSFT_VOTES_ROWS, RSFT_VOTES_SCATTER = 0, 1
 RSFT_WARN_SPARSITY_LIMIT = 1
 RSFT_GET_SIGMA, RSFT_GET_SIGMA_INV, RSFT_GET_GAMMA, RSFT_GET_BETA = 1, 2, 3, 4
 RSFT_GET_MU, RSFT_GET_PFA1, RSFT_GET_ETA_M, RSFT_GET_PD_BAR = 5, 6, 7, 8
 RSFT_GET_WINDOW, RSFT_GET_FLAT, RSFT_GET_WARNINGS, RSFT_GET_SNR_DB = 9, 10, 11, 12
-RSFT_GET_WORKSPACE_BYTES, RSFT_GET_STAGE_MS, RSFT_GET_FOLD_BYTES = 13, 14, 15
+RSFT_GET_WORKSPACE_BYTES, RSFT_GET_STAGE_MS, RSFT_GET_FOLD_BYTES, RSFT_GET_FOLD_COPY = 13, 14, 15, 16
 RSFT_BUCKETS_FOLDED, RSFT_BUCKETS_SPECTRUM = 0, 1
 
 # Every C entry point declared in include/rsft.h.
@@ -56,7 +57,7 @@ class RsftDesc(ctypes.Structure):
         ("k_max", c_int32), ("eta_p", c_double), ("p_fa1_override", c_double),
         ("mu_override", c_int32), ("noise_var", c_double), ("seed", c_uint64),
         ("sigma", POINTER(c_int64)), ("beta_mode", c_int32), ("max_located", c_int64),
-        ("device", c_int32),
+        ("device", c_int32), ("vote_mode", c_int32),
     ]
 
 
@@ -181,7 +182,8 @@ def rsft_desc_init() -> RsftDesc:
 
 def make_desc(n, b, loops, *, window=RSFT_WIN_CHEB, atten_db=60.0, flat=RSFT_FLAT_CHEB, flat_support=None,
               p_fa=1e-6, p_d=0.9, k_max=8, eta_p=1.0, p_fa1=None, mu=None, noise_var=1.0, seed=0,
-              sigma=None, beta_mode=RSFT_BETA_EXACT, max_located=65536, device=0) -> RsftDesc:
+              sigma=None, beta_mode=RSFT_BETA_EXACT, max_located=65536, device=0,
+              vote_mode=RSFT_VOTES_ROWS) -> RsftDesc:
     """Descriptor from keyword arguments (sizes per dimension, powers of two)."""
     d = rsft_desc_init()
     d.ndim = len(n)
@@ -203,6 +205,7 @@ def make_desc(n, b, loops, *, window=RSFT_WIN_CHEB, atten_db=60.0, flat=RSFT_FLA
     d.beta_mode = int(beta_mode)
     d.max_located = int(max_located)
     d.device = int(device)
+    d.vote_mode = int(vote_mode)
     if sigma is not None:
         arr = np.ascontiguousarray(np.asarray(sigma, dtype=np.int64).reshape(-1))
         d._sigma_keep = arr
@@ -254,7 +257,7 @@ _GET_SHAPES = {
     RSFT_GET_PD_BAR: ("float64", "1"), RSFT_GET_WINDOW: ("float64", "sn"),
     RSFT_GET_FLAT: ("float64", "2sn"), RSFT_GET_WARNINGS: ("int32", "1"),
     RSFT_GET_SNR_DB: ("float64", "1"), RSFT_GET_WORKSPACE_BYTES: ("int64", "1"),
-    RSFT_GET_STAGE_MS: ("float64", "8"), RSFT_GET_FOLD_BYTES: ("int64", "1"),
+    RSFT_GET_STAGE_MS: ("float64", "8"), RSFT_GET_FOLD_BYTES: ("int64", "1"), RSFT_GET_FOLD_COPY: ("int32", "1"),
 }
 
 

@@ -23,6 +23,8 @@ struct rsft_plan {
   int device = -1;
   rsft::Geometry geom{};
   rsft::FoldSchedule fold{};
+  rsft::VoteRowSchedule rows{};
+  bool rows_mode = false;
   std::vector<rsft::FftPass> passes;
   rsft::DeviceTables tables{};
   rsft::Workspace ws{};
@@ -36,6 +38,9 @@ struct rsft_plan {
   bool snr_cached = false;
   double snr_db = 0.0;
   bool timing = false;
+  int fold_copy_mode = -1;          // last fold launch: 0 per-row bulk copies, 3/5 tensor box rank
+  std::vector<int> h_sinvb;                 // [L][D] sigma^{-1} mod B_d (fold kernel parameters)
+  std::vector<unsigned short> h_slots, h_xdig;
   std::vector<cudaEvent_t> event_pool;
   std::vector<std::array<cudaEvent_t, 6>> pending;  // events of timed executes not yet summed
   double stage_ms[6] = {0, 0, 0, 0, 0, 0};
@@ -117,7 +122,7 @@ bool choose_fold_schedule(const rsft::Geometry& g, rsft::FoldSchedule& out) {
       rows_pc *= g.m[e];
       classes *= g.b[e];
     }
-    const int64_t width = std::min<int64_t>(row_len, 2 * rsft::kFoldThreads);
+    const int64_t width = std::min<int64_t>(row_len, 2 * rsft::kFoldConsumers);
     if (width < row_len) {
       // a chunk must hold whole residue periods: W = w_p * prod_{e > d_in} N_e, B_{d_in} | w_p
       if (width % after != 0) continue;
@@ -125,7 +130,7 @@ bool choose_fold_schedule(const rsft::Geometry& g, rsft::FoldSchedule& out) {
     }
     if (xcount > width || xcount > 65535) continue;
     if (classes > (int64_t(1) << 30)) continue;
-    const int64_t table_cap = std::max<int64_t>(1, (64 * 1024) / (16 * lg + 4));
+    const int64_t table_cap = std::max<int64_t>(1, (64 * 1024) / (16 * lg));
     int64_t rpc = 1;
     while (rpc * 2 <= std::min(rows_pc, table_cap)) rpc *= 2;
     const int64_t row_chunks = rows_pc / rpc;
@@ -150,11 +155,61 @@ bool choose_fold_schedule(const rsft::Geometry& g, rsft::FoldSchedule& out) {
       out.rows_per_chunk = static_cast<int>(rpc);
       out.row_chunks = static_cast<int>(row_chunks);
       out.xcount = static_cast<int>(xcount);
-      out.mult = static_cast<int>(width / xcount);
       out.direct = (row_chunks * col_chunks == 1) ? 1 : 0;
     }
   }
   return found;
+}
+
+// Rows of the vote count: the fewest trailing dimensions whose product of N_d reaches a
+// useful row length, bounded by the per-warp shared-memory counters (16 KiB).
+bool choose_vote_rows(const rsft::Geometry& g, rsft::VoteRowSchedule& vs) {
+  // rows of at most 64 locations use the bit-sliced kernel: the most trailing dimensions that fit
+  {
+    int best = -1;
+    int64_t n_in = 1, b_in = 1, m_in = 1;
+    for (int d_v = g.ndim - 1; d_v >= 0; --d_v) {
+      n_in *= g.n[d_v];
+      b_in *= g.b[d_v];
+      m_in *= g.m[d_v];
+      if (n_in > 64 || b_in > 64) break;
+      best = d_v;
+      vs.d_v = d_v;
+      vs.n_in = n_in;
+      vs.b_in = static_cast<int>(b_in);
+      vs.m_in = static_cast<int>(m_in);
+    }
+    if (best >= 0 && vs.n_in >= 16) {
+      vs.small = 1;
+      vs.rows = g.total_n / vs.n_in;
+      vs.rows_per_warp = 64;
+      vs.warps = (vs.rows + vs.rows_per_warp - 1) / vs.rows_per_warp;
+      return true;
+    }
+    vs = rsft::VoteRowSchedule{};
+  }
+  for (int d_v = g.ndim - 1; d_v >= 0; --d_v) {
+    int64_t n_in = 1, b_in = 1, m_in = 1;
+    for (int e = d_v; e < g.ndim; ++e) {
+      n_in *= g.n[e];
+      b_in *= g.b[e];
+      m_in *= g.m[e];
+    }
+    if (n_in > 16384 || b_in > 1024) break;
+    vs.d_v = d_v;
+    vs.n_in = n_in;
+    vs.b_in = static_cast<int>(b_in);
+    vs.m_in = static_cast<int>(m_in);
+    if (n_in >= 64 && (d_v == 0 || n_in * g.n[d_v - 1] > 4096)) break;
+  }
+  if (vs.n_in == 0 || vs.n_in > 16384 || vs.b_in > 1024) return false;
+  vs.rows = g.total_n / vs.n_in;
+  int64_t rpw = 4096 / vs.n_in;
+  if (rpw < 1) rpw = 1;
+  if (rpw > 64) rpw = 64;
+  vs.rows_per_warp = static_cast<int>(rpw);
+  vs.warps = (vs.rows + rpw - 1) / rpw;
+  return true;
 }
 
 // Group the bucket dimensions into shared-memory FFT passes, last dimension last.
@@ -214,6 +269,9 @@ rsft_status build_device(rsft_plan* p) {
   }
   if (!choose_fold_schedule(g, p->fold))
     return fail(RSFT_ERR_UNSUPPORTED, "no fold schedule for this bucket grid (inner B_d too large)");
+  p->rows = rsft::VoteRowSchedule{};
+  p->rows_mode = h.desc.vote_mode == RSFT_VOTES_ROWS && choose_vote_rows(g, p->rows) &&
+                 static_cast<int64_t>(8) * ((p->rows.n_in + 3) / 4) * 4 <= 200 * 1024;
   if (!plan_fft_passes(g, p->passes))
     return fail(RSFT_ERR_UNSUPPORTED, "a bucket dimension is too large for the shared-memory FFT");
 
@@ -230,6 +288,14 @@ rsft_status build_device(rsft_plan* p) {
     float2* dp = nullptr;
     if ((st = upload(p, &dp, tab)) != RSFT_OK) return st;
     p->tables.wtab[d] = dp;
+    // grouped by residue class: [x][l][m] = a_{l,d}(x + B_d m), contiguous per class
+    std::vector<float2> cls(static_cast<size_t>(L) * n);
+    const int64_t bd = h.b[d], md = h.m[d];
+    for (int64_t x = 0; x < bd; ++x)
+      for (int l = 0; l < L; ++l)
+        for (int64_t m = 0; m < md; ++m) cls[(x * L + l) * md + m] = tab[l * n + x + bd * m];
+    if ((st = upload(p, &dp, cls)) != RSFT_OK) return st;
+    p->tables.wcls[d] = dp;
     // twiddles e^{-j 2 pi k / B_d}
     std::vector<float2> tw(std::max<int64_t>(1, h.b[d] / 2));
     for (int64_t k = 0; k < h.b[d] / 2; ++k)
@@ -248,6 +314,7 @@ rsft_status build_device(rsft_plan* p) {
   }
   for (int d = D; d < rsft::kMaxDim; ++d) {
     p->tables.wtab[d] = nullptr;
+    p->tables.wcls[d] = nullptr;
     p->tables.twiddle[d] = nullptr;
     p->tables.ginv[d] = nullptr;
   }
@@ -270,22 +337,60 @@ rsft_status build_device(rsft_plan* p) {
   float* fp = nullptr;
   if ((st = upload(p, &fp, gam)) != RSFT_OK) return st;
   p->tables.gamma = fp;
-  // fold residue tables: columns of a chunk grouped by inner residue, and residue digits
+  // fold epilogue tables: the partial sums left after the warp shuffle, grouped by the
+  // inner residue of their columns, and the residue digits of each inner residue
   {
-    const rsft::FoldSchedule& fs = p->fold;
-    std::vector<unsigned short> cols(fs.width), digits(static_cast<size_t>(fs.xcount) * 4, 0);
-    std::vector<int> fill(fs.xcount, 0);
-    for (int c = 0; c < fs.width; ++c) {
-      int64_t rem = c;
-      int64_t x = 0, xstride = 1;
+    rsft::FoldSchedule& fs = p->fold;
+    auto residue = [&](int64_t c) {  // inner residue index of chunk column c
+      int64_t rem = c, x = 0, xstride = 1;
       for (int d = D - 1; d >= fs.d_in; --d) {
         const int64_t sd = rem % h.n[d];
         rem /= h.n[d];
         x += (sd % h.b[d]) * xstride;
         xstride *= h.b[d];
       }
-      cols[x * fs.mult + fill[x]++] = static_cast<unsigned short>(c);
+      return x;
+    };
+    // lane bit k moves a thread by 2^(k+1) elements: a column bit or, past the chunk width, a row
+    int rmask = 0;
+    for (int k = 0; k < 5; ++k) {
+      const int pbit = k + 1;
+      bool keep = true;
+      if ((int64_t(1) << pbit) < fs.width) {
+        int acc = 0;
+        for (int d = D - 1; d >= fs.d_in; --d) {
+          const int ln = ilog2(h.n[d]);
+          if (pbit < acc + ln) {
+            keep = (pbit - acc) >= ilog2(h.b[d]);
+            break;
+          }
+          acc += ln;
+        }
+      }
+      if (keep) rmask |= 1 << k;
     }
+    int nbits = 0;
+    for (int k = 0; k < 5; ++k) nbits += (rmask >> k) & 1;
+    fs.red_mask = rmask;
+    fs.leaders = 32 >> nbits;
+    const int warps = rsft::kFoldConsumers / 32;
+    const int nslots = warps * fs.leaders * 2;
+    if (nslots % fs.xcount != 0) return fail(RSFT_ERR_UNSUPPORTED, "fold epilogue: residues not balanced");
+    fs.slots_per_x = nslots / fs.xcount;
+    std::vector<unsigned short> cols(static_cast<size_t>(nslots)), digits(static_cast<size_t>(fs.xcount) * 4, 0);
+    std::vector<int> fill(fs.xcount, 0);
+    for (int w = 0; w < warps; ++w)
+      for (int j = 0; j < fs.leaders; ++j) {
+        int lane = 0, bit = 0;
+        for (int b = 0; b < 5; ++b)
+          if (!((rmask >> b) & 1)) lane |= ((j >> bit++) & 1) << b;
+        for (int c = 0; c < 2; ++c) {
+          const int64_t elem = 2 * (32 * w + lane) + c;
+          const int64_t x = residue(elem & (fs.width - 1));
+          if (fill[x] >= fs.slots_per_x) return fail(RSFT_ERR_UNSUPPORTED, "fold epilogue: residues not balanced");
+          cols[x * fs.slots_per_x + fill[x]++] = static_cast<unsigned short>((w * fs.leaders + j) * 2 + c);
+        }
+      }
     for (int x = 0; x < fs.xcount; ++x) {
       int64_t rem = x;
       for (int d = D - 1; d >= fs.d_in; --d) {
@@ -295,9 +400,93 @@ rsft_status build_device(rsft_plan* p) {
     }
     unsigned short* up = nullptr;
     if ((st = upload(p, &up, cols)) != RSFT_OK) return st;
-    p->tables.cols_by_x = up;
+    p->tables.slots_by_x = up;
     if ((st = upload(p, &up, digits)) != RSFT_OK) return st;
     p->tables.x_digits = up;
+    p->h_slots = cols;
+    p->h_xdig = digits;
+    p->h_sinvb = sib;
+    p->tables.h_slots = p->h_slots.data();
+    p->tables.h_xdig = p->h_xdig.data();
+    p->tables.h_sinvb = p->h_sinvb.data();
+  }
+  // fold tables in FP64, rounded once: per row the product of the row dimensions' weights
+  // a_{l,d}(s_d) as (c, d - c, c + d) of w = c + jd, and per column the product of the rest
+  {
+    const rsft::FoldSchedule& fs = p->fold;
+    auto weight = [&](int l, int d, int64_t sd) {
+      return h.wbar[d][(h.sigma_inv[l * D + d] * sd) & (h.n[d] - 1)] * h.w[d][sd];
+    };
+    const int64_t R = fs.rows_per_chunk, tunits = static_cast<int64_t>(fs.classes) * fs.row_chunks;
+    std::vector<float4> ft(static_cast<size_t>(L) * tunits * R);
+    std::vector<float2> fc(static_cast<size_t>(L) * fs.col_chunks * fs.width);
+    for (int l0 = 0; l0 < L; l0 += rsft::kMaxLoopGroup) {
+      const int lg = std::min(rsft::kMaxLoopGroup, L - l0);
+      const size_t tbase = static_cast<size_t>(l0) * tunits * R;
+      for (int64_t tu = 0; tu < tunits; ++tu) {
+        const int64_t cls = tu / fs.row_chunks, rc = tu % fs.row_chunks;
+        for (int64_t r = 0; r < R; ++r) {
+          int64_t sdig[rsft::kMaxDim] = {0, 0, 0, 0};
+          int64_t rr = rc * R + r, cres = cls;
+          for (int d = fs.d_in - 1; d >= 0; --d) {
+            const int64_t md = rr % h.m[d], xd = cres % h.b[d];
+            rr /= h.m[d];
+            cres /= h.b[d];
+            sdig[d] = xd + h.b[d] * md;
+          }
+          for (int l = 0; l < lg; ++l) {
+            cplx wv(1.0, 0.0);
+            for (int d = 0; d < fs.d_in; ++d) wv *= weight(l0 + l, d, sdig[d]);
+            ft[tbase + static_cast<size_t>(tu * R + r) * lg + l] =
+                make_float4(static_cast<float>(wv.real()), static_cast<float>(wv.imag() - wv.real()),
+                            static_cast<float>(wv.real() + wv.imag()), 0.f);
+          }
+        }
+      }
+      const size_t cbase = static_cast<size_t>(l0) * fs.col_chunks * fs.width;
+      for (int cc = 0; cc < fs.col_chunks; ++cc)
+        for (int l = 0; l < lg; ++l)
+          for (int c = 0; c < fs.width; ++c) {
+            int64_t col = static_cast<int64_t>(cc) * fs.width + c;
+            cplx wv(1.0, 0.0);
+            for (int d = D - 1; d >= fs.d_in; --d) {
+              const int64_t sd = col % h.n[d];
+              col /= h.n[d];
+              wv *= weight(l0 + l, d, sd);
+            }
+            fc[cbase + (static_cast<size_t>(cc) * lg + l) * fs.width + c] = to_f2(wv);
+          }
+    }
+    float4* f4 = nullptr;
+    if ((st = upload(p, &f4, ft)) != RSFT_OK) return st;
+    p->tables.ftable = f4;
+    float2* f2p = nullptr;
+    if ((st = upload(p, &f2p, fc)) != RSFT_OK) return st;
+    p->tables.fcolw = f2p;
+  }
+  p->tables.rowmask = nullptr;
+  if (p->rows_mode && p->rows.small) {
+    // candidate masks of the inner buckets of a row: bit i_in of mask[l][b] set iff the
+    // inner candidates R(b, sigma_l^{-1}) (Def. 4, trailing dimensions) contain i_in
+    const rsft::VoteRowSchedule& vs = p->rows;
+    std::vector<uint64_t> masks(static_cast<size_t>(L) * vs.b_in, 0ull);
+    for (int l = 0; l < L; ++l)
+      for (int b = 0; b < vs.b_in; ++b)
+        for (int u = 0; u < vs.m_in; ++u) {
+          int64_t iin = 0, brem = b, urem = u, stride = 1;
+          for (int d = D - 1; d >= vs.d_v; --d) {
+            const int64_t bd = brem % h.b[d], ud = urem % h.m[d];
+            brem /= h.b[d];
+            urem /= h.m[d];
+            const int64_t id = (h.sigma_inv[l * D + d] * (bd * h.m[d] + ud)) & (h.n[d] - 1);
+            iin += id * stride;
+            stride *= h.n[d];
+          }
+          masks[static_cast<size_t>(l) * vs.b_in + b] |= 1ull << iin;
+        }
+    uint64_t* mp = nullptr;
+    if ((st = upload(p, &mp, masks)) != RSFT_OK) return st;
+    p->tables.rowmask = mp;
   }
   // workspace
   rsft::Workspace& ws = p->ws;
@@ -321,8 +510,15 @@ rsft_status build_device(rsft_plan* p) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(votes)");
   if ((st = dev_alloc(p, &ws.seg_count, static_cast<size_t>(ws.segments) * 4)) != RSFT_OK) return st;
   if ((st = dev_alloc(p, &ws.seg_offset, static_cast<size_t>(ws.segments + 1) * 8)) != RSFT_OK) return st;
-  if ((st = dev_alloc(p, &p->d_count, 8)) != RSFT_OK) return st;
-  e = cudaMallocHost(reinterpret_cast<void**>(&p->h_count), 8);
+  if (p->rows_mode) {
+    if ((st = dev_alloc(p, &ws.warp_count, static_cast<size_t>(p->rows.warps) * 4)) != RSFT_OK) return st;
+    if ((st = dev_alloc(p, &ws.warp_offset, static_cast<size_t>(p->rows.warps + 1) * 8)) != RSFT_OK) return st;
+  }
+  if ((st = dev_alloc(p, &p->d_count, 16)) != RSFT_OK) return st;
+  ws.err_flag = reinterpret_cast<int*>(p->d_count + 1);  // [1] of the count block
+  e = cudaMemset(p->d_count, 0, 16);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(flags)");
+  e = cudaMallocHost(reinterpret_cast<void**>(&p->h_count), 16);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
   e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "plan upload");
@@ -364,7 +560,7 @@ void drain_timing(rsft_plan* p) {
 
 int launches_per_execute(const rsft_plan* p) {
   const int groups = (p->geom.loops + rsft::kMaxLoopGroup - 1) / rsft::kMaxLoopGroup;
-  return groups * (p->fold.direct ? 1 : 2) + static_cast<int>(p->passes.size()) + 1 + 3 + 1;
+  return groups * (p->fold.direct ? 1 : 2) + static_cast<int>(p->passes.size()) + (p->rows_mode ? 3 : 4) + 1;
 }
 
 void release(rsft_plan* p) {
@@ -404,7 +600,7 @@ rsft_status run(rsft_plan* p, const void* d_cube, cudaStream_t stream, uint64_t*
   for (int l0 = 0; l0 < g.loops; l0 += rsft::kMaxLoopGroup) {
     const int lg = std::min(rsft::kMaxLoopGroup, g.loops - l0);
     e = rsft::launch_fold(g, p->fold, p->tables, static_cast<const float2*>(d_cube), l0, lg, ws.folded,
-                          ws.partial, stream);
+                          ws.partial, ws.err_flag, &p->fold_copy_mode, stream);
     if (e != cudaSuccess) return cuda_fail(e, "permute_window_fold");
     if (!p->fold.direct) {
       e = rsft::launch_fold_reduce(g, p->fold, p->tables, l0, lg, ws.partial, ws.folded, stream);
@@ -418,14 +614,22 @@ rsft_status run(rsft_plan* p, const void* d_cube, cudaStream_t stream, uint64_t*
     if (e != cudaSuccess) return cuda_fail(e, "bucket_fft/np_detect");
   }
   mark(2);
-  p->votes_dirty = true;
-  e = rsft::launch_vote_scatter(g, p->tables, ws.det_bits, ws.words_b, ws.votes, stream);
-  if (e != cudaSuccess) return cuda_fail(e, "vote_scatter");
-  mark(3);
-  e = rsft::launch_stage2(g, p->host.mu, ws, d_located, d_located_votes, d_votes_out, p->host.desc.max_located,
-                          d_count, stream);
-  if (e != cudaSuccess) return cuda_fail(e, "stage2_compact");
-  p->votes_dirty = false;
+  if (p->rows_mode) {
+    mark(3);
+    e = rsft::launch_vote_rows(g, p->rows, p->tables, ws.det_bits, ws.words_b, p->host.mu, ws.warp_count,
+                               ws.warp_offset, d_located, d_located_votes, d_votes_out, p->host.desc.max_located,
+                               d_count, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "vote_rows");
+  } else {
+    p->votes_dirty = true;
+    e = rsft::launch_vote_scatter(g, p->tables, ws.det_bits, ws.words_b, ws.votes, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "vote_scatter");
+    mark(3);
+    e = rsft::launch_stage2(g, p->host.mu, ws, d_located, d_located_votes, d_votes_out, p->host.desc.max_located,
+                            d_count, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stage2_compact");
+    p->votes_dirty = false;
+  }
   mark(4);
   if (d_amp && p->host.desc.max_located > 0) {
     e = rsft::launch_median(g, p->tables, ws.spectrum, d_located, d_count, p->host.desc.max_located, d_amp, stream);
@@ -469,6 +673,7 @@ void rsft_desc_init(rsft_desc* d) {
   d->beta_mode = RSFT_BETA_EXACT;
   d->max_located = 65536;
   d->device = 0;
+  d->vote_mode = RSFT_VOTES_ROWS;
 }
 
 rsft_status rsft_plan_create(const rsft_desc* desc, rsft_plan** plan) {
@@ -535,10 +740,14 @@ rsft_status rsft_execute(rsft_plan* plan, const void* d_cube, void* stream, uint
   if (st != RSFT_OK) return st;
   DeviceGuard guard(plan->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpyAsync(plan->h_count, plan->d_count, 8, cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaMemcpyAsync(plan->h_count, plan->d_count, 16, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "rsft_execute");
   *n_located = *plan->h_count;
+  if (reinterpret_cast<const int*>(plan->h_count + 1)[0] != 0) {
+    cudaMemsetAsync(plan->ws.err_flag, 0, sizeof(int), s);
+    return fail(RSFT_ERR_TIMEOUT, "a bounded device wait gave up (results invalid)");
+  }
   if (*n_located > plan->host.desc.max_located)
     return fail(RSFT_ERR_CAPACITY, "located list truncated to max_located");
   return RSFT_OK;
@@ -566,9 +775,13 @@ rsft_status rsft_execute_host(rsft_plan* plan, const void* h_cube, void* stream,
   st = run(plan, plan->staging, s, plan->d_loc_stage, nullptr, h_amp ? plan->d_amp_stage : nullptr, nullptr,
            plan->d_count);
   if (st != RSFT_OK) return st;
-  e = cudaMemcpyAsync(plan->h_count, plan->d_count, 8, cudaMemcpyDeviceToHost, s);
+  e = cudaMemcpyAsync(plan->h_count, plan->d_count, 16, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "rsft_execute_host");
+  if (reinterpret_cast<const int*>(plan->h_count + 1)[0] != 0) {
+    cudaMemsetAsync(plan->ws.err_flag, 0, sizeof(int), s);
+    return fail(RSFT_ERR_TIMEOUT, "a bounded device wait gave up (results invalid)");
+  }
   const int64_t cnt = *plan->h_count;
   const int64_t ncopy = std::min(cnt, cap);
   if (ncopy > 0) {
@@ -674,6 +887,10 @@ rsft_status rsft_plan_get(const rsft_plan* plan, int32_t what, void* out, size_t
       o[7] = mp->has_device ? static_cast<double>(launches_per_execute(mp)) : 0.0;
       return RSFT_OK;
     }
+    case RSFT_GET_FOLD_COPY:
+      if (!need(4)) break;
+      *static_cast<int32_t*>(out) = plan->fold_copy_mode;
+      return RSFT_OK;
     case RSFT_GET_FOLD_BYTES: {
       if (!need(8)) break;
       const int groups = (L + rsft::kMaxLoopGroup - 1) / rsft::kMaxLoopGroup;

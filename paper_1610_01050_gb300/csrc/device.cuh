@@ -8,7 +8,7 @@ namespace rsft {
 
 constexpr int kMaxDim = 4;
 constexpr int kMaxLoopGroup = 16;    // loops folded per pass over the cube
-constexpr int kFoldThreads = 256;    // threads per fold CTA (two elements each per row step)
+constexpr int kFoldConsumers = 256;  // fold consumer threads per CTA (two columns each)
 
 // Sizes of the cube and the bucket grid, in the form the kernels index with.
 struct Geometry {
@@ -39,9 +39,10 @@ struct FoldSchedule {
   int rows_per_chunk;
   int row_chunks;
   int xcount;             // X: inner residues per chunk = prod_{e >= d_in} B_e
-  int mult;               // columns per residue in a chunk = W / X
-  int smem_bytes;         // dynamic shared memory of one fold CTA (per loop-group size)
   int direct;             // 1: one chunk per class, write buckets directly
+  int red_mask;           // lane bits whose flip keeps a thread's column residues (shuffle-summed)
+  int leaders;            // lanes per warp left after the shuffle sum: 32 >> popcount(red_mask)
+  int slots_per_x;        // epilogue partial sums per residue: 2 * warps * leaders / X
 };
 
 // One FFT pass over the bucket arrays: transforms dimensions [da, db) in shared memory.
@@ -56,17 +57,37 @@ struct FftPass {
   int last;               // final pass: writes the spectrum and the detections
 };
 
+// Row-organised vote counting: trailing dimensions [d_v, D) form a row of n_in
+// locations whose buckets lie in one plane of b_in buckets per loop.
+struct VoteRowSchedule {
+  int d_v;
+  int64_t n_in;        // prod_{e >= d_v} N_e
+  int b_in;            // prod_{e >= d_v} B_e
+  int m_in;            // prod_{e >= d_v} M_e
+  int64_t rows;        // N / n_in
+  int rows_per_warp;
+  int64_t warps;       // ceil(rows / rows_per_warp)
+  int small;           // rows of <= 64 locations: bit-sliced lane-per-row counting
+};
+
 // Device pointers and tables owned by a plan.
 struct DeviceTables {
   const float2* wtab[kMaxDim];   // [L][N_d]: w-bar_d(sigma^{-1} s mod N_d) * w_d(s)
+  const float2* wcls[kMaxDim];   // [B_d][L][M_d]: the same weights grouped by residue x = s mod B_d
   const int* sigma;              // [L][D]
   const int* sigma_inv;          // [L][D] mod N_d
   const int* sigma_inv_b;        // [L][D] sigma^{-1} mod B_d
   const float* gamma;            // [L]
   const float2* twiddle[kMaxDim];// [B_d / 2]: e^{-j 2 pi k / B_d}
   const float2* ginv[kMaxDim];   // [M_d]: 1 / G_d(-v) (dimension 0 also holds 1 / sum w)
-  const unsigned short* cols_by_x;  // [W]: chunk columns grouped by inner residue
+  const unsigned short* slots_by_x; // [X][slots_per_x]: epilogue partial sums of each residue
+  const float4* ftable;          // fold row table [loop group][class][row chunk][row][lg]: (c, d-c, c+d, 0)
+  const float2* fcolw;           // fold column weights [loop group][col chunk][lg][W]
+  const int* h_sinvb;            // host copies of small tables passed as kernel parameters
+  const unsigned short* h_slots;
+  const unsigned short* h_xdig;
   const unsigned short* x_digits;   // [X][4]: inner residue digit per inner dimension
+  const uint64_t* rowmask;          // [L][b_in]: candidate mask of each inner bucket (rows <= 64)
 };
 
 struct Workspace {
@@ -78,6 +99,9 @@ struct Workspace {
   uint32_t* votes;       // [ceil(N / 16) * 4] packed 8-bit votes
   uint32_t* seg_count;   // [segments] stage-2 hits per segment
   uint64_t* seg_offset;  // [segments + 1] exclusive scan of seg_count; last = total
+  int* err_flag;         // set by a bounded device wait that gave up
+  uint32_t* warp_count;  // [row warps] vote_rows hits per warp
+  uint64_t* warp_offset; // [row warps + 1]
   int64_t words_b;
   int64_t segments;
   int64_t vote_words;
@@ -85,8 +109,8 @@ struct Workspace {
 
 // Launchers (return cudaSuccess or the launch error).
 cudaError_t launch_fold(const Geometry& g, const FoldSchedule& fs, const DeviceTables& t,
-                        const float2* cube, int loop0, int lg, float2* folded, float2* partial,
-                        cudaStream_t stream);
+                        const float2* cube, int loop0, int lg, float2* folded, float2* partial, int* err,
+                        int* copy_mode, cudaStream_t stream);
 cudaError_t launch_fold_reduce(const Geometry& g, const FoldSchedule& fs, const DeviceTables& t,
                                int loop0, int lg, const float2* partial, float2* folded,
                                cudaStream_t stream);
@@ -102,8 +126,12 @@ cudaError_t launch_median(const Geometry& g, const DeviceTables& t, const float2
                           const uint64_t* located, const int64_t* d_count, int64_t capacity,
                           float2* amp, cudaStream_t stream);
 int64_t stage2_segments(int64_t total_n);   // 16 KiB vote segments covering N bytes
+cudaError_t launch_vote_rows(const Geometry& g, const VoteRowSchedule& vs, const DeviceTables& t,
+                             const uint32_t* det_bits, int64_t words_b, int mu, uint32_t* warp_count,
+                             uint64_t* warp_offset, uint64_t* located, uint8_t* located_votes,
+                             uint8_t* votes_out, int64_t capacity, int64_t* d_count, cudaStream_t stream);
 
-int fold_smem_bytes(const FoldSchedule& fs, int lg);
+int fold_smem_bytes(const Geometry& g, const FoldSchedule& fs, int lg);
 
 // Message returned by rsft_last_error() on this thread.
 void set_last_error(const char* msg);

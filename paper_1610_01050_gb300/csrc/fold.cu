@@ -11,13 +11,25 @@
 // the permutation only selects the weight and relabels the B outputs.
 //
 // Work split (FoldSchedule): dimensions [0, d_in) index rows, [d_in, D) columns.
-// A CTA owns one residue class of the row dimensions, a chunk of that class's
-// rows, and a chunk of W columns; each thread keeps two fixed adjacent columns
-// and walks the rows, so its column weights factor out of the row loop:
+// A unit is one residue class of the row dimensions, a chunk of that class's
+// rows and a chunk of W columns.  Each consumer thread keeps two fixed adjacent
+// columns and walks the rows, so its column weights factor out of the row loop:
 //     acc_l(c) = sum_rows a_l^{row}(row) r(row, c),   contribution a_l^{col}(c) acc_l(c).
-// Row weights for all loops of the group sit in shared memory as
-// (re, re, -im, im) so one complex multiply-add is two packed FP32x2 FMAs.
-// Sums over threads use a fixed order (deterministic results).
+// A complex multiply-add w x r (w = c + jd, r = a + jb) is done with three real
+// multiply-adds, K1 += c (a + b), K2 += (d - c) a, K3 += (c + d) b, and
+// Re = K1 - K3, Im = K1 + K2 at the end; the row table holds (c, d - c, c + d).
+//
+// One CTA per unit, two or more CTAs per SM.  At its start a CTA requests the
+// unit's rows with TMA -- one tensor-map box per stage of a shared-memory ring
+// (the strided rows of a residue class form one box), or one 1-D bulk copy per
+// row when rows are long -- and builds the unit's row table while the copies
+// fly; mbarriers signal each stage.  The epilogue applies the column weights,
+// sums threads of equal residue with warp shuffles over the lane bits that do
+// not change the residue, then across warps in a fixed order (deterministic
+// results).  Every barrier wait is bounded in time; a wait that gives up sets
+// the plan's error flag and the CTA skips its remaining work.
+#include <cuda.h>
+
 #include "device.cuh"
 
 namespace rsft {
@@ -42,175 +54,360 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
   return d;
 }
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// L2 policies: the cube streams through once per frame (evict first); the fold tables
+// are read by every frame (evict last).
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// 1-D bulk copy global -> shared, completion counted on `bar` (bytes: multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
+}
+
+// Tiled tensor copy global -> shared of one box (rank 3 or 5), completion counted on `bar`.
+__device__ __forceinline__ void tensor_g2s_3d(void* dst, const void* tmap, int c0, int c1, int c2, uint64_t* bar,
+                                              uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
+}
+
+__device__ __forceinline__ void tensor_g2s_5d(void* dst, const void* tmap, int c0, int c1, int c2, int c3, int c4,
+                                              uint64_t* bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, %3, %4, %5, %6}], [%7], %8;" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar)),
+      "l"(pol)
+      : "memory");
+}
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // a barrier wait gives up after 2 s
+
+// Wait until the barrier completes the phase of the given parity.  False if the CTA
+// already gave up, or if this wait times out (then the CTA's abort flag and the global
+// error flag are set).
+__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (true) {
+    if (*abort_flag) return false;
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitLimitNs) {
+      *abort_flag = 1;
+      atomicExch(err, 1);
+      return false;
+    }
+    __nanosleep(100);
+  }
+}
+
+constexpr int kThreads = kFoldConsumers;   // 256 threads, two columns each
+constexpr int kRing = 8;                   // shared-memory stages
+constexpr int kStepsPerStage = 2;          // row steps (2 * threads elements each) per stage
+constexpr int kStageElems = kStepsPerStage * 2 * kThreads;
+constexpr int kStageBytes = kStageElems * 8;
+
 struct FoldArgs {
-  const float4* cube;
+  CUtensorMap tmap;       // rows of a residue class as one box (tensor mode)
+  int tensor_rank;        // 0: one 1-D bulk copy per row; 3 or 5: one tensor copy per stage
+  const float2* cube;
   Geometry g;
   FoldSchedule fs;
-  DeviceTables t;
   int loop0;
+  int lg;
   int log_width;
   float2* folded;
   float2* partial;
+  int* err;
+  const float4* table;    // this loop group's row table: [class][row chunk][row][lg] (c, d - c, c + d, 0)
+  const float2* colw;     // this loop group's column weights: [col chunk][lg][W]
+  int small_colw;         // column weights staged in shared memory
+  int table_off, colw_off, red_off, bar_off;  // shared-memory layout (bytes)
+  int sinvb[kMaxLoopGroup * kMaxDim];        // sigma^{-1} mod B_d of the group's loops
+  unsigned short slots[512];                  // [X][slots_per_x] epilogue partial sums per residue
+  unsigned short xdig[2048];                  // [X][4] inner residue digits
 };
 
-constexpr int kUnroll = 4;
+// Column weights are kept per column in shared memory when they fit in 16 KiB.
+__host__ __device__ __forceinline__ bool colw_in_smem(const FoldSchedule& fs, int lg) {
+  return lg * fs.width * 8 <= 16 * 1024;
+}
+
+__host__ __device__ __forceinline__ int fold_layout(const FoldSchedule& fs, int lg, int* table_off, int* colw_off,
+                                                    int* red_off, int* bar_off) {
+  int off = kRing * kStageBytes;
+  *table_off = off;
+  off += fs.rows_per_chunk * lg * 16;
+  *colw_off = off;
+  if (colw_in_smem(fs, lg)) off += lg * fs.width * 8;
+  *red_off = off;
+  off += (kThreads / 32) * fs.leaders * 2 * lg * 8;
+  *bar_off = off;
+  off += (kRing + 1) * 8 + 16;
+  return off;
+}
 
 template <int LG>
-__global__ void __launch_bounds__(kFoldThreads, 2) fold_kernel(const FoldArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant__ FoldArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
   const Geometry& g = a.g;
   const FoldSchedule& fs = a.fs;
   const int tid = threadIdx.x;
-  const int chunks = fs.row_chunks * fs.col_chunks;
-  const int cc = blockIdx.x % fs.col_chunks;
-  const int rc = (blockIdx.x / fs.col_chunks) % fs.row_chunks;
-  const int cls = blockIdx.x / chunks;
+  const int warp = tid >> 5, lane = tid & 31;
   const int R = fs.rows_per_chunk;
+  const int W = fs.width;
+  const int RS = (2 * kThreads) >> a.log_width;             // rows per row step
+  const int rows_per_step = R < RS ? R : RS;                 // valid rows in a step
+  const int steps = R < RS ? 1 : R / RS;                     // row steps per unit
+  const int spst = steps < kStepsPerStage ? steps : kStepsPerStage;
+  const int nst = steps / spst;                              // stages per unit
+  const int chunks = fs.row_chunks * fs.col_chunks;
+  const int u = blockIdx.x;
+  const int cc = u % fs.col_chunks;
+  const int rc = (u / fs.col_chunks) % fs.row_chunks;
+  const int cls = u / chunks;
 
-  // residues of the row dimensions for this class (row-major over [0, d_in))
-  int xo[kMaxDim];
-  {
-    int c = cls;
-#pragma unroll
-    for (int e = kMaxDim - 1; e >= 0; --e) {
-      xo[e] = 0;
-      if (e < fs.d_in) {
-        xo[e] = c & static_cast<int>(g.b[e] - 1);
-        c >>= g.log_b[e];
-      }
-    }
-  }
+  float2* ring = reinterpret_cast<float2*>(smem);
+  float4* table = reinterpret_cast<float4*>(smem + a.table_off);
+  float2* colw = reinterpret_cast<float2*>(smem + a.colw_off);
+  float2* red = reinterpret_cast<float2*>(smem + a.red_off);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + a.bar_off);
+  uint64_t* tbar = full + kRing;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tbar + 1);
 
-  // ---- row table: global row index and (re, re, -im, im) row weight per loop
-  float4* wrow = reinterpret_cast<float4*>(smem);
-  uint32_t* rowidx = reinterpret_cast<uint32_t*>(smem + static_cast<size_t>(R) * LG * sizeof(float4));
-  for (int e = tid; e < R * LG; e += kFoldThreads) {
-    const int rl = e / LG;
-    const int l = e - rl * LG;
-    int r = rc * R + rl;
-    float2 w = make_float2(1.f, 0.f);
-    uint32_t row = 0, stride = 1;
-#pragma unroll
-    for (int d = kMaxDim - 1; d >= 0; --d) {
-      if (d < fs.d_in) {
-        const int mdig = r & static_cast<int>(g.m[d] - 1);
-        r >>= g.log_m[d];
-        const uint32_t s = static_cast<uint32_t>(xo[d]) + (static_cast<uint32_t>(mdig) << g.log_b[d]);
-        row += s * stride;
-        stride *= static_cast<uint32_t>(g.n[d]);
-        w = cmul(w, __ldg(a.t.wtab[d] + static_cast<int64_t>(a.loop0 + l) * g.n[d] + s));
-      }
-    }
-    wrow[e] = make_float4(w.x, w.x, -w.y, w.y);
-    if (l == 0) rowidx[rl] = row;
+  if (tid == 0) {
+    for (int i = 0; i < kRing + 1; ++i) mbar_init(full + i, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
 
-  // ---- stream the rows: each thread holds columns cp, cp + 1 of the chunk
-  const int W = fs.width;
+  const uint64_t pol_stream = policy_evict_first();
+  // Stage k of the unit into slot k % kRing (warp 0).
+  auto issue_stage = [&](int k) {
+    const int slot = k % kRing;
+    const int s0 = k * spst;
+    const int nrows = spst * rows_per_step;
+    if (lane == 0) mbar_arrive_expect_tx(full + slot, static_cast<uint32_t>(nrows * W * 8));
+    __syncwarp();
+    float2* dst = ring + slot * kStageElems;
+    if (a.tensor_rank != 0) {
+      if (lane == 0) {
+        const int r0 = rc * R + s0 * RS;
+        if (a.tensor_rank == 3) {
+          tensor_g2s_3d(dst, &a.tmap, cc * W, cls & static_cast<int>(g.b[0] - 1), r0, full + slot, pol_stream);
+        } else {
+          const int x1 = cls & static_cast<int>(g.b[1] - 1);
+          const int x0 = (cls >> g.log_b[1]) & static_cast<int>(g.b[0] - 1);
+          tensor_g2s_5d(dst, &a.tmap, cc * W, x1, r0 & static_cast<int>(g.m[1] - 1), x0, r0 >> g.log_m[1],
+                        full + slot, pol_stream);
+        }
+      }
+    } else {
+      for (int j = lane; j < nrows; j += 32) {
+        const int step = j / rows_per_step;
+        const int ro = j - step * rows_per_step;
+        int r = rc * R + (s0 + step) * RS + ro, c = cls;
+        int64_t row = 0, stride = 1;
+#pragma unroll
+        for (int d = kMaxDim - 1; d >= 0; --d) {
+          if (d < fs.d_in) {
+            const int xd = c & static_cast<int>(g.b[d] - 1);
+            c >>= g.log_b[d];
+            const int md = r & static_cast<int>(g.m[d] - 1);
+            r >>= g.log_m[d];
+            row += static_cast<int64_t>(xd + (md << g.log_b[d])) * stride;
+            stride *= g.n[d];
+          }
+        }
+        bulk_g2s(dst + step * (2 * kThreads) + ro * W, a.cube + row * fs.row_len + static_cast<int64_t>(cc) * W,
+                 static_cast<uint32_t>(W * 8), full + slot, pol_stream);
+      }
+    }
+  };
+  const bool small_colw = a.small_colw != 0;
+  if (warp == 0) {
+    // the unit's row table and (small) column weights, kept in L2 across frames
+    if (lane == 0) {
+      const uint64_t pol_keep = policy_evict_last();
+      const uint32_t tbytes = static_cast<uint32_t>(R * LG * 16);
+      const uint32_t cbytes = small_colw ? static_cast<uint32_t>(LG * W * 8) : 0u;
+      mbar_arrive_expect_tx(tbar, tbytes + cbytes);
+      bulk_g2s(table, a.table + static_cast<int64_t>(cls * fs.row_chunks + rc) * R * LG, tbytes, tbar, pol_keep);
+      if (small_colw) bulk_g2s(colw, a.colw + static_cast<int64_t>(cc) * LG * W, cbytes, tbar, pol_keep);
+    }
+    __syncwarp();
+    const int first = nst < kRing ? nst : kRing;
+    for (int k = 0; k < first; ++k) issue_stage(k);
+  }
+
+  // ---- stream the stages: each thread holds columns cp, cp + 1 of rows ro, ro + RS, ...
   const int cp = (2 * tid) & (W - 1);
   const int ro = (2 * tid) >> a.log_width;
-  const int RS = (2 * kFoldThreads) >> a.log_width;
-  const int64_t col = static_cast<int64_t>(cc) * W + cp;
-  unsigned long long acc0[LG], acc1[LG];
+  const bool active = ro < rows_per_step;
+  unsigned long long k12a[LG], k12b[LG];
+  float k3a[LG], k3b[LG];
 #pragma unroll
   for (int l = 0; l < LG; ++l) {
-    acc0[l] = 0ull;
-    acc1[l] = 0ull;
+    k12a[l] = 0ull;
+    k12b[l] = 0ull;
+    k3a[l] = 0.f;
+    k3b[l] = 0.f;
   }
-  for (int rl = ro; rl < R; rl += RS * kUnroll) {
-    float4 v[kUnroll];
-    int rr[kUnroll];
+  bool ok = mbar_wait(tbar, 0u, abort_flag, a.err);
+  const float4* ring4 = reinterpret_cast<const float4*>(ring);
+  for (int k = 0; k < nst; ++k) {
+    const int slot = k % kRing;
+    if (ok && !mbar_wait(full + slot, static_cast<uint32_t>(k / kRing) & 1u, abort_flag, a.err)) ok = false;
+    if (ok && active) {
+      const float4* src = ring4 + slot * (kStageElems / 2) + tid;
+      const float4* tr = table + (k * spst * RS + ro) * LG;
+      for (int step = 0; step < spst; ++step) {
+        const float4 v = src[step * kThreads];
+        const unsigned long long d0 = pack2(v.x + v.y, v.x);
+        const unsigned long long d1 = pack2(v.z + v.w, v.z);
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int r2 = rl + u * RS;
-      rr[u] = r2 < R ? r2 : 0;
-      if (r2 < R) {
-        const int64_t off = static_cast<int64_t>(rowidx[r2]) * fs.row_len + col;
-        v[u] = __ldcs(a.cube + (off >> 1));
-      } else {
-        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int l = 0; l < LG; ++l) {
+          const float4 w = tr[l];
+          const unsigned long long cw = pack2(w.x, w.y);
+          k12a[l] = fma2(cw, d0, k12a[l]);
+          k3a[l] = fmaf(w.z, v.y, k3a[l]);
+          k12b[l] = fma2(cw, d1, k12b[l]);
+          k3b[l] = fmaf(w.z, v.w, k3b[l]);
+        }
+        tr += RS * LG;
       }
     }
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const unsigned long long d0 = pack2(v[u].x, v[u].y), d0s = pack2(v[u].y, v[u].x);
-      const unsigned long long d1 = pack2(v[u].z, v[u].w), d1s = pack2(v[u].w, v[u].z);
-      const float4* wr = wrow + rr[u] * LG;
-#pragma unroll
-      for (int l = 0; l < LG; ++l) {
-        const float4 w = wr[l];
-        const unsigned long long wa = pack2(w.x, w.y), wb = pack2(w.z, w.w);
-        acc0[l] = fma2(wa, d0, acc0[l]);
-        acc0[l] = fma2(wb, d0s, acc0[l]);
-        acc1[l] = fma2(wa, d1, acc1[l]);
-        acc1[l] = fma2(wb, d1s, acc1[l]);
-      }
+    if (k + kRing < nst) {
+      __syncthreads();  // every thread is done with the slot
+      if (warp == 0) issue_stage(k + kRing);
     }
   }
-  __syncthreads();  // the row table is dead; its space now holds per-thread sums
 
-  // ---- column weights, then a fixed-order reduction over threads of equal residue
-  float2* S = reinterpret_cast<float2*>(smem);  // [LG][2 * threads]
+  // ---- epilogue: column weights, shuffle over residue-preserving lane bits, then across warps
+  const int nl = fs.leaders;
+  const unsigned rmask = static_cast<unsigned>(fs.red_mask);
+  const bool leader = (lane & rmask) == 0;
+  int lj = 0;  // index of this leader among the warp's leaders (lane bits outside rmask, compressed)
   {
-    int s0[kMaxDim];
-    int64_t c = col;
+    int bit = 0;
 #pragma unroll
-    for (int d = kMaxDim - 1; d >= 0; --d) {
-      s0[d] = 0;
-      if (d >= fs.d_in && d < g.ndim) {
-        s0[d] = static_cast<int>(c & (g.n[d] - 1));
-        c >>= g.log_n[d];
+    for (int b = 0; b < 5; ++b)
+      if (!((rmask >> b) & 1u)) {
+        lj |= ((lane >> b) & 1) << bit;
+        ++bit;
+      }
+  }
+  const float2* cw_g = a.colw + static_cast<int64_t>(cc) * LG * W;
+#pragma unroll
+  for (int l = 0; l < LG; ++l) {
+    const float2 pa = unpack2(k12a[l]), pb = unpack2(k12b[l]);
+    float2 v0 = make_float2(pa.x - k3a[l], pa.x + pa.y);
+    float2 v1 = make_float2(pb.x - k3b[l], pb.x + pb.y);
+    const float2 w0 = small_colw ? colw[l * W + cp] : __ldg(cw_g + l * W + cp);
+    const float2 w1 = small_colw ? colw[l * W + cp + 1] : __ldg(cw_g + l * W + cp + 1);
+    v0 = (ok && active) ? cmul(w0, v0) : make_float2(0.f, 0.f);
+    v1 = (ok && active) ? cmul(w1, v1) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+      if ((rmask >> b) & 1u) {
+        v0.x += __shfl_xor_sync(0xffffffffu, v0.x, 1 << b);
+        v0.y += __shfl_xor_sync(0xffffffffu, v0.y, 1 << b);
+        v1.x += __shfl_xor_sync(0xffffffffu, v1.x, 1 << b);
+        v1.y += __shfl_xor_sync(0xffffffffu, v1.y, 1 << b);
       }
     }
-    const int last = g.ndim - 1;
-#pragma unroll
-    for (int l = 0; l < LG; ++l) {
-      float2 w0 = make_float2(1.f, 0.f), w1;
-#pragma unroll
-      for (int d = 0; d < kMaxDim; ++d) {
-        if (d >= fs.d_in && d < last) w0 = cmul(w0, __ldg(a.t.wtab[d] + static_cast<int64_t>(a.loop0 + l) * g.n[d] + s0[d]));
-      }
-      const float2* wl = a.t.wtab[last] + static_cast<int64_t>(a.loop0 + l) * g.n[last];
-      w1 = cmul(w0, __ldg(wl + s0[last] + 1));
-      w0 = cmul(w0, __ldg(wl + s0[last]));
-      S[l * 2 * kFoldThreads + 2 * tid] = cmul(w0, unpack2(acc0[l]));
-      S[l * 2 * kFoldThreads + 2 * tid + 1] = cmul(w1, unpack2(acc1[l]));
+    if (leader) {
+      const int slot = (warp * nl + lj) * 2;
+      red[slot * LG + l] = v0;
+      red[(slot + 1) * LG + l] = v1;
     }
   }
   __syncthreads();
 
   const int X = fs.xcount;
-  for (int o = tid; o < LG * X; o += kFoldThreads) {
+  const int per = fs.slots_per_x;
+  for (int o = tid; o < LG * X; o += kThreads) {
     const int l = o / X;
     const int x = o - l * X;
     float2 sum = make_float2(0.f, 0.f);
-    const float2* Sl = S + l * 2 * kFoldThreads;
-    for (int k = 0; k < fs.mult; ++k) {
-      const int c = a.t.cols_by_x[x * fs.mult + k];
-      for (int r = 0; r < RS; ++r) {
-        const float2 v = Sl[r * W + c];
-        sum.x += v.x;
-        sum.y += v.y;
-      }
+    for (int k = 0; k < per; ++k) {
+      const float2 v = red[static_cast<int>(a.slots[x * per + k]) * LG + l];
+      sum.x += v.x;
+      sum.y += v.y;
     }
     if (fs.direct) {
       // bucket j = sigma^{-1} x mod B per dimension (paper order)
-      const int lg = a.loop0 + l;
       int64_t j = 0;
+      int cres = cls;
+      int xo[kMaxDim];
+#pragma unroll
+      for (int d = kMaxDim - 1; d >= 0; --d) {
+        xo[d] = 0;
+        if (d < fs.d_in) {
+          xo[d] = cres & static_cast<int>(g.b[d] - 1);
+          cres >>= g.log_b[d];
+        }
+      }
 #pragma unroll
       for (int d = 0; d < kMaxDim; ++d) {
         if (d < g.ndim) {
-          const int xd = d < fs.d_in ? xo[d] : a.t.x_digits[x * 4 + (d - fs.d_in)];
-          const int jd = (a.t.sigma_inv_b[lg * g.ndim + d] * xd) & static_cast<int>(g.b[d] - 1);
+          const int xd = d < fs.d_in ? xo[d] : static_cast<int>(a.xdig[x * 4 + (d - fs.d_in)]);
+          const int jd = (a.sinvb[l * kMaxDim + d] * xd) & static_cast<int>(g.b[d] - 1);
           j += static_cast<int64_t>(jd) << g.b_shift[d];
         }
       }
-      a.folded[static_cast<int64_t>(lg) * g.total_b + j] = sum;
+      a.folded[static_cast<int64_t>(a.loop0 + l) * g.total_b + j] = sum;
     } else {
       const int ch = rc * fs.col_chunks + cc;
       a.partial[((static_cast<int64_t>(l) * fs.classes + cls) * chunks + ch) * X + x] = sum;
@@ -269,62 +466,135 @@ __global__ void fold_reduce_kernel(const ReduceArgs a) {
 }
 
 template <int LG>
-cudaError_t launch_fold_lg(const FoldArgs& args, int ctas, int smem, cudaStream_t stream) {
-  // raise the dynamic shared-memory cap of this instance once per device
-  static int configured_smem[64] = {0};
+cudaError_t launch_fold_lg(const FoldArgs& args, int smem, cudaStream_t stream) {
+  static int cached_smem[64] = {0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (smem > 48 * 1024 && (dev >= 64 || smem > configured_smem[dev])) {
+  if (dev >= 64 || cached_smem[dev] != smem) {
     e = cudaFuncSetAttribute(fold_kernel<LG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    if (dev < 64) configured_smem[dev] = smem;
+    if (dev < 64) cached_smem[dev] = smem;
   }
-  fold_kernel<LG><<<ctas, kFoldThreads, smem, stream>>>(args);
+  const int units = args.fs.classes * args.fs.row_chunks * args.fs.col_chunks;
+  fold_kernel<LG><<<units, kThreads, smem, stream>>>(args);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-int fold_smem_bytes(const FoldSchedule& fs, int lg) {
-  const int table = fs.rows_per_chunk * (lg * 16 + 4);
-  const int sums = lg * 2 * kFoldThreads * 8;
-  return table > sums ? table : sums;
+int fold_smem_bytes(const Geometry& g, const FoldSchedule& fs, int lg) {
+  (void)g;
+  int a, b, c, d;
+  return fold_layout(fs, lg, &a, &b, &c, &d);
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess && ptr)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// Tensor map of the fold's row boxes: dim 0 = a row's complex elements (8-byte units),
+// then for each row dimension d (last first) its residue x_d (size B_d) and its alias
+// index m_d (size M_d), so a class's run of local rows is one box.  Returns the rank
+// (3 or 5), or 0 when the geometry needs per-row 1-D copies instead.
+int encode_fold_map(const Geometry& g, const FoldSchedule& fs, const float2* cube, CUtensorMap* map) {
+  if (fs.d_in < 1 || fs.d_in > 2 || fs.width > 256) return 0;
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return 0;
+  const int RS = (2 * kFoldConsumers) / fs.width;
+  const int rows_per_step = fs.rows_per_chunk < RS ? fs.rows_per_chunk : RS;
+  const int steps = fs.rows_per_chunk < RS ? 1 : fs.rows_per_chunk / RS;
+  const int nrows = (steps < kStepsPerStage ? steps : kStepsPerStage) * rows_per_step;
+  cuuint64_t dims[5], strides[4];
+  cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
+  dims[0] = static_cast<cuuint64_t>(fs.row_len);
+  box[0] = static_cast<cuuint32_t>(fs.width);
+  int rank = 1;
+  int64_t sd = fs.row_len;  // element stride of s_d
+  int left = nrows;
+  for (int d = fs.d_in - 1; d >= 0; --d) {
+    const int64_t md = g.m[d];
+    const int bm = static_cast<int>(left < md ? left : md);
+    if (bm > 256) return 0;
+    dims[rank] = static_cast<cuuint64_t>(g.b[d]);
+    strides[rank - 1] = static_cast<cuuint64_t>(sd * 8);
+    box[rank] = 1;
+    ++rank;
+    dims[rank] = static_cast<cuuint64_t>(md);
+    strides[rank - 1] = static_cast<cuuint64_t>(sd * g.b[d] * 8);
+    box[rank] = static_cast<cuuint32_t>(bm);
+    ++rank;
+    left /= bm;
+    sd *= g.n[d];
+  }
+  if (left != 1) return 0;
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, static_cast<cuuint32_t>(rank), const_cast<float2*>(cube), dims,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? rank : 0;
 }
 
 cudaError_t launch_fold(const Geometry& g, const FoldSchedule& fs, const DeviceTables& t,
-                        const float2* cube, int loop0, int lg, float2* folded, float2* partial,
-                        cudaStream_t stream) {
-  FoldArgs args;
-  args.cube = reinterpret_cast<const float4*>(cube);
+                        const float2* cube, int loop0, int lg, float2* folded, float2* partial, int* err,
+                        int* copy_mode, cudaStream_t stream) {
+  thread_local FoldArgs args;  // large (parameter tables); filled, then copied by the launch
+  args.tensor_rank = encode_fold_map(g, fs, cube, &args.tmap);
+  if (copy_mode) *copy_mode = args.tensor_rank;
+  args.cube = cube;
   args.g = g;
   args.fs = fs;
-  args.t = t;
   args.loop0 = loop0;
+  args.lg = lg;
   int lw = 0;
   while ((1 << lw) < fs.width) ++lw;
   args.log_width = lw;
   args.folded = folded;
   args.partial = partial;
-  const int ctas = fs.classes * fs.row_chunks * fs.col_chunks;
-  const int smem = fold_smem_bytes(fs, lg);
+  args.err = err;
+  const int64_t rows_tab = static_cast<int64_t>(fs.classes) * fs.row_chunks * fs.rows_per_chunk;
+  args.table = t.ftable + static_cast<int64_t>(loop0) * rows_tab;
+  args.colw = t.fcolw + static_cast<int64_t>(loop0) * fs.col_chunks * fs.width;
+  args.small_colw = colw_in_smem(fs, lg) ? 1 : 0;
+  for (int l = 0; l < kMaxLoopGroup; ++l)
+    for (int d = 0; d < kMaxDim; ++d)
+      args.sinvb[l * kMaxDim + d] = (l < lg && d < g.ndim) ? t.h_sinvb[(loop0 + l) * g.ndim + d] : 0;
+  const int nslots = fs.slots_per_x * fs.xcount;
+  for (int i = 0; i < nslots && i < 512; ++i) args.slots[i] = t.h_slots[i];
+  for (int i = 0; i < fs.xcount * 4 && i < 2048; ++i) args.xdig[i] = t.h_xdig[i];
+  const int smem = fold_layout(fs, lg, &args.table_off, &args.colw_off, &args.red_off, &args.bar_off);
   switch (lg) {
-    case 1: return launch_fold_lg<1>(args, ctas, smem, stream);
-    case 2: return launch_fold_lg<2>(args, ctas, smem, stream);
-    case 3: return launch_fold_lg<3>(args, ctas, smem, stream);
-    case 4: return launch_fold_lg<4>(args, ctas, smem, stream);
-    case 5: return launch_fold_lg<5>(args, ctas, smem, stream);
-    case 6: return launch_fold_lg<6>(args, ctas, smem, stream);
-    case 7: return launch_fold_lg<7>(args, ctas, smem, stream);
-    case 8: return launch_fold_lg<8>(args, ctas, smem, stream);
-    case 9: return launch_fold_lg<9>(args, ctas, smem, stream);
-    case 10: return launch_fold_lg<10>(args, ctas, smem, stream);
-    case 11: return launch_fold_lg<11>(args, ctas, smem, stream);
-    case 12: return launch_fold_lg<12>(args, ctas, smem, stream);
-    case 13: return launch_fold_lg<13>(args, ctas, smem, stream);
-    case 14: return launch_fold_lg<14>(args, ctas, smem, stream);
-    case 15: return launch_fold_lg<15>(args, ctas, smem, stream);
-    case 16: return launch_fold_lg<16>(args, ctas, smem, stream);
+    case 1: return launch_fold_lg<1>(args, smem, stream);
+    case 2: return launch_fold_lg<2>(args, smem, stream);
+    case 3: return launch_fold_lg<3>(args, smem, stream);
+    case 4: return launch_fold_lg<4>(args, smem, stream);
+    case 5: return launch_fold_lg<5>(args, smem, stream);
+    case 6: return launch_fold_lg<6>(args, smem, stream);
+    case 7: return launch_fold_lg<7>(args, smem, stream);
+    case 8: return launch_fold_lg<8>(args, smem, stream);
+    case 9: return launch_fold_lg<9>(args, smem, stream);
+    case 10: return launch_fold_lg<10>(args, smem, stream);
+    case 11: return launch_fold_lg<11>(args, smem, stream);
+    case 12: return launch_fold_lg<12>(args, smem, stream);
+    case 13: return launch_fold_lg<13>(args, smem, stream);
+    case 14: return launch_fold_lg<14>(args, smem, stream);
+    case 15: return launch_fold_lg<15>(args, smem, stream);
+    case 16: return launch_fold_lg<16>(args, smem, stream);
     default: return cudaErrorInvalidValue;
   }
 }

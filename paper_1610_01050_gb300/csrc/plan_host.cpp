@@ -244,6 +244,10 @@ rsft_status validate_desc(const rsft_desc& d, std::string& err) {
         }
       }
   }
+  if (d.vote_mode != RSFT_VOTES_ROWS && d.vote_mode != RSFT_VOTES_SCATTER) {
+    err = "unknown vote_mode";
+    return RSFT_ERR_INVALID_ARG;
+  }
   if (d.max_located < 0) {
     err = "max_located must be >= 0";
     return RSFT_ERR_INVALID_ARG;

@@ -314,6 +314,351 @@ __global__ void __launch_bounds__(kMedianWarps * 32) median_kernel(const MedianA
   }
 }
 
+// ---------------------------------------------------------------------------
+// vote_rows: the reverse mapping and accumulation of Algorithm 1 and the
+// second-stage detection, organised by output rows instead of by detected
+// buckets.  A location i gets one vote from loop l iff bucket M(i, sigma_l)
+// was detected (Def. 3 and Prop. 3: i is in R(j, sigma^{-1}) iff j = M(i,
+// sigma)), so the votes of an output row (the trailing dimensions [d_v, D) at
+// fixed leading indices) come from one plane of B_in buckets per loop.  A lane
+// first counts, per row, the loops whose plane holds any detection; a row with
+// at most mu such loops cannot pass the second stage and is skipped.  For the
+// remaining rows the warp expands the detected buckets of each loop into their
+// candidates (Def. 4) and counts votes in shared memory (candidates of one
+// loop are distinct, Prop. 4, so a loop's increments never collide), then
+// emits {i : votes > mu} in ascending order.  Pass 0 counts the hits of each
+// warp, a scan turns them into offsets, pass 1 repeats the work and writes.
+struct RowArgs {
+  Geometry g;
+  DeviceTables t;
+  const uint32_t* det_bits;
+  int64_t words_b;
+  int d_v;
+  int64_t n_in;
+  int b_in;
+  int m_in;
+  int64_t rows;
+  int rows_per_warp;
+  int64_t warps;
+  int mu;
+  uint32_t* warp_count;
+  const uint64_t* warp_offset;
+  uint64_t* located;
+  uint8_t* located_votes;
+  uint8_t* votes_out;
+  int64_t capacity;
+};
+
+constexpr int kRowWarps = 8;
+
+// First bucket index of the B_in-bucket plane that row `row` maps to in loop l.
+__device__ __forceinline__ int64_t plane_of(const RowArgs& a, int l, int64_t row) {
+  const Geometry& g = a.g;
+  int64_t kb = 0, r = row;
+#pragma unroll
+  for (int d = kMaxDim - 1; d >= 0; --d) {
+    if (d < a.d_v) {
+      const uint32_t id = static_cast<uint32_t>(r & (g.n[d] - 1));
+      r >>= g.log_n[d];
+      const uint32_t p = (static_cast<uint32_t>(a.t.sigma[l * g.ndim + d]) * id) & static_cast<uint32_t>(g.n[d] - 1);
+      kb += static_cast<int64_t>(p >> g.log_m[d]) << g.b_shift[d];
+    }
+  }
+  return kb;
+}
+
+// Detection bits [kb, kb + B_in) of loop l, word w of the plane (one word when B_in <= 32).
+// `bits` is the detection bitmap, staged in shared memory when it fits.
+__device__ __forceinline__ uint32_t plane_word(const RowArgs& a, const uint32_t* bits, int l, int64_t kb, int w) {
+  const uint32_t* b = bits + static_cast<int64_t>(l) * a.words_b;
+  if (a.b_in < 32) return (b[kb >> 5] >> (kb & 31)) & ((1u << a.b_in) - 1u);
+  return b[(kb >> 5) + w];
+}
+
+__device__ __forceinline__ bool plane_any(const RowArgs& a, const uint32_t* bits, int l, int64_t kb) {
+  const int words = a.b_in < 32 ? 1 : (a.b_in >> 5);
+  for (int w = 0; w < words; ++w)
+    if (plane_word(a, bits, l, kb, w)) return true;
+  return false;
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(kRowWarps * 32) vote_rows_kernel(const RowArgs a, int staged) {
+  extern __shared__ uint32_t smem_words[];
+  const Geometry& g = a.g;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t cwords = (a.n_in + 3) >> 2;
+  const int64_t bit_words = static_cast<int64_t>(g.loops) * a.words_b;
+  const uint32_t* bits = a.det_bits;
+  if (staged) {
+    // all L detection bitmaps, copied once per CTA (latency of shared memory instead of L2)
+    uint32_t* sb = smem_words + kRowWarps * cwords;
+    for (int64_t w = threadIdx.x; w < bit_words; w += kRowWarps * 32) sb[w] = __ldg(a.det_bits + w);
+    __syncthreads();
+    bits = sb;
+  }
+  const int64_t gw = static_cast<int64_t>(blockIdx.x) * kRowWarps + wid;
+  if (gw >= a.warps) return;  // no block-wide barriers below
+  uint32_t* cnt = smem_words + wid * cwords;
+  uint8_t* cnt8 = reinterpret_cast<uint8_t*>(cnt);
+  for (int64_t w = lane; w < cwords; w += 32) cnt[w] = 0u;
+  __syncwarp();
+  const int L = g.loops;
+  const bool full = PASS == 1 && a.votes_out != nullptr;
+  const uint32_t mu4 = static_cast<uint32_t>(a.mu) * 0x01010101u;
+  uint64_t pos = PASS == 1 ? a.warp_offset[gw] : 0ull;
+  uint32_t hits = 0;
+  const int64_t row0 = gw * a.rows_per_warp;
+  const int plane_words = a.b_in < 32 ? 1 : (a.b_in >> 5);
+  for (int rb = 0; rb < a.rows_per_warp; rb += 32) {
+    const int64_t row = row0 + rb + lane;
+    const bool valid = rb + lane < a.rows_per_warp && row < a.rows;
+    int nz = 0;
+    if (valid && !full) {
+#pragma unroll 4
+      for (int l = 0; l < L; ++l) nz += plane_any(a, bits, l, plane_of(a, l, row)) ? 1 : 0;
+    }
+    unsigned cand = __ballot_sync(0xffffffffu, valid && (full || nz > a.mu));
+    while (cand) {
+      const int src = __ffs(cand) - 1;
+      cand &= cand - 1;
+      const int64_t crow = row0 + rb + src;
+      // ---- votes of row crow
+      for (int l0 = 0; l0 < L; l0 += 32) {
+        const int l = l0 + lane;
+        int64_t kb = 0;
+        bool live = false;
+        if (l < L) {
+          kb = plane_of(a, l, crow);
+          live = plane_any(a, bits, l, kb);
+        }
+        unsigned lm = __ballot_sync(0xffffffffu, live);
+        while (lm) {
+          const int ls = __ffs(lm) - 1;
+          lm &= lm - 1;
+          const int ll = l0 + ls;
+          const int64_t kbl = __shfl_sync(0xffffffffu, kb, ls);
+          for (int pw = 0; pw < plane_words; ++pw) {
+            uint32_t word = plane_word(a, bits, ll, kbl, pw);
+            while (word) {
+              const int b = pw * 32 + __ffs(word) - 1;
+              word &= word - 1;
+              for (int u = lane; u < a.m_in; u += 32) {
+                // candidate sigma^{-1} (b_e M_e + u_e) mod N_e per trailing dimension (Def. 4)
+                int64_t iin = 0;
+                int mshift = 0;
+#pragma unroll
+                for (int d = kMaxDim - 1; d >= 0; --d) {
+                  if (d >= a.d_v && d < g.ndim) {
+                    const uint32_t bd = static_cast<uint32_t>(b >> g.b_shift[d]) & static_cast<uint32_t>(g.b[d] - 1);
+                    const uint32_t ud = static_cast<uint32_t>(u >> mshift) & static_cast<uint32_t>(g.m[d] - 1);
+                    mshift += g.log_m[d];
+                    const uint32_t id = (static_cast<uint32_t>(a.t.sigma_inv[ll * g.ndim + d]) * ((bd << g.log_m[d]) + ud)) &
+                                        static_cast<uint32_t>(g.n[d] - 1);
+                    iin += static_cast<int64_t>(id) << g.n_shift[d];
+                  }
+                }
+                cnt8[iin] = static_cast<uint8_t>(cnt8[iin] + 1);
+              }
+            }
+          }
+          __syncwarp();
+        }
+      }
+      // ---- second stage on the row: votes > mu, ascending; clear the counters
+      for (int64_t w0 = 0; w0 < cwords; w0 += 32) {
+        const int64_t w = w0 + lane;
+        const uint32_t v = w < cwords ? cnt[w] : 0u;
+        const int h = v ? (__popc(__vcmpgtu4(v, mu4)) >> 3) : 0;
+        if (PASS == 0) {
+          hits += static_cast<uint32_t>(h);
+        } else {
+          int incl = h;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+          }
+          const int tot = __shfl_sync(0xffffffffu, incl, 31);
+          uint64_t out = pos + static_cast<uint64_t>(incl - h);
+          if (h) {
+#pragma unroll
+            for (int bb = 0; bb < 4; ++bb) {
+              const uint32_t c = (v >> (8 * bb)) & 0xffu;
+              if (c > static_cast<uint32_t>(a.mu)) {
+                if (out < static_cast<uint64_t>(a.capacity)) {
+                  a.located[out] = static_cast<uint64_t>(crow * a.n_in + w * 4 + bb);
+                  if (a.located_votes) a.located_votes[out] = static_cast<uint8_t>(c);
+                }
+                ++out;
+              }
+            }
+          }
+          pos += static_cast<uint64_t>(tot);
+          if (full && w < cwords) {
+            for (int bb = 0; bb < 4 && w * 4 + bb < a.n_in; ++bb)
+              a.votes_out[crow * a.n_in + w * 4 + bb] = static_cast<uint8_t>((v >> (8 * bb)) & 0xffu);
+          }
+        }
+        if (v) cnt[w] = 0u;
+      }
+      __syncwarp();
+    }
+  }
+  if (PASS == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) hits += __shfl_xor_sync(0xffffffffu, hits, o);
+    if (lane == 0) a.warp_count[gw] = hits;
+  }
+}
+
+// vote_rows_small: rows of at most 64 locations.  A lane owns a row; the votes
+// of its 64 locations are kept as eight 64-bit bit-planes (bit p of every
+// location's count), each loop adds the mask of candidates of its detected
+// buckets (the OR of the precomputed masks R(b, sigma_l^{-1}) of the row's
+// detected inner buckets b, Def. 4) with a ripple carry, and a bit-sliced
+// comparison with mu gives the second-stage hits of all 64 locations at once.
+template <int PASS>
+__global__ void __launch_bounds__(kRowWarps * 32) vote_rows_small_kernel(const RowArgs a, const uint64_t* masks,
+                                                                         int staged) {
+  extern __shared__ uint64_t smem_small[];
+  const Geometry& g = a.g;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int L = g.loops;
+  const int64_t bit_words = static_cast<int64_t>(L) * a.words_b;
+  const int64_t mask_n = static_cast<int64_t>(L) * a.b_in;
+  const uint32_t* bits = a.det_bits;
+  const uint64_t* mk = masks;
+  // sigma of the row dimensions, [L][d_v], always staged
+  int* ssig = reinterpret_cast<int*>(smem_small);
+  for (int e = threadIdx.x; e < L * a.d_v; e += kRowWarps * 32) {
+    const int l = e / a.d_v, d = e - l * a.d_v;
+    ssig[e] = a.t.sigma[l * g.ndim + d];
+  }
+  const int sig_words = ((L * a.d_v + 1) / 2 + 1) & ~1;  // in uint64 units, kept 16-byte aligned
+  if (staged) {
+    uint64_t* sm = smem_small + sig_words;
+    uint32_t* sb = reinterpret_cast<uint32_t*>(sm + mask_n);
+    for (int64_t w = threadIdx.x; w < mask_n; w += kRowWarps * 32) sm[w] = __ldg(masks + w);
+    for (int64_t w = threadIdx.x; w < bit_words; w += kRowWarps * 32) sb[w] = __ldg(a.det_bits + w);
+    bits = sb;
+    mk = sm;
+  }
+  __syncthreads();
+  const int64_t gw = static_cast<int64_t>(blockIdx.x) * kRowWarps + wid;
+  if (gw >= a.warps) return;  // no block-wide barriers below
+  const uint64_t valid_bits = a.n_in >= 64 ? ~0ull : ((1ull << a.n_in) - 1ull);
+  uint64_t pos = PASS == 1 ? a.warp_offset[gw] : 0ull;
+  uint32_t hits = 0;
+  const int64_t row0 = gw * a.rows_per_warp;
+  const int plane_words = a.b_in <= 32 ? 1 : 2;
+  const uint32_t pat_mask = a.b_in < 32 ? ((1u << a.b_in) - 1u) : 0xffffffffu;
+  for (int rb = 0; rb < a.rows_per_warp; rb += 32) {
+    const int64_t row = row0 + rb + lane;
+    const bool valid = rb + lane < a.rows_per_warp && row < a.rows;
+    // digits of the row's leading indices, once per row
+    uint32_t id[kMaxDim];
+    {
+      uint64_t r = static_cast<uint64_t>(row);
+#pragma unroll
+      for (int d = kMaxDim - 1; d >= 0; --d) {
+        id[d] = 0u;
+        if (d < a.d_v) {
+          id[d] = static_cast<uint32_t>(r) & static_cast<uint32_t>(g.n[d] - 1);
+          r >>= g.log_n[d];
+        }
+      }
+    }
+    uint64_t c[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) c[p] = 0ull;
+    if (valid) {
+      for (int l = 0; l < L; ++l) {
+        uint32_t kb = 0u;
+        const int* sl = ssig + l * a.d_v;
+#pragma unroll
+        for (int d = 0; d < kMaxDim; ++d) {
+          if (d < a.d_v) {
+            const uint32_t p = (static_cast<uint32_t>(sl[d]) * id[d]) & static_cast<uint32_t>(g.n[d] - 1);
+            kb += (p >> g.log_m[d]) << g.b_shift[d];
+          }
+        }
+        const uint32_t* bl = bits + static_cast<int64_t>(l) * a.words_b;
+        uint64_t pat = (bl[kb >> 5] >> (kb & 31u)) & pat_mask;
+        if (plane_words == 2) pat |= static_cast<uint64_t>(bl[(kb >> 5) + 1]) << 32;
+        if (!pat) continue;
+        uint64_t m = 0ull;
+        const uint64_t* ml = mk + static_cast<int64_t>(l) * a.b_in;
+        while (pat) {
+          m |= ml[__ffsll(static_cast<long long>(pat)) - 1];
+          pat &= pat - 1;
+        }
+        uint64_t carry = m;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          const uint64_t t = c[p] & carry;
+          c[p] ^= carry;
+          carry = t;
+        }
+      }
+    }
+    // votes > mu, bit-sliced
+    uint64_t gt = 0ull, eq = ~0ull;
+#pragma unroll
+    for (int p = 7; p >= 0; --p) {
+      if ((a.mu >> p) & 1) {
+        eq &= c[p];
+      } else {
+        gt |= eq & c[p];
+        eq &= ~c[p];
+      }
+    }
+    gt &= valid ? valid_bits : 0ull;
+    const int h = __popcll(gt);
+    if (PASS == 0) {
+      hits += static_cast<uint32_t>(h);
+    } else {
+      int incl = h;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int tot = __shfl_sync(0xffffffffu, incl, 31);
+      uint64_t out = pos + static_cast<uint64_t>(incl - h);
+      uint64_t rem = gt;
+      while (rem) {
+        const int bit = __ffsll(static_cast<long long>(rem)) - 1;
+        rem &= rem - 1;
+        if (out < static_cast<uint64_t>(a.capacity)) {
+          a.located[out] = static_cast<uint64_t>(row * a.n_in + bit);
+          if (a.located_votes) {
+            uint32_t v = 0;
+#pragma unroll
+            for (int p = 0; p < 8; ++p) v |= static_cast<uint32_t>((c[p] >> bit) & 1ull) << p;
+            a.located_votes[out] = static_cast<uint8_t>(v);
+          }
+        }
+        ++out;
+      }
+      pos += static_cast<uint64_t>(tot);
+      if (a.votes_out && valid) {
+        for (int bit = 0; bit < a.n_in; ++bit) {
+          uint32_t v = 0;
+#pragma unroll
+          for (int p = 0; p < 8; ++p) v |= static_cast<uint32_t>((c[p] >> bit) & 1ull) << p;
+          a.votes_out[row * a.n_in + bit] = static_cast<uint8_t>(v);
+        }
+      }
+    }
+  }
+  if (PASS == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) hits += __shfl_xor_sync(0xffffffffu, hits, o);
+    if (lane == 0) a.warp_count[gw] = hits;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_vote_scatter(const Geometry& g, const DeviceTables& t, const uint32_t* det_bits,
@@ -350,6 +695,92 @@ cudaError_t launch_stage2(const Geometry& g, int mu, Workspace& ws, uint64_t* lo
   stage2_write_kernel<<<grid, kSegThreads, 0, stream>>>(reinterpret_cast<uint4*>(ws.votes), segs,
                                                         static_cast<uint32_t>(mu), mu4, ws.seg_offset, located,
                                                         located_votes, votes_out, g.total_n, capacity);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vote_rows(const Geometry& g, const VoteRowSchedule& vs, const DeviceTables& t,
+                             const uint32_t* det_bits, int64_t words_b, int mu, uint32_t* warp_count,
+                             uint64_t* warp_offset, uint64_t* located, uint8_t* located_votes,
+                             uint8_t* votes_out, int64_t capacity, int64_t* d_count, cudaStream_t stream) {
+  if (vs.small) {
+    RowArgs a;
+    a.g = g;
+    a.t = t;
+    a.det_bits = det_bits;
+    a.words_b = words_b;
+    a.d_v = vs.d_v;
+    a.n_in = vs.n_in;
+    a.b_in = vs.b_in;
+    a.m_in = vs.m_in;
+    a.rows = vs.rows;
+    a.rows_per_warp = vs.rows_per_warp;
+    a.warps = vs.warps;
+    a.mu = mu;
+    a.warp_count = warp_count;
+    a.warp_offset = warp_offset;
+    a.located = located;
+    a.located_votes = located_votes;
+    a.votes_out = votes_out;
+    a.capacity = capacity;
+    const unsigned blocks = static_cast<unsigned>((vs.warps + kRowWarps - 1) / kRowWarps);
+    const size_t sig_bytes = static_cast<size_t>((((g.loops * vs.d_v + 1) / 2 + 1) & ~1)) * 8;
+    const size_t need = static_cast<size_t>(g.loops) * vs.b_in * 8 + static_cast<size_t>(g.loops) * words_b * 4;
+    const int staged = need <= 112 * 1024 ? 1 : 0;
+    const size_t smem = sig_bytes + (staged ? need : 0);
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(vote_rows_small_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(smem));
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(vote_rows_small_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem));
+      if (e != cudaSuccess) return e;
+    }
+    vote_rows_small_kernel<0><<<blocks, kRowWarps * 32, smem, stream>>>(a, t.rowmask, staged);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    stage2_scan_kernel<<<1, 1024, 0, stream>>>(warp_count, vs.warps, warp_offset, d_count);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    vote_rows_small_kernel<1><<<blocks, kRowWarps * 32, smem, stream>>>(a, t.rowmask, staged);
+    return cudaGetLastError();
+  }
+  RowArgs a;
+  a.g = g;
+  a.t = t;
+  a.det_bits = det_bits;
+  a.words_b = words_b;
+  a.d_v = vs.d_v;
+  a.n_in = vs.n_in;
+  a.b_in = vs.b_in;
+  a.m_in = vs.m_in;
+  a.rows = vs.rows;
+  a.rows_per_warp = vs.rows_per_warp;
+  a.warps = vs.warps;
+  a.mu = mu;
+  a.warp_count = warp_count;
+  a.warp_offset = warp_offset;
+  a.located = located;
+  a.located_votes = located_votes;
+  a.votes_out = votes_out;
+  a.capacity = capacity;
+  const unsigned blocks = static_cast<unsigned>((vs.warps + kRowWarps - 1) / kRowWarps);
+  const size_t cnt_bytes = static_cast<size_t>(kRowWarps) * ((vs.n_in + 3) / 4) * 4;
+  const size_t bit_bytes = static_cast<size_t>(g.loops) * words_b * 4;
+  const int staged = cnt_bytes + bit_bytes <= 112 * 1024 ? 1 : 0;
+  const size_t smem = cnt_bytes + (staged ? bit_bytes : 0);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(vote_rows_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(vote_rows_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+  }
+  vote_rows_kernel<0><<<blocks, kRowWarps * 32, smem, stream>>>(a, staged);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  stage2_scan_kernel<<<1, 1024, 0, stream>>>(warp_count, vs.warps, warp_offset, d_count);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  vote_rows_kernel<1><<<blocks, kRowWarps * 32, smem, stream>>>(a, staged);
   return cudaGetLastError();
 }
 

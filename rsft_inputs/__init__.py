@@ -61,6 +61,11 @@ class Workload:
     flat_support: tuple | None = None
     noise_var: float = 1.0
     index: int = 0
+    design_k: int = 0       # sparsity budget of the threshold design (0: k_range[1])
+
+    @property
+    def k_design(self) -> int:
+        return self.design_k or self.k_range[1]
 
 
 WORKLOADS = {
@@ -70,9 +75,10 @@ WORKLOADS = {
     "c2_3d_radar": Workload("c2_3d_radar", (1024, 256, 64), (64, 32, 8), 12,
                             80.0, 1e-6, (32, 32), (5.0, 25.0), "offgrid",
                             "rayleigh", index=1),
+    # B = 128 buckets: K eta_m >= B for K = 64 (Remark 2), so the design budget is K = 8
     "c3_small": Workload("c3_small", (256, 128, 16), (16, 8, 1), 10, 60.0,
                          1e-5, (4, 64), (5.0, 25.0), "offgrid", "rayleigh",
-                         index=2),
+                         index=2, design_k=8),
     "c3_mid": Workload("c3_mid", (512, 256, 32), (32, 16, 2), 10, 60.0, 1e-5,
                        (4, 64), (5.0, 25.0), "offgrid", "rayleigh", index=2),
     "c3_large": Workload("c3_large", (1024, 256, 64), (64, 16, 4), 10, 60.0,

@@ -30,11 +30,11 @@ def _lib():
 
 
 def make_pair(n, b, loops, *, seed, atten=60.0, window="cheb", flat="cheb", support=None, noise_var=1.0,
-              pfa1=None, mu=None, p_fa=1e-6, k_max=8, max_located=65536):
+              pfa1=None, mu=None, p_fa=1e-6, k_max=8, max_located=65536, vote_mode=R.RSFT_VOTES_ROWS):
     d = R.make_desc(n, b, loops, window=R.RSFT_WIN_CHEB if window == "cheb" else R.RSFT_WIN_RECT,
                     atten_db=atten, flat=R.RSFT_FLAT_CHEB if flat == "cheb" else R.RSFT_FLAT_IDEAL,
                     flat_support=support, p_fa=p_fa, k_max=k_max, p_fa1=pfa1, mu=mu, noise_var=noise_var,
-                    seed=seed, max_located=max_located)
+                    seed=seed, max_located=max_located, vote_mode=vote_mode)
     op = O.make_plan(n, b, loops, seed=seed, window=window, atten_db=atten, flat=flat, flat_support=support,
                      noise_var=noise_var, p_fa=p_fa, k_max=k_max, pfa1=pfa1, mu=mu)
     return d, op
@@ -73,6 +73,33 @@ def test_parity_small(name, n, b, loops, extra):
     rep = compare_full(g, ref, op)
     print(f"parity {name}: {rep}")
     assert rep["detected"] > 0
+
+
+VOTE_CASES = [
+    ("3d_rows", (64, 32, 16), (8, 4, 4), 5, dict(pfa1=0.03, mu=1)),
+    ("2d_col_chunks", (64, 2048), (8, 128), 6, dict(pfa1=0.02, mu=2)),
+    ("4d_lg16", (16, 16, 8, 8), (4, 4, 2, 2), 16, dict(pfa1=0.05, mu=4)),
+    ("1d", (4096,), (64,), 3, dict(pfa1=0.05, mu=1)),
+    ("3d_b1", (32, 16, 16), (8, 4, 1), 6, dict(pfa1=0.05, mu=2)),
+]
+
+
+@pytest.mark.parametrize("name,n,b,loops,extra", VOTE_CASES, ids=[c[0] for c in VOTE_CASES])
+def test_vote_modes_agree_with_oracle(name, n, b, loops, extra):
+    """Row-organised votes and the atomic scatter give the oracle's votes and located set."""
+    seed = zlib.crc32(name.encode()) % 1000 + 7
+    nv = 1.5
+    cube, _ = tone_input(n, b, 6, seed, noise_var=nv)
+    outs = []
+    for mode in (R.RSFT_VOTES_ROWS, R.RSFT_VOTES_SCATTER):
+        d, op = make_pair(n, b, loops, seed=seed, noise_var=nv, vote_mode=mode, **extra)
+        g = gpu_run(d, cube)
+        outs.append(g)
+    ref = O.rsft(op, cube.astype(np.complex128))
+    for g in outs:
+        compare_full(g, ref, op)
+    np.testing.assert_array_equal(outs[0]["votes"], outs[1]["votes"])
+    np.testing.assert_array_equal(outs[0]["located"], outs[1]["located"])
 
 
 def test_parity_config1_workload():
@@ -173,13 +200,13 @@ def _full_oracle_case(name, frame=0):
     cube, tg, wl, nv = ri.workload_frame(name, frame)
     d, op = make_pair(wl.shape, wl.buckets, wl.loops, seed=ri.frame_seed(wl, frame), atten=wl.atten_db,
                       support=wl.flat_support, noise_var=nv, p_fa=wl.p_fa,
-                      k_max=wl.k_range[1], max_located=1 << 20)
+                      k_max=wl.k_design, max_located=1 << 20)
     g = gpu_run(d, cube)
     ref = O.rsft(op, cube.astype(np.complex128))
     return compare_full(g, ref, op), g, ref, tg, wl
 
 
-@pytest.mark.parametrize("name", ["c2_3d_radar", "c3_large", "c4_2d_4096"])
+@pytest.mark.parametrize("name", ["c2_3d_radar", "c3_small", "c3_mid", "c3_large", "c4_2d_4096"])
 def test_parity_full_workload(name):
     rep, g, ref, tg, wl = _full_oracle_case(name)
     print(f"parity {name}: {rep}")
@@ -193,7 +220,7 @@ def test_parity_c5_sampled():
     name = "c5_4d"
     cube, tg, wl, nv = ri.workload_frame(name, 0)
     d, op = make_pair(wl.shape, wl.buckets, wl.loops, seed=ri.frame_seed(wl, 0), atten=wl.atten_db,
-                      noise_var=nv, p_fa=wl.p_fa, k_max=wl.k_range[1], max_located=1 << 22)
+                      noise_var=nv, p_fa=wl.p_fa, k_max=wl.k_design, max_located=1 << 22)
     g = gpu_run(d, cube, want_votes=True)
     compare_tables(g["plan"], op)
     rng = np.random.default_rng(5)
