@@ -179,7 +179,10 @@ bool choose_vote_rows(const rsft::Geometry& g, rsft::VoteRowSchedule& vs) {
       vs.b_in = static_cast<int>(b_in);
       vs.m_in = static_cast<int>(m_in);
     }
-    if (best >= 0 && vs.n_in >= 16) {
+    // the kernel keeps a [L][N_d] bucket-offset table of each row dimension in shared memory
+    int64_t kb_words = 0;
+    for (int d = 0; best >= 0 && d < vs.d_v; ++d) kb_words += static_cast<int64_t>(g.loops) * g.n[d];
+    if (best >= 0 && vs.n_in >= 16 && kb_words <= 24576) {
       vs.small = 1;
       vs.rows = g.total_n / vs.n_in;
       vs.rows_per_warp = 64;
@@ -214,7 +217,10 @@ bool choose_vote_rows(const rsft::Geometry& g, rsft::VoteRowSchedule& vs) {
 
 // Group the bucket dimensions into shared-memory FFT passes, last dimension last.
 bool plan_fft_passes(const rsft::Geometry& g, std::vector<rsft::FftPass>& passes) {
-  const int64_t target = 2048, cap = 16384;
+  // slab size: about four CTAs per SM over all loops, between 256 and 2048 buckets
+  int64_t target = 256;
+  while (target < 2048 && target * 4 * 152 < static_cast<int64_t>(g.loops) * g.total_b) target *= 2;
+  const int64_t cap = 16384;
   passes.clear();
   int db = g.ndim;
   while (db > 0) {
@@ -465,6 +471,7 @@ rsft_status build_device(rsft_plan* p) {
     p->tables.fcolw = f2p;
   }
   p->tables.rowmask = nullptr;
+  p->tables.kbtab = nullptr;
   if (p->rows_mode && p->rows.small) {
     // candidate masks of the inner buckets of a row: bit i_in of mask[l][b] set iff the
     // inner candidates R(b, sigma_l^{-1}) (Def. 4, trailing dimensions) contain i_in
@@ -485,8 +492,20 @@ rsft_status build_device(rsft_plan* p) {
           masks[static_cast<size_t>(l) * vs.b_in + b] |= 1ull << iin;
         }
     uint64_t* mp = nullptr;
+    if (masks.size() % 2) masks.push_back(0ull);  // whole 16-byte units for the bulk copy
     if ((st = upload(p, &mp, masks)) != RSFT_OK) return st;
     p->tables.rowmask = mp;
+    // bucket-plane offsets of the row dimensions: ((sigma i mod N_d) >> log M_d) << b_shift_d
+    std::vector<uint32_t> kb;
+    for (int d = 0; d < vs.d_v; ++d)
+      for (int l = 0; l < L; ++l)
+        for (int64_t i = 0; i < h.n[d]; ++i)
+          kb.push_back(static_cast<uint32_t>((((h.sigma[l * D + d] * i) & (h.n[d] - 1)) >> p->geom.log_m[d])
+                                             << p->geom.b_shift[d]));
+    while (kb.empty() || kb.size() % 4 != 0) kb.push_back(0u);  // whole 16-byte units for the bulk copy
+    uint32_t* kp = nullptr;
+    if ((st = upload(p, &kp, kb)) != RSFT_OK) return st;
+    p->tables.kbtab = kp;
   }
   // workspace
   rsft::Workspace& ws = p->ws;
@@ -500,7 +519,10 @@ rsft_status build_device(rsft_plan* p) {
     if ((st = dev_alloc(p, &ws.partial, np * sizeof(float2))) != RSFT_OK) return st;
   }
   ws.words_b = (h.total_b + 31) / 32;
-  if ((st = dev_alloc(p, &ws.det_bits, static_cast<size_t>(L) * ws.words_b * 4)) != RSFT_OK) return st;
+  // rounded up to 16 bytes: the vote kernel stages the bitmaps with one bulk copy
+  if ((st = dev_alloc(p, &ws.det_bits, (static_cast<size_t>(L) * ws.words_b * 4 + 15) & ~static_cast<size_t>(15))) !=
+      RSFT_OK)
+    return st;
   if ((st = dev_alloc(p, &ws.det_count, static_cast<size_t>(L) * 4)) != RSFT_OK) return st;
   ws.segments = rsft::stage2_segments(h.total_n);
   const size_t vote_bytes = static_cast<size_t>(ws.segments) * 16 * 1024;
@@ -510,9 +532,23 @@ rsft_status build_device(rsft_plan* p) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(votes)");
   if ((st = dev_alloc(p, &ws.seg_count, static_cast<size_t>(ws.segments) * 4)) != RSFT_OK) return st;
   if ((st = dev_alloc(p, &ws.seg_offset, static_cast<size_t>(ws.segments + 1) * 8)) != RSFT_OK) return st;
+  if (p->rows_mode && p->rows.small) {
+    // one wave of resident blocks: each block stages its tables once
+    int per_sm = 0, sms = 0;
+    cudaError_t oe = rsft::vote_rows_small_residency(g, p->rows, ws.words_b, &per_sm);
+    if (oe == cudaSuccess) oe = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (oe != cudaSuccess) return cuda_fail(oe, "vote kernel residency");
+    const int64_t resident_warps = static_cast<int64_t>(std::max(per_sm, 1)) * sms * 8;
+    int64_t rpw = (p->rows.rows + resident_warps - 1) / resident_warps;
+    rpw = std::max<int64_t>(32, (rpw + 31) / 32 * 32);
+    p->rows.rows_per_warp = static_cast<int>(rpw);
+    p->rows.warps = (p->rows.rows + rpw - 1) / rpw;
+  }
   if (p->rows_mode) {
     if ((st = dev_alloc(p, &ws.warp_count, static_cast<size_t>(p->rows.warps) * 4)) != RSFT_OK) return st;
     if ((st = dev_alloc(p, &ws.warp_offset, static_cast<size_t>(p->rows.warps + 1) * 8)) != RSFT_OK) return st;
+    if (p->rows.small && (st = dev_alloc(p, &ws.row_gt, static_cast<size_t>(p->rows.rows) * 8)) != RSFT_OK)
+      return st;
   }
   if ((st = dev_alloc(p, &p->d_count, 16)) != RSFT_OK) return st;
   ws.err_flag = reinterpret_cast<int*>(p->d_count + 1);  // [1] of the count block
@@ -618,7 +654,7 @@ rsft_status run(rsft_plan* p, const void* d_cube, cudaStream_t stream, uint64_t*
     mark(3);
     e = rsft::launch_vote_rows(g, p->rows, p->tables, ws.det_bits, ws.words_b, p->host.mu, ws.warp_count,
                                ws.warp_offset, d_located, d_located_votes, d_votes_out, p->host.desc.max_located,
-                               d_count, stream);
+                               d_count, ws.err_flag, ws.row_gt, stream);
     if (e != cudaSuccess) return cuda_fail(e, "vote_rows");
   } else {
     p->votes_dirty = true;

@@ -88,6 +88,7 @@ struct DeviceTables {
   const unsigned short* h_xdig;
   const unsigned short* x_digits;   // [X][4]: inner residue digit per inner dimension
   const uint64_t* rowmask;          // [L][b_in]: candidate mask of each inner bucket (rows <= 64)
+  const uint32_t* kbtab;            // per row dimension d < d_v: [L][N_d] bucket offset (Def. 3) of index i_d
 };
 
 struct Workspace {
@@ -102,6 +103,7 @@ struct Workspace {
   int* err_flag;         // set by a bounded device wait that gave up
   uint32_t* warp_count;  // [row warps] vote_rows hits per warp
   uint64_t* warp_offset; // [row warps + 1]
+  uint64_t* row_gt;      // [rows] small-row vote kernel: per-row mask of votes > mu
   int64_t words_b;
   int64_t segments;
   int64_t vote_words;
@@ -129,7 +131,11 @@ int64_t stage2_segments(int64_t total_n);   // 16 KiB vote segments covering N b
 cudaError_t launch_vote_rows(const Geometry& g, const VoteRowSchedule& vs, const DeviceTables& t,
                              const uint32_t* det_bits, int64_t words_b, int mu, uint32_t* warp_count,
                              uint64_t* warp_offset, uint64_t* located, uint8_t* located_votes,
-                             uint8_t* votes_out, int64_t capacity, int64_t* d_count, cudaStream_t stream);
+                             uint8_t* votes_out, int64_t capacity, int64_t* d_count, int* err,
+                             uint64_t* row_gt, cudaStream_t stream);
+// Resident blocks per SM of the small-row vote kernel at this plan's shared-memory size.
+cudaError_t vote_rows_small_residency(const Geometry& g, const VoteRowSchedule& vs, int64_t words_b,
+                                      int* blocks_per_sm);
 
 int fold_smem_bytes(const Geometry& g, const FoldSchedule& fs, int lg);
 

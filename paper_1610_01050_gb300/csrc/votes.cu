@@ -24,6 +24,7 @@
 
 #include "device.cuh"
 #include "rsft.h"
+#include "tma.cuh"
 
 namespace rsft {
 namespace {
@@ -314,6 +315,66 @@ __global__ void __launch_bounds__(kMedianWarps * 32) median_kernel(const MedianA
   }
 }
 
+// Loops of G lanes (L <= G): 32 / G located indices per warp, the per-loop
+// values stay in registers and the ranks come from shuffles within the group.
+template <int G>
+__global__ void __launch_bounds__(kMedianWarps * 32) median_group_kernel(const MedianArgs a) {
+  const Geometry& g = a.g;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int sub = lane / G, l = lane % G;
+  constexpr int kPerWarp = 32 / G;
+  int64_t count = *a.d_count;
+  if (count > a.capacity) count = a.capacity;
+  const int L = g.loops;
+  const int lo_rank = (L - 1) / 2, hi_rank = L / 2;
+  const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (sub * G);
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * kMedianWarps * kPerWarp;
+  for (int64_t base = (static_cast<int64_t>(blockIdx.x) * kMedianWarps + wid) * kPerWarp; base < count;
+       base += stride) {
+    const int64_t q = base + sub;
+    const bool active = q < count && l < L;
+    float xr = 0.f, xi = 0.f;
+    if (active) {
+      const uint64_t i = a.located[q];
+      int64_t k = 0;
+      float2 val = make_float2(1.f, 0.f);
+#pragma unroll
+      for (int d = 0; d < kMaxDim; ++d) {
+        if (d < g.ndim) {
+          const uint32_t id = static_cast<uint32_t>((i >> g.n_shift[d]) & static_cast<uint64_t>(g.n[d] - 1));
+          const uint32_t p = (static_cast<uint32_t>(a.t.sigma[l * g.ndim + d]) * id) &
+                             static_cast<uint32_t>(g.n[d] - 1);  // [sigma i]_N
+          const uint32_t kd = p >> g.log_m[d];                  // M(i, sigma), Def. 3
+          const uint32_t v = p & static_cast<uint32_t>(g.m[d] - 1);
+          k += static_cast<int64_t>(kd) << g.b_shift[d];
+          const float2 gi = __ldg(a.t.ginv[d] + v);
+          val = make_float2(val.x * gi.x - val.y * gi.y, val.x * gi.y + val.y * gi.x);
+        }
+      }
+      const float2 f = a.spectrum[static_cast<int64_t>(l) * g.total_b + k];
+      xr = f.x * val.x - f.y * val.y;
+      xi = f.x * val.y + f.y * val.x;
+    }
+    int rr = 0, ri = 0;
+    for (int m2 = 0; m2 < L; ++m2) {
+      const float yr = __shfl_sync(0xffffffffu, xr, m2, G);
+      const float yi = __shfl_sync(0xffffffffu, xi, m2, G);
+      rr += (yr < xr) || (yr == xr && m2 < l);
+      ri += (yi < xi) || (yi == xi && m2 < l);
+    }
+    // ranks are a permutation of [0, L): exactly one lane of an active group holds each
+    const unsigned b0 = __ballot_sync(0xffffffffu, active && rr == lo_rank) & gmask;
+    const unsigned b1 = __ballot_sync(0xffffffffu, active && rr == hi_rank) & gmask;
+    const unsigned b2 = __ballot_sync(0xffffffffu, active && ri == lo_rank) & gmask;
+    const unsigned b3 = __ballot_sync(0xffffffffu, active && ri == hi_rank) & gmask;
+    const float r0 = __shfl_sync(0xffffffffu, xr, b0 ? __ffs(b0) - 1 : lane);
+    const float r1 = __shfl_sync(0xffffffffu, xr, b1 ? __ffs(b1) - 1 : lane);
+    const float i0 = __shfl_sync(0xffffffffu, xi, b2 ? __ffs(b2) - 1 : lane);
+    const float i1 = __shfl_sync(0xffffffffu, xi, b3 ? __ffs(b3) - 1 : lane);
+    if (active && l == 0) a.amp[q] = make_float2(0.5f * (r0 + r1), 0.5f * (i0 + i1));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // vote_rows: the reverse mapping and accumulation of Algorithm 1 and the
 // second-stage detection, organised by output rows instead of by detected
@@ -331,6 +392,7 @@ __global__ void __launch_bounds__(kMedianWarps * 32) median_kernel(const MedianA
 struct RowArgs {
   Geometry g;
   DeviceTables t;
+  int* err;                 // set when a barrier wait gives up
   const uint32_t* det_bits;
   int64_t words_b;
   int d_v;
@@ -347,6 +409,7 @@ struct RowArgs {
   uint8_t* located_votes;
   uint8_t* votes_out;
   int64_t capacity;
+  uint64_t* row_gt;         // small rows: [rows] locations of the row with votes > mu (pass 0 -> pass 1)
 };
 
 constexpr int kRowWarps = 8;
@@ -518,92 +581,121 @@ __global__ void __launch_bounds__(kRowWarps * 32) vote_rows_kernel(const RowArgs
 // buckets (the OR of the precomputed masks R(b, sigma_l^{-1}) of the row's
 // detected inner buckets b, Def. 4) with a ripple carry, and a bit-sliced
 // comparison with mu gives the second-stage hits of all 64 locations at once.
+// Shared-memory layout of the small-row kernel (byte offsets, all multiples of 16):
+// [0, 16) barrier, then the bucket-offset tables, then (staged) the candidate masks
+// and the detection bitmaps.  Copy sizes are rounded up to 16 bytes; the plan pads
+// the three device arrays to match.
+struct SmallRowLayout {
+  uint32_t kb_bytes, mask_bytes, bit_bytes;
+  uint32_t kb_off, mask_off, bit_off, queue_off, total;
+  int kb_words;
+};
+
+__host__ __device__ __forceinline__ uint32_t round16(uint64_t v) { return static_cast<uint32_t>((v + 15) & ~15ull); }
+
+__host__ __device__ inline SmallRowLayout small_row_layout(const Geometry& g, int d_v, int b_in, int64_t words_b,
+                                                           int staged) {
+  SmallRowLayout s{};
+  s.kb_words = 0;
+  for (int d = 0; d < d_v; ++d) s.kb_words += g.loops * static_cast<int>(g.n[d]);
+  s.kb_bytes = round16(static_cast<uint64_t>(s.kb_words) * 4);
+  s.mask_bytes = round16(static_cast<uint64_t>(g.loops) * b_in * 8);
+  s.bit_bytes = round16(static_cast<uint64_t>(g.loops) * words_b * 4);
+  s.kb_off = 16;
+  s.mask_off = s.kb_off + s.kb_bytes;
+  s.bit_off = s.mask_off + (staged ? s.mask_bytes : 0);
+  s.queue_off = s.bit_off + (staged ? s.bit_bytes : 0);
+  s.total = s.queue_off + kRowWarps * 64 * 8;  // per-warp FIFO of 64 row indices
+  return s;
+}
+
 template <int PASS>
 __global__ void __launch_bounds__(kRowWarps * 32) vote_rows_small_kernel(const RowArgs a, const uint64_t* masks,
-                                                                         int staged) {
-  extern __shared__ uint64_t smem_small[];
+                                                                         const uint32_t* kbtab, int staged) {
+  extern __shared__ __align__(16) unsigned char smem_small[];
   const Geometry& g = a.g;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int L = g.loops;
-  const int64_t bit_words = static_cast<int64_t>(L) * a.words_b;
-  const int64_t mask_n = static_cast<int64_t>(L) * a.b_in;
-  const uint32_t* bits = a.det_bits;
-  const uint64_t* mk = masks;
-  // sigma of the row dimensions, [L][d_v], always staged
-  int* ssig = reinterpret_cast<int*>(smem_small);
-  for (int e = threadIdx.x; e < L * a.d_v; e += kRowWarps * 32) {
-    const int l = e / a.d_v, d = e - l * a.d_v;
-    ssig[e] = a.t.sigma[l * g.ndim + d];
+  const SmallRowLayout lay = small_row_layout(g, a.d_v, a.b_in, a.words_b, staged);
+  // bucket-plane offsets of the row dimensions: kbtab[d] = [L][N_d] ((sigma i mod N_d) >> log M_d) << b_shift_d
+  int kb_off[kMaxDim];
+  {
+    int off = 0;
+#pragma unroll
+    for (int d = 0; d < kMaxDim; ++d) {
+      kb_off[d] = off;
+      if (d < a.d_v) off += L * static_cast<int>(g.n[d]);
+    }
   }
-  const int sig_words = ((L * a.d_v + 1) / 2 + 1) & ~1;  // in uint64 units, kept 16-byte aligned
-  if (staged) {
-    uint64_t* sm = smem_small + sig_words;
-    uint32_t* sb = reinterpret_cast<uint32_t*>(sm + mask_n);
-    for (int64_t w = threadIdx.x; w < mask_n; w += kRowWarps * 32) sm[w] = __ldg(masks + w);
-    for (int64_t w = threadIdx.x; w < bit_words; w += kRowWarps * 32) sb[w] = __ldg(a.det_bits + w);
-    bits = sb;
-    mk = sm;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_small);
+  const uint32_t* skb = reinterpret_cast<const uint32_t*>(smem_small + lay.kb_off);
+  const uint32_t* bits = staged ? reinterpret_cast<const uint32_t*>(smem_small + lay.bit_off) : a.det_bits;
+  const uint64_t* mk = staged ? reinterpret_cast<const uint64_t*>(smem_small + lay.mask_off) : masks;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
   }
   __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint64_t pol = policy_evict_last();
+    const uint32_t bytes = lay.kb_bytes + (staged ? lay.mask_bytes + lay.bit_bytes : 0u);
+    mbar_arrive_expect_tx(bar, bytes);
+    if (lay.kb_bytes) bulk_g2s(smem_small + lay.kb_off, kbtab, lay.kb_bytes, bar, pol);  // none when d_v == 0
+    if (staged) {
+      bulk_g2s(smem_small + lay.mask_off, masks, lay.mask_bytes, bar, pol);
+      bulk_g2s(smem_small + lay.bit_off, a.det_bits, lay.bit_bytes, bar, pol);
+    }
+  }
+  if (!mbar_wait_bounded(bar, 0u, a.err)) return;  // no block-wide barriers below
   const int64_t gw = static_cast<int64_t>(blockIdx.x) * kRowWarps + wid;
-  if (gw >= a.warps) return;  // no block-wide barriers below
+  if (gw >= a.warps) return;
+  int64_t* queue = reinterpret_cast<int64_t*>(smem_small + lay.queue_off) + wid * 64;
   const uint64_t valid_bits = a.n_in >= 64 ? ~0ull : ((1ull << a.n_in) - 1ull);
-  uint64_t pos = PASS == 1 ? a.warp_offset[gw] : 0ull;
-  uint32_t hits = 0;
-  const int64_t row0 = gw * a.rows_per_warp;
-  const int plane_words = a.b_in <= 32 ? 1 : 2;
+  const bool full = PASS == 1 && a.votes_out != nullptr;
+  const bool wide = a.b_in > 32;
   const uint32_t pat_mask = a.b_in < 32 ? ((1u << a.b_in) - 1u) : 0xffffffffu;
-  for (int rb = 0; rb < a.rows_per_warp; rb += 32) {
-    const int64_t row = row0 + rb + lane;
-    const bool valid = rb + lane < a.rows_per_warp && row < a.rows;
-    // digits of the row's leading indices, once per row
-    uint32_t id[kMaxDim];
-    {
-      uint64_t r = static_cast<uint64_t>(row);
+
+  // bucket-plane offset of `row` in loop l, from the per-dimension tables
+  auto plane = [&](int64_t row, int l) -> uint32_t {
+    uint64_t r = static_cast<uint64_t>(row);
+    uint32_t kb = 0u;
 #pragma unroll
-      for (int d = kMaxDim - 1; d >= 0; --d) {
-        id[d] = 0u;
-        if (d < a.d_v) {
-          id[d] = static_cast<uint32_t>(r) & static_cast<uint32_t>(g.n[d] - 1);
-          r >>= g.log_n[d];
-        }
+    for (int d = kMaxDim - 1; d >= 0; --d) {
+      if (d < a.d_v) {
+        kb += skb[kb_off[d] + l * static_cast<int>(g.n[d]) +
+                  (static_cast<uint32_t>(r) & static_cast<uint32_t>(g.n[d] - 1))];
+        r >>= g.log_n[d];
       }
     }
-    uint64_t c[8];
+    return kb;
+  };
+  // bit-sliced vote counters of the row's n_in locations (bit p of every location in c[p])
+  auto count = [&](int64_t row, uint64_t* c) {
 #pragma unroll
     for (int p = 0; p < 8; ++p) c[p] = 0ull;
-    if (valid) {
-      for (int l = 0; l < L; ++l) {
-        uint32_t kb = 0u;
-        const int* sl = ssig + l * a.d_v;
-#pragma unroll
-        for (int d = 0; d < kMaxDim; ++d) {
-          if (d < a.d_v) {
-            const uint32_t p = (static_cast<uint32_t>(sl[d]) * id[d]) & static_cast<uint32_t>(g.n[d] - 1);
-            kb += (p >> g.log_m[d]) << g.b_shift[d];
-          }
-        }
-        const uint32_t* bl = bits + static_cast<int64_t>(l) * a.words_b;
-        uint64_t pat = (bl[kb >> 5] >> (kb & 31u)) & pat_mask;
-        if (plane_words == 2) pat |= static_cast<uint64_t>(bl[(kb >> 5) + 1]) << 32;
-        if (!pat) continue;
-        uint64_t m = 0ull;
-        const uint64_t* ml = mk + static_cast<int64_t>(l) * a.b_in;
-        while (pat) {
-          m |= ml[__ffsll(static_cast<long long>(pat)) - 1];
-          pat &= pat - 1;
-        }
-        uint64_t carry = m;
-#pragma unroll
-        for (int p = 0; p < 8; ++p) {
-          const uint64_t t = c[p] & carry;
-          c[p] ^= carry;
-          carry = t;
-        }
+    for (int l = 0; l < L; ++l) {
+      const uint32_t kb = plane(row, l);
+      const uint32_t* bl = bits + static_cast<int64_t>(l) * a.words_b;
+      uint64_t pat = (bl[kb >> 5] >> (kb & 31u)) & pat_mask;
+      if (wide) pat |= static_cast<uint64_t>(bl[(kb >> 5) + 1]) << 32;
+      if (!pat) continue;
+      uint64_t m = 0ull;
+      const uint64_t* ml = mk + static_cast<int64_t>(l) * a.b_in;
+      while (pat) {
+        m |= ml[__ffsll(static_cast<long long>(pat)) - 1];
+        pat &= pat - 1;
+      }
+      uint64_t carry = m;
+      for (int p = 0; p < 8 && carry; ++p) {
+        const uint64_t t = c[p] & carry;
+        c[p] ^= carry;
+        carry = t;
       }
     }
-    // votes > mu, bit-sliced
-    uint64_t gt = 0ull, eq = ~0ull;
+  };
+  // votes > mu, bit-sliced
+  auto above = [&](const uint64_t* c) -> uint64_t {
+    uint64_t eq = ~0ull, gt = 0ull;
 #pragma unroll
     for (int p = 7; p >= 0; --p) {
       if ((a.mu >> p) & 1) {
@@ -613,11 +705,34 @@ __global__ void __launch_bounds__(kRowWarps * 32) vote_rows_small_kernel(const R
         eq &= ~c[p];
       }
     }
-    gt &= valid ? valid_bits : 0ull;
-    const int h = __popcll(gt);
+    return gt & valid_bits;
+  };
+
+  uint64_t pos = PASS == 1 ? a.warp_offset[gw] : 0ull;
+  uint32_t hits = 0;
+  int head = 0, queued = 0;  // FIFO of rows (ascending) that need their votes counted
+  // Count the votes of up to 32 queued rows, one per lane, in queue order.
+  auto drain = [&](int take) {
+    const bool act = lane < take;
+    const int64_t row = act ? queue[(head + lane) & 63] : 0;
+    uint64_t c[8];
+    uint64_t gt = 0ull;
     if (PASS == 0) {
-      hits += static_cast<uint32_t>(h);
+      if (act) {
+        count(row, c);
+        gt = above(c);
+        a.row_gt[row] = gt;
+      }
+      hits += static_cast<uint32_t>(__popcll(gt));
     } else {
+      if (act) {
+        gt = full ? 0ull : a.row_gt[row];
+        if (full || a.located_votes) {
+          count(row, c);
+          if (full) gt = above(c);
+        }
+      }
+      const int h = __popcll(gt);
       int incl = h;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -642,7 +757,7 @@ __global__ void __launch_bounds__(kRowWarps * 32) vote_rows_small_kernel(const R
         ++out;
       }
       pos += static_cast<uint64_t>(tot);
-      if (a.votes_out && valid) {
+      if (full && act) {
         for (int bit = 0; bit < a.n_in; ++bit) {
           uint32_t v = 0;
 #pragma unroll
@@ -651,7 +766,43 @@ __global__ void __launch_bounds__(kRowWarps * 32) vote_rows_small_kernel(const R
         }
       }
     }
+    head = (head + take) & 63;
+    queued -= take;
+  };
+
+  const int64_t row0 = gw * a.rows_per_warp;
+  for (int rb = 0; rb < a.rows_per_warp; rb += 32) {
+    const int64_t row = row0 + rb + lane;
+    const bool valid = rb + lane < a.rows_per_warp && row < a.rows;
+    bool take = false;
+    if (PASS == 0) {
+      // how many loops hold a detection in this row's planes; a row with at most mu
+      // of them cannot pass the second stage
+      int nz = 0;
+      if (valid) {
+        for (int l = 0; l < L; ++l) {
+          const uint32_t kb = plane(row, l);
+          const uint32_t* bl = bits + static_cast<int64_t>(l) * a.words_b;
+          bool any = ((bl[kb >> 5] >> (kb & 31u)) & pat_mask) != 0u;
+          if (wide) any = any || bl[(kb >> 5) + 1] != 0u;
+          nz += any ? 1 : 0;
+        }
+      }
+      take = valid && nz > a.mu;
+      if (valid && !take) a.row_gt[row] = 0ull;
+    } else {
+      take = valid && (full || a.row_gt[row] != 0ull);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, take);
+    if (take) queue[(head + queued + __popc(bal & ((1u << lane) - 1u))) & 63] = row;
+    __syncwarp();
+    queued += __popc(bal);
+    if (queued >= 32) {
+      drain(32);
+      __syncwarp();
+    }
   }
+  if (queued > 0) drain(queued);
   if (PASS == 0) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) hits += __shfl_xor_sync(0xffffffffu, hits, o);
@@ -698,10 +849,36 @@ cudaError_t launch_stage2(const Geometry& g, int mu, Workspace& ws, uint64_t* lo
   return cudaGetLastError();
 }
 
+// Shared memory of the small-row kernel (staging the masks and bitmaps when they fit),
+// with the kernels' dynamic shared-memory limit raised to match.
+static cudaError_t small_rows_smem(const Geometry& g, const VoteRowSchedule& vs, int64_t words_b, int* staged,
+                            size_t* smem) {
+  const SmallRowLayout full = small_row_layout(g, vs.d_v, vs.b_in, words_b, 1);
+  *staged = full.total <= 160 * 1024 ? 1 : 0;
+  *smem = *staged ? full.total : small_row_layout(g, vs.d_v, vs.b_in, words_b, 0).total;
+  cudaError_t e = cudaFuncSetAttribute(vote_rows_small_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(*smem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(vote_rows_small_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(*smem));
+  return e;
+}
+
+cudaError_t vote_rows_small_residency(const Geometry& g, const VoteRowSchedule& vs, int64_t words_b,
+                                      int* blocks_per_sm) {
+  int staged = 0;
+  size_t smem = 0;
+  cudaError_t e = small_rows_smem(g, vs, words_b, &staged, &smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, vote_rows_small_kernel<1>, kRowWarps * 32,
+                                                       smem);
+}
+
 cudaError_t launch_vote_rows(const Geometry& g, const VoteRowSchedule& vs, const DeviceTables& t,
                              const uint32_t* det_bits, int64_t words_b, int mu, uint32_t* warp_count,
                              uint64_t* warp_offset, uint64_t* located, uint8_t* located_votes,
-                             uint8_t* votes_out, int64_t capacity, int64_t* d_count, cudaStream_t stream) {
+                             uint8_t* votes_out, int64_t capacity, int64_t* d_count, int* err,
+                             uint64_t* row_gt, cudaStream_t stream) {
   if (vs.small) {
     RowArgs a;
     a.g = g;
@@ -722,31 +899,26 @@ cudaError_t launch_vote_rows(const Geometry& g, const VoteRowSchedule& vs, const
     a.located_votes = located_votes;
     a.votes_out = votes_out;
     a.capacity = capacity;
+    a.err = err;
+    a.row_gt = row_gt;
     const unsigned blocks = static_cast<unsigned>((vs.warps + kRowWarps - 1) / kRowWarps);
-    const size_t sig_bytes = static_cast<size_t>((((g.loops * vs.d_v + 1) / 2 + 1) & ~1)) * 8;
-    const size_t need = static_cast<size_t>(g.loops) * vs.b_in * 8 + static_cast<size_t>(g.loops) * words_b * 4;
-    const int staged = need <= 112 * 1024 ? 1 : 0;
-    const size_t smem = sig_bytes + (staged ? need : 0);
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(vote_rows_small_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(smem));
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(vote_rows_small_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(smem));
-      if (e != cudaSuccess) return e;
-    }
-    vote_rows_small_kernel<0><<<blocks, kRowWarps * 32, smem, stream>>>(a, t.rowmask, staged);
-    cudaError_t e = cudaGetLastError();
+    int staged = 0;
+    size_t smem = 0;
+    cudaError_t e = small_rows_smem(g, vs, words_b, &staged, &smem);
+    if (e != cudaSuccess) return e;
+    vote_rows_small_kernel<0><<<blocks, kRowWarps * 32, smem, stream>>>(a, t.rowmask, t.kbtab, staged);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     stage2_scan_kernel<<<1, 1024, 0, stream>>>(warp_count, vs.warps, warp_offset, d_count);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    vote_rows_small_kernel<1><<<blocks, kRowWarps * 32, smem, stream>>>(a, t.rowmask, staged);
+    vote_rows_small_kernel<1><<<blocks, kRowWarps * 32, smem, stream>>>(a, t.rowmask, t.kbtab, staged);
     return cudaGetLastError();
   }
   RowArgs a;
   a.g = g;
   a.t = t;
+  a.err = err;
   a.det_bits = det_bits;
   a.words_b = words_b;
   a.d_v = vs.d_v;
@@ -798,6 +970,19 @@ cudaError_t launch_median(const Geometry& g, const DeviceTables& t, const float2
   int64_t blocks = (capacity + kMedianWarps - 1) / kMedianWarps;
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks < 1) blocks = 1;
+  const int L = g.loops;
+  const int per_warp = L <= 4 ? 8 : L <= 8 ? 4 : L <= 16 ? 2 : L <= 32 ? 1 : 0;
+  if (per_warp > 0) {
+    int64_t gb = (capacity + kMedianWarps * per_warp - 1) / (kMedianWarps * per_warp);
+    if (gb > 152 * 8) gb = 152 * 8;
+    if (gb < 1) gb = 1;
+    const unsigned gu = static_cast<unsigned>(gb);
+    if (per_warp == 8) median_group_kernel<4><<<gu, kMedianWarps * 32, 0, stream>>>(args);
+    else if (per_warp == 4) median_group_kernel<8><<<gu, kMedianWarps * 32, 0, stream>>>(args);
+    else if (per_warp == 2) median_group_kernel<16><<<gu, kMedianWarps * 32, 0, stream>>>(args);
+    else median_group_kernel<32><<<gu, kMedianWarps * 32, 0, stream>>>(args);
+    return cudaGetLastError();
+  }
   median_kernel<<<static_cast<unsigned>(blocks), kMedianWarps * 32, 0, stream>>>(args);
   return cudaGetLastError();
 }
