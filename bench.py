@@ -52,6 +52,27 @@ def dist_env():
     return ws, rank, local
 
 
+def shard_frames(rank, frames):
+    """Frame ids of one rank: ranks own disjoint frames (weak scaling, no data exchange)."""
+    return [rank * frames + f for f in range(frames)]
+
+
+def max_over_ranks(value, ws, device=None):
+    """The largest of the ranks' values (the slowest rank's time); identity for one rank."""
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws, steps, ms):
+    """Frames per second of the whole job: every rank runs `steps` frames in at most `ms`."""
+    return ws * steps / (ms / 1e3)
+
+
 def measured_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -130,28 +151,35 @@ def workload_desc(R, wl, nv, seed):
                        p_fa=wl.p_fa, k_max=wl.k_design, noise_var=nv, seed=seed, max_located=1 << 20)
 
 
-def oracle_sample(wl, cube, nv, seed, loops):
-    """Time the FP64 oracle (as it stands) on `loops` loops of one frame; returns seconds."""
+def oracle_plan(wl, nv, seed):
     import oracle as O
-    op = O.make_plan(wl.shape, wl.buckets, wl.loops, seed=seed, atten_db=wl.atten_db,
-                     flat_support=wl.flat_support, noise_var=nv, p_fa=wl.p_fa, k_max=wl.k_design)
-    sub = O.make_plan(wl.shape, wl.buckets, loops, seed=seed, atten_db=wl.atten_db,
-                      flat_support=wl.flat_support, noise_var=nv, sigma=op.sigma[:loops], pfa1=op.pfa1,
-                      mu=min(op.mu, loops - 1))
+    return O.make_plan(wl.shape, wl.buckets, wl.loops, seed=seed, atten_db=wl.atten_db,
+                       flat_support=wl.flat_support, noise_var=nv, p_fa=wl.p_fa, k_max=wl.k_design)
+
+
+def oracle_frame(op, x):
+    """Time the FP64 oracle (as it stands) on one whole frame, all L loops; returns
+    (wall seconds, threads used = CPU time / wall time)."""
+    import oracle as O
+    t0, c0 = time.perf_counter(), time.process_time()
+    O.rsft(op, x, estimate=True, keep=False)
+    wall = time.perf_counter() - t0
+    return wall, max(1, int(round((time.process_time() - c0) / max(wall, 1e-9))))
+
+
+def cpu_baseline(wl, cube, nv, seed, min_s=10.0, max_frames=3):
+    """Whole frames through the oracle until about 10 s of CPU work (at most 3 frames)."""
+    op = oracle_plan(wl, nv, seed)
     x = cube.astype(np.complex128)
-    t0 = time.perf_counter()
-    O.rsft(sub, x, estimate=True, keep=False)
-    return time.perf_counter() - t0
-
-
-def cpu_baseline(wl, cube, nv, seed):
-    t1 = oracle_sample(wl, cube, nv, seed, 1)
-    loops = wl.loops if t1 * wl.loops <= 30.0 else max(1, int(20.0 / t1))
-    t = oracle_sample(wl, cube, nv, seed, loops) if loops > 1 else t1
-    per_frame = t * wl.loops / loops
-    sample = (f"one {'x'.join(map(str, wl.shape))} frame, {loops} of {wl.loops} loops of the FP64 oracle "
-              f"(plan excluded), {t:.1f} s, scaled to a frame by L/{loops}")
-    return {"value": 1.0 / per_frame, "unit": "frames/s", "cores": 1, "kind": "oracle", "sample": sample}
+    times, cores = [], 1
+    while len(times) < max_frames and sum(times) < min_s:
+        t, c = oracle_frame(op, x)
+        times.append(t)
+        cores = max(cores, c)
+    per_frame = sum(times) / len(times)
+    sample = (f"{len(times)} whole {'x'.join(map(str, wl.shape))} frame(s), all {wl.loops} loops of the FP64 "
+              f"oracle (plan excluded), {sum(times):.1f} s")
+    return {"value": 1.0 / per_frame, "unit": "frames/s", "cores": cores, "kind": "oracle", "sample": sample}
 
 
 def run_reference(args):
@@ -162,20 +190,25 @@ def run_reference(args):
     wl = ri.WORKLOADS[args.workload]
     cube, _, _, nv = ri.workload_frame(args.workload, 0)
     seed = ri.frame_seed(wl, 0)
-    # a step = one loop of the oracle on one frame (a bounded sample); frames/s scales by 1/L
-    for _ in range(args.warmup):
-        oracle_sample(wl, cube, nv, seed, 1)
-    steps = max(1, min(args.steps, 20))
-    times = [oracle_sample(wl, cube, nv, seed, 1) for _ in range(steps)]
-    per_step = sum(times) / len(times)
-    value = 1.0 / (per_step * wl.loops)
-    sample = f"1 of {wl.loops} loops of one frame per step, {steps} steps, scaled by 1/L"
+    # a step is one whole frame through the oracle (seconds each): at most 3 warm-up and 5 timed steps
+    op = oracle_plan(wl, nv, seed)
+    x = cube.astype(np.complex128)
+    warmup = min(args.warmup, 3)
+    for _ in range(warmup):
+        oracle_frame(op, x)
+    steps = max(1, min(args.steps, 5))
+    runs = [oracle_frame(op, x) for _ in range(steps)]
+    per_step = sum(t for t, _ in runs) / len(runs)
+    cores = max(c for _, c in runs)
+    value = 1.0 / per_step
+    sample = (f"one whole {'x'.join(map(str, wl.shape))} frame per step (all {wl.loops} loops), {steps} steps "
+              f"after {warmup} warm-up")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
-        "steps": steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+        "steps": steps, "warmup": warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name, "shape": list(wl.shape), "buckets": list(wl.buckets), "loops": wl.loops},
-        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -216,8 +249,8 @@ def run_ours(args):
     F = max(1, args.frames)
     host, targets = [], []
     nv = wl.noise_var
-    for f in range(F):
-        cube, tg, _, nv = ri.workload_frame(args.workload, rank * F + f)
+    for fid in shard_frames(rank, F):
+        cube, tg, _, nv = ri.workload_frame(args.workload, fid)
         host.append(torch.from_numpy(cube).pin_memory())
         targets.append(tg)
     dev = torch.device("cuda", local)
@@ -266,11 +299,8 @@ def run_ours(args):
     stage = R.rsft_plan_get(plan, R.RSFT_GET_STAGE_MS)
     R.rsft_plan_timing(plan, False)
     clocks = sampler.stop()
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, ws, dev)
+    value = whole_job_rate(ws, args.steps, ms)
 
     # roofline of the dominant kernel (the fold): algorithmic bytes / average launch time
     fold_bytes = int(R.rsft_plan_get(plan, R.RSFT_GET_FOLD_BYTES)[0])
@@ -289,17 +319,15 @@ def run_ours(args):
     for k in range(3):
         R.rsft_execute_host(plan, host[k % F], h_loc, h_amp, stream=stream, allow_capacity=True)
     torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
     t0 = time.perf_counter()
     d2h = 0
     for k in range(e2e_steps):
         c = R.rsft_execute_host(plan, host[k % F], h_loc, h_amp, stream=stream, allow_capacity=True)
         d2h += 8 + 16 * min(c, cap)
-    t_e2e = time.perf_counter() - t0
-    e2e_val = e2e_steps / t_e2e
-    if ws > 1:
-        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_val = ws * e2e_steps / float(t.item())
+    t_e2e = max_over_ranks(time.perf_counter() - t0, ws, dev)
+    e2e_val = whole_job_rate(ws, e2e_steps, t_e2e * 1e3)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
