@@ -130,19 +130,26 @@ bool choose_fold_schedule(const rsft::Geometry& g, rsft::FoldSchedule& out) {
     }
     if (xcount > width || xcount > 65535) continue;
     if (classes > (int64_t(1) << 30)) continue;
-    const int64_t table_cap = std::max<int64_t>(1, (64 * 1024) / (16 * lg));
-    int64_t rpc = 1;
-    while (rpc * 2 <= std::min(rows_pc, table_cap)) rpc *= 2;
-    const int64_t row_chunks = rows_pc / rpc;
+    // C classes side by side in a step: consecutive residues of the innermost row dimension
+    int64_t cps = 1;
+    if (d_in >= 1)
+      while (cps * 2 * width <= 2 * rsft::kFoldConsumers && cps * 2 <= g.b[d_in - 1] && cps * 2 <= classes) cps *= 2;
+    const int64_t rpc = rows_pc;  // whole classes per unit (direct output unless columns are chunked)
+    const int64_t crow = std::min<int64_t>(2 * rsft::kFoldConsumers / (width * cps), rpc);
+    const int64_t row_chunks = 1;
     const int64_t col_chunks = row_len / width;
-    const int64_t ctas = classes * row_chunks * col_chunks;
-    if (ctas > 0x7fffffff) continue;
-    const double setup = static_cast<double>(lg) / static_cast<double>(width);
+    const int64_t units = classes / cps * row_chunks * col_chunks;
+    if (units > 0x7fffffff || rpc > (int64_t(1) << 30)) continue;
+    const double setup = static_cast<double>(lg) / static_cast<double>(width * cps * crow / 2);
     const double partial = (row_chunks * col_chunks > 1)
                                ? 2.0 * lg * static_cast<double>(xcount) / static_cast<double>(rpc * width)
                                : 0.0;
-    const double fill = ctas < 2 * 152 ? static_cast<double>(2 * 152 - ctas) / (2 * 152) : 0.0;
-    const double cost = 0.5 * setup + partial + fill;
+    const double idle = 1.0 - static_cast<double>(width * cps * crow) / (2 * rsft::kFoldConsumers);
+    const double fill = units < 2 * 152 ? static_cast<double>(2 * 152 - units) / (2 * 152) : 0.0;
+    // rows without a tensor map go as one bulk copy each: small ones are request-rate bound
+    const bool tensor_map = d_in >= 1 && d_in <= 2 && width <= 256;
+    const double copies = (!tensor_map && width < 256) ? 1.0 : 0.0;
+    const double cost = 0.5 * setup + partial + fill + idle + copies;
     if (cost < best) {
       best = cost;
       found = true;
@@ -156,6 +163,9 @@ bool choose_fold_schedule(const rsft::Geometry& g, rsft::FoldSchedule& out) {
       out.row_chunks = static_cast<int>(row_chunks);
       out.xcount = static_cast<int>(xcount);
       out.direct = (row_chunks * col_chunks == 1) ? 1 : 0;
+      out.cps = static_cast<int>(cps);
+      out.crow = static_cast<int>(crow);
+      out.groups = static_cast<int>(classes / cps);
     }
   }
   return found;
@@ -357,12 +367,15 @@ rsft_status build_device(rsft_plan* p) {
       }
       return x;
     };
-    // lane bit k moves a thread by 2^(k+1) elements: a column bit or, past the chunk width, a row
+    // lane bit k moves a thread by 2^(k+1) elements: a column bit or, past the chunk width, a
+    // row bit (the class of the row for the first log2 C row bits, then its row)
     int rmask = 0;
     for (int k = 0; k < 5; ++k) {
       const int pbit = k + 1;
       bool keep = true;
-      if ((int64_t(1) << pbit) < fs.width) {
+      if ((int64_t(1) << pbit) >= fs.width) {
+        keep = ((int64_t(1) << pbit) / fs.width) >= fs.cps;
+      } else {
         int acc = 0;
         for (int d = D - 1; d >= fs.d_in; --d) {
           const int ln = ilog2(h.n[d]);
@@ -381,10 +394,12 @@ rsft_status build_device(rsft_plan* p) {
     fs.leaders = 32 >> nbits;
     const int warps = rsft::kFoldConsumers / 32;
     const int nslots = warps * fs.leaders * 2;
-    if (nslots % fs.xcount != 0) return fail(RSFT_ERR_UNSUPPORTED, "fold epilogue: residues not balanced");
-    fs.slots_per_x = nslots / fs.xcount;
+    const int keys = fs.cps * fs.xcount;  // (class in step, inner residue)
+    if (nslots % keys != 0) return fail(RSFT_ERR_UNSUPPORTED, "fold epilogue: residues not balanced");
+    fs.slots_per_x = nslots / keys;
+    if (nslots > 512 || fs.xcount > 512) return fail(RSFT_ERR_UNSUPPORTED, "fold epilogue: too many residues");
     std::vector<unsigned short> cols(static_cast<size_t>(nslots)), digits(static_cast<size_t>(fs.xcount) * 4, 0);
-    std::vector<int> fill(fs.xcount, 0);
+    std::vector<int> fill(keys, 0);
     for (int w = 0; w < warps; ++w)
       for (int j = 0; j < fs.leaders; ++j) {
         int lane = 0, bit = 0;
@@ -392,7 +407,7 @@ rsft_status build_device(rsft_plan* p) {
           if (!((rmask >> b) & 1)) lane |= ((j >> bit++) & 1) << b;
         for (int c = 0; c < 2; ++c) {
           const int64_t elem = 2 * (32 * w + lane) + c;
-          const int64_t x = residue(elem & (fs.width - 1));
+          const int64_t x = ((elem / fs.width) % fs.cps) * fs.xcount + residue(elem & (fs.width - 1));
           if (fill[x] >= fs.slots_per_x) return fail(RSFT_ERR_UNSUPPORTED, "fold epilogue: residues not balanced");
           cols[x * fs.slots_per_x + fill[x]++] = static_cast<unsigned short>((w * fs.leaders + j) * 2 + c);
         }
@@ -415,23 +430,28 @@ rsft_status build_device(rsft_plan* p) {
     p->tables.h_slots = p->h_slots.data();
     p->tables.h_xdig = p->h_xdig.data();
     p->tables.h_sinvb = p->h_sinvb.data();
+    if (rsft::fold_smem_bytes(g, fs, std::min(L, rsft::kMaxLoopGroup)) > 227 * 1024)
+      return fail(RSFT_ERR_UNSUPPORTED, "fold schedule needs more shared memory than a CTA has");
   }
   // fold tables in FP64, rounded once: per row the product of the row dimensions' weights
-  // a_{l,d}(s_d) as (c, d - c, c + d) of w = c + jd, and per column the product of the rest
+  // a_{l,d}(s_d) as (c, d - c, c + d, c + d) of w = c + jd, and per column the product of the rest
   {
     const rsft::FoldSchedule& fs = p->fold;
     auto weight = [&](int l, int d, int64_t sd) {
       return h.wbar[d][(h.sigma_inv[l * D + d] * sd) & (h.n[d] - 1)] * h.w[d][sd];
     };
-    const int64_t R = fs.rows_per_chunk, tunits = static_cast<int64_t>(fs.classes) * fs.row_chunks;
-    std::vector<float4> ft(static_cast<size_t>(L) * tunits * R);
+    // layout [class group][row chunk][row][class in group][loop]: a stage's rows are contiguous
+    const int64_t R = fs.rows_per_chunk, C = fs.cps;
+    const int64_t tunits = static_cast<int64_t>(fs.groups) * fs.row_chunks;
+    std::vector<float4> ft(static_cast<size_t>(L) * tunits * R * C);
     std::vector<float2> fc(static_cast<size_t>(L) * fs.col_chunks * fs.width);
     for (int l0 = 0; l0 < L; l0 += rsft::kMaxLoopGroup) {
       const int lg = std::min(rsft::kMaxLoopGroup, L - l0);
-      const size_t tbase = static_cast<size_t>(l0) * tunits * R;
-      for (int64_t tu = 0; tu < tunits; ++tu) {
-        const int64_t cls = tu / fs.row_chunks, rc = tu % fs.row_chunks;
-        for (int64_t r = 0; r < R; ++r) {
+      const size_t tbase = static_cast<size_t>(l0) * tunits * R * C;
+      for (int64_t e = 0; e < tunits * R * C; ++e) {
+        const int64_t ci = e % C, r = (e / C) % R, tu = e / (C * R);
+        const int64_t cls = (tu / fs.row_chunks) * C + ci, rc = tu % fs.row_chunks;
+        {
           int64_t sdig[rsft::kMaxDim] = {0, 0, 0, 0};
           int64_t rr = rc * R + r, cres = cls;
           for (int d = fs.d_in - 1; d >= 0; --d) {
@@ -443,9 +463,9 @@ rsft_status build_device(rsft_plan* p) {
           for (int l = 0; l < lg; ++l) {
             cplx wv(1.0, 0.0);
             for (int d = 0; d < fs.d_in; ++d) wv *= weight(l0 + l, d, sdig[d]);
-            ft[tbase + static_cast<size_t>(tu * R + r) * lg + l] =
+            ft[tbase + static_cast<size_t>(e) * lg + l] =
                 make_float4(static_cast<float>(wv.real()), static_cast<float>(wv.imag() - wv.real()),
-                            static_cast<float>(wv.real() + wv.imag()), 0.f);
+                            static_cast<float>(wv.real() + wv.imag()), static_cast<float>(wv.real() + wv.imag()));
           }
         }
       }

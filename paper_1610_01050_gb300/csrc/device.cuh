@@ -36,13 +36,16 @@ struct FoldSchedule {
   int col_chunks;         // row_len / W
   int classes;            // prod_{e < d_in} B_e
   int rows_per_class;     // prod_{e < d_in} M_e
-  int rows_per_chunk;
+  int rows_per_chunk;     // rows of each class per unit
   int row_chunks;
   int xcount;             // X: inner residues per chunk = prod_{e >= d_in} B_e
   int direct;             // 1: one chunk per class, write buckets directly
-  int red_mask;           // lane bits whose flip keeps a thread's column residues (shuffle-summed)
+  int cps;                // C: residue classes side by side in a row step (consecutive x_{d_in - 1})
+  int crow;               // rows of each class per row step (C * crow * W <= 2 * threads)
+  int groups;             // classes / C
+  int red_mask;           // lane bits whose flip keeps a thread's (class, column residue) (shuffle-summed)
   int leaders;            // lanes per warp left after the shuffle sum: 32 >> popcount(red_mask)
-  int slots_per_x;        // epilogue partial sums per residue: 2 * warps * leaders / X
+  int slots_per_x;        // epilogue partial sums per (class, residue): 2 * warps * leaders / (C X)
 };
 
 // One FFT pass over the bucket arrays: transforms dimensions [da, db) in shared memory.

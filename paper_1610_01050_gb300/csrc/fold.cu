@@ -79,9 +79,9 @@ __device__ __forceinline__ void tensor_g2s_5d(void* dst, const void* tmap, int c
       : "memory");
 }
 
-// Wait until the barrier completes the phase of the given parity.  False if the CTA
-// already gave up, or if this wait times out (then the CTA's abort flag and the global
-// error flag are set).
+// Wait until the barrier completes the phase of the given parity (try_wait suspends the
+// thread for a while on each attempt).  False if the CTA already gave up, or if this wait
+// times out (then the CTA's abort flag and the global error flag are set).
 __device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
@@ -93,18 +93,19 @@ __device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile 
       atomicExch(err, 1);
       return false;
     }
-    __nanosleep(100);
   }
 }
 
 constexpr int kThreads = kFoldConsumers;   // 256 threads, two columns each
-constexpr int kRing = 8;                   // shared-memory stages
-constexpr int kStepsPerStage = 2;          // row steps (2 * threads elements each) per stage
-constexpr int kStageElems = kStepsPerStage * 2 * kThreads;
-constexpr int kStageBytes = kStageElems * 8;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxRing = 8;                // shared-memory stages
+constexpr int kStepsPerStage = 4;          // row steps (2 * threads elements each) per stage
+constexpr int kStepElems = 2 * kThreads;
+constexpr int kStageBytes = kStepsPerStage * kStepElems * 8;
+constexpr int kSmemBudget = 110 * 1024;    // two CTAs per SM
 
 struct FoldArgs {
-  CUtensorMap tmap;       // rows of a residue class as one box (tensor mode)
+  CUtensorMap tmap;       // rows of C classes as one box (tensor mode)
   int tensor_rank;        // 0: one 1-D bulk copy per row; 3 or 5: one tensor copy per stage
   const float2* cube;
   Geometry g;
@@ -115,34 +116,72 @@ struct FoldArgs {
   float2* folded;
   float2* partial;
   int* err;
-  const float4* table;    // this loop group's row table: [class][row chunk][row][lg] (c, d - c, c + d, 0)
+  const float4* table;    // this loop group's row table: [group][row chunk][row][class][lg] (c, d - c, c + d, c + d)
   const float2* colw;     // this loop group's column weights: [col chunk][lg][W]
-  int small_colw;         // column weights staged in shared memory
-  int table_off, colw_off, red_off, bar_off;  // shared-memory layout (bytes)
+  int smem_colw;          // one column chunk: its weights staged in shared memory once
+  int ring;               // stages in the ring
+  int slot_bytes;         // data + the stage's row-table slice
+  int colw_off, red_off, bar_off;             // shared-memory layout (bytes)
   int sinvb[kMaxLoopGroup * kMaxDim];        // sigma^{-1} mod B_d of the group's loops
-  unsigned short slots[512];                  // [X][slots_per_x] epilogue partial sums per residue
+  unsigned short slots[512];                  // [C X][slots_per_x] epilogue partial sums per (class, residue)
   unsigned short xdig[2048];                  // [X][4] inner residue digits
 };
 
-// Column weights are kept per column in shared memory when they fit in 16 KiB.
-__host__ __device__ __forceinline__ bool colw_in_smem(const FoldSchedule& fs, int lg) {
-  return lg * fs.width * 8 <= 16 * 1024;
+// Stage geometry: a row step holds C classes x crow rows of W columns (rs = C crow rows);
+// spst steps form a stage, nst stages a unit.
+struct StageShape {
+  int rs, spst, nst, data_bytes, table_bytes;
+};
+
+__host__ __device__ __forceinline__ StageShape stage_shape(const FoldSchedule& fs, int lg) {
+  StageShape s;
+  s.rs = fs.cps * fs.crow;
+  const int steps = fs.rows_per_chunk / fs.crow;
+  s.spst = steps < kStepsPerStage ? steps : kStepsPerStage;
+  s.nst = steps / s.spst;
+  s.data_bytes = s.spst * s.rs * fs.width * 8;
+  s.table_bytes = s.spst * s.rs * lg * 16;
+  return s;
 }
 
-__host__ __device__ __forceinline__ int fold_layout(const FoldSchedule& fs, int lg, int* table_off, int* colw_off,
-                                                    int* red_off, int* bar_off) {
-  int off = kRing * kStageBytes;
-  *table_off = off;
-  off += fs.rows_per_chunk * lg * 16;
+// Column weights are staged once in shared memory when there is one column chunk and they
+// fit in 16 KiB; otherwise the epilogue reads them through L1.
+__host__ __device__ __forceinline__ bool colw_staged(const FoldSchedule& fs, int lg) {
+  return fs.col_chunks == 1 && lg * fs.width * 8 <= 16 * 1024;
+}
+
+// Shared memory: [ring x (stage data | stage row table)] [column weights] [epilogue partials] [barriers].
+__host__ __device__ __forceinline__ int fold_layout(const FoldSchedule& fs, int lg, int* ring, int* slot_bytes,
+                                                    int* colw_off, int* red_off, int* bar_off) {
+  const StageShape sh = stage_shape(fs, lg);
+  *slot_bytes = kStageBytes + sh.table_bytes;
+  const int colw = colw_staged(fs, lg) ? lg * fs.width * 8 : 0;
+  const int red = kWarps * fs.leaders * 2 * lg * 8;
+  const int bars = (kMaxRing + 1) * 8 + kMaxRing * 4 + 16;
+  int r = (kSmemBudget - colw - red - bars) / *slot_bytes;
+  if (r > kMaxRing) r = kMaxRing;
+  if (r < 2) r = 2;
+  *ring = r;
+  int off = r * *slot_bytes;
   *colw_off = off;
-  if (colw_in_smem(fs, lg)) off += lg * fs.width * 8;
+  off += colw;
   *red_off = off;
-  off += (kThreads / 32) * fs.leaders * 2 * lg * 8;
+  off += red;
   *bar_off = off;
-  off += (kRing + 1) * 8 + 16;
+  off += bars;
   return off;
 }
 
+// Two 64-bit shared-memory words (a table entry as two packed float pairs).
+__device__ __forceinline__ void lds_pair64(uint32_t addr, unsigned long long& lo, unsigned long long& hi) {
+  asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(lo), "=l"(hi) : "r"(addr));
+}
+
+// Persistent fold: CTA b folds units b, b + grid, b + 2 grid, ... (a unit: C classes side by
+// side, one row chunk, one column chunk).  The ring stays full across unit boundaries (the
+// next unit's rows arrive during this unit's epilogue): the last warp to finish with stage i
+// (a shared-memory count per slot) issues stage i + ring into the same slot.  Each stage
+// brings its rows and their row-table slice.
 template <int LG>
 __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant__ FoldArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -152,58 +191,63 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
   const int warp = tid >> 5, lane = tid & 31;
   const int R = fs.rows_per_chunk;
   const int W = fs.width;
-  const int RS = (2 * kThreads) >> a.log_width;             // rows per row step
-  const int rows_per_step = R < RS ? R : RS;                 // valid rows in a step
-  const int steps = R < RS ? 1 : R / RS;                     // row steps per unit
-  const int spst = steps < kStepsPerStage ? steps : kStepsPerStage;
-  const int nst = steps / spst;                              // stages per unit
+  const int C = fs.cps;
+  const StageShape sh = stage_shape(fs, LG);
+  const int RS = sh.rs, spst = sh.spst, nst = sh.nst;
+  const int ring = a.ring;
   const int chunks = fs.row_chunks * fs.col_chunks;
-  const int u = blockIdx.x;
-  const int cc = u % fs.col_chunks;
-  const int rc = (u / fs.col_chunks) % fs.row_chunks;
-  const int cls = u / chunks;
+  const int units = fs.groups * chunks;
+  const int my_units = (units - static_cast<int>(blockIdx.x) + static_cast<int>(gridDim.x) - 1) /
+                       static_cast<int>(gridDim.x);
+  const int total = my_units * nst;  // stages of this CTA
 
-  float2* ring = reinterpret_cast<float2*>(smem);
-  float4* table = reinterpret_cast<float4*>(smem + a.table_off);
   float2* colw = reinterpret_cast<float2*>(smem + a.colw_off);
   float2* red = reinterpret_cast<float2*>(smem + a.red_off);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + a.bar_off);
-  uint64_t* tbar = full + kRing;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tbar + 1);
+  uint64_t* cbar = full + kMaxRing;
+  int* released = reinterpret_cast<int*>(cbar + 1);  // [ring] warps done with the slot's stage
+  volatile int* abort_flag = released + kMaxRing;
 
   if (tid == 0) {
-    for (int i = 0; i < kRing + 1; ++i) mbar_init(full + i, 1);
+    for (int i = 0; i < ring; ++i) {
+      mbar_init(full + i, 1);
+      released[i] = 0;
+    }
+    mbar_init(cbar, 1);
     *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_init_fence();
   }
   __syncthreads();
 
   const uint64_t pol_stream = policy_evict_first();
-  // Stage k of the unit into slot k % kRing (warp 0).
-  auto issue_stage = [&](int k) {
-    const int slot = k % kRing;
-    const int s0 = k * spst;
-    const int nrows = spst * rows_per_step;
-    if (lane == 0) mbar_arrive_expect_tx(full + slot, static_cast<uint32_t>(nrows * W * 8));
-    __syncwarp();
-    float2* dst = ring + slot * kStageElems;
-    if (a.tensor_rank != 0) {
-      if (lane == 0) {
-        const int r0 = rc * R + s0 * RS;
-        if (a.tensor_rank == 3) {
-          tensor_g2s_3d(dst, &a.tmap, cc * W, cls & static_cast<int>(g.b[0] - 1), r0, full + slot, pol_stream);
-        } else {
-          const int x1 = cls & static_cast<int>(g.b[1] - 1);
-          const int x0 = (cls >> g.log_b[1]) & static_cast<int>(g.b[0] - 1);
-          tensor_g2s_5d(dst, &a.tmap, cc * W, x1, r0 & static_cast<int>(g.m[1] - 1), x0, r0 >> g.log_m[1],
-                        full + slot, pol_stream);
-        }
-      }
+  const uint64_t pol_keep = policy_evict_last();
+  // Stage i of this CTA (one thread): unit blockIdx.x + (i / nst) grid, stage i % nst of it.
+  auto issue = [&](int i) {
+    const int u = static_cast<int>(blockIdx.x) + (i / nst) * static_cast<int>(gridDim.x);
+    const int k = i % nst;
+    const int cc = u % fs.col_chunks;
+    const int rc = (u / fs.col_chunks) % fs.row_chunks;
+    const int cls0 = (u / chunks) * C;     // first class of the unit
+    const int slot = i % ring;
+    unsigned char* base = smem + slot * a.slot_bytes;
+    float2* dst = reinterpret_cast<float2*>(base);
+    mbar_arrive_expect_tx(full + slot, static_cast<uint32_t>(sh.data_bytes + sh.table_bytes));
+    const int r0 = rc * R + k * spst * fs.crow;  // first row (within each class) of the stage
+    bulk_g2s(base + kStageBytes,
+             a.table + ((static_cast<int64_t>(u / chunks) * fs.row_chunks + rc) * R + k * spst * fs.crow) * C * LG,
+             static_cast<uint32_t>(sh.table_bytes), full + slot, pol_keep);
+    if (a.tensor_rank == 3) {
+      tensor_g2s_3d(dst, &a.tmap, cc * W, cls0 & static_cast<int>(g.b[0] - 1), r0, full + slot, pol_stream);
+    } else if (a.tensor_rank == 5) {
+      const int x1 = cls0 & static_cast<int>(g.b[1] - 1);
+      const int x0 = (cls0 >> g.log_b[1]) & static_cast<int>(g.b[0] - 1);
+      tensor_g2s_5d(dst, &a.tmap, cc * W, x1, r0 & static_cast<int>(g.m[1] - 1), x0, r0 >> g.log_m[1], full + slot,
+                    pol_stream);
     } else {
-      for (int j = lane; j < nrows; j += 32) {
-        const int step = j / rows_per_step;
-        const int ro = j - step * rows_per_step;
-        int r = rc * R + (s0 + step) * RS + ro, c = cls;
+      for (int j = 0; j < spst * RS; ++j) {
+        const int step = j / RS;
+        const int ro = j - step * RS;
+        int r = r0 + step * fs.crow + ro / C, c = cls0 + ro % C;
         int64_t row = 0, stride = 1;
 #pragma unroll
         for (int d = kMaxDim - 1; d >= 0; --d) {
@@ -216,71 +260,29 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
             stride *= g.n[d];
           }
         }
-        bulk_g2s(dst + step * (2 * kThreads) + ro * W, a.cube + row * fs.row_len + static_cast<int64_t>(cc) * W,
+        bulk_g2s(dst + step * RS * W + ro * W, a.cube + row * fs.row_len + static_cast<int64_t>(cc) * W,
                  static_cast<uint32_t>(W * 8), full + slot, pol_stream);
       }
     }
   };
-  const bool small_colw = a.small_colw != 0;
-  if (warp == 0) {
-    // the unit's row table and (small) column weights, kept in L2 across frames
-    if (lane == 0) {
-      const uint64_t pol_keep = policy_evict_last();
-      const uint32_t tbytes = static_cast<uint32_t>(R * LG * 16);
-      const uint32_t cbytes = small_colw ? static_cast<uint32_t>(LG * W * 8) : 0u;
-      mbar_arrive_expect_tx(tbar, tbytes + cbytes);
-      bulk_g2s(table, a.table + static_cast<int64_t>(cls * fs.row_chunks + rc) * R * LG, tbytes, tbar, pol_keep);
-      if (small_colw) bulk_g2s(colw, a.colw + static_cast<int64_t>(cc) * LG * W, cbytes, tbar, pol_keep);
+  const bool smem_colw = a.smem_colw != 0;
+  if (tid == 0) {
+    if (smem_colw) {
+      mbar_arrive_expect_tx(cbar, static_cast<uint32_t>(LG * W * 8));
+      bulk_g2s(colw, a.colw, static_cast<uint32_t>(LG * W * 8), cbar, pol_keep);
     }
-    __syncwarp();
-    const int first = nst < kRing ? nst : kRing;
-    for (int k = 0; k < first; ++k) issue_stage(k);
+    const int first = total < ring ? total : ring;
+    for (int i = 0; i < first; ++i) issue(i);
   }
 
-  // ---- stream the stages: each thread holds columns cp, cp + 1 of rows ro, ro + RS, ...
+  // this thread: columns cp, cp + 1 of row slot ro = (class c = ro % C, row ro / C) of each step
   const int cp = (2 * tid) & (W - 1);
   const int ro = (2 * tid) >> a.log_width;
-  const bool active = ro < rows_per_step;
-  unsigned long long k12a[LG], k12b[LG];
-  float k3a[LG], k3b[LG];
-#pragma unroll
-  for (int l = 0; l < LG; ++l) {
-    k12a[l] = 0ull;
-    k12b[l] = 0ull;
-    k3a[l] = 0.f;
-    k3b[l] = 0.f;
-  }
-  bool ok = mbar_wait(tbar, 0u, abort_flag, a.err);
-  const float4* ring4 = reinterpret_cast<const float4*>(ring);
-  for (int k = 0; k < nst; ++k) {
-    const int slot = k % kRing;
-    if (ok && !mbar_wait(full + slot, static_cast<uint32_t>(k / kRing) & 1u, abort_flag, a.err)) ok = false;
-    if (ok && active) {
-      const float4* src = ring4 + slot * (kStageElems / 2) + tid;
-      const float4* tr = table + (k * spst * RS + ro) * LG;
-      for (int step = 0; step < spst; ++step) {
-        const float4 v = src[step * kThreads];
-        const unsigned long long d0 = pack2(v.x + v.y, v.x);
-        const unsigned long long d1 = pack2(v.z + v.w, v.z);
-#pragma unroll
-        for (int l = 0; l < LG; ++l) {
-          const float4 w = tr[l];
-          const unsigned long long cw = pack2(w.x, w.y);
-          k12a[l] = fma2(cw, d0, k12a[l]);
-          k3a[l] = fmaf(w.z, v.y, k3a[l]);
-          k12b[l] = fma2(cw, d1, k12b[l]);
-          k3b[l] = fmaf(w.z, v.w, k3b[l]);
-        }
-        tr += RS * LG;
-      }
-    }
-    if (k + kRing < nst) {
-      __syncthreads();  // every thread is done with the slot
-      if (warp == 0) issue_stage(k + kRing);
-    }
-  }
+  const bool active = ro < RS;
+  bool ok = true;
+  if (smem_colw) ok = mbar_wait(cbar, 0u, abort_flag, a.err);
 
-  // ---- epilogue: column weights, shuffle over residue-preserving lane bits, then across warps
+  // epilogue constants
   const int nl = fs.leaders;
   const unsigned rmask = static_cast<unsigned>(fs.red_mask);
   const bool leader = (lane & rmask) == 0;
@@ -294,70 +296,127 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
         ++bit;
       }
   }
-  const float2* cw_g = a.colw + static_cast<int64_t>(cc) * LG * W;
-#pragma unroll
-  for (int l = 0; l < LG; ++l) {
-    const float2 pa = unpack2(k12a[l]), pb = unpack2(k12b[l]);
-    float2 v0 = make_float2(pa.x - k3a[l], pa.x + pa.y);
-    float2 v1 = make_float2(pb.x - k3b[l], pb.x + pb.y);
-    const float2 w0 = small_colw ? colw[l * W + cp] : __ldg(cw_g + l * W + cp);
-    const float2 w1 = small_colw ? colw[l * W + cp + 1] : __ldg(cw_g + l * W + cp + 1);
-    v0 = (ok && active) ? cmul(w0, v0) : make_float2(0.f, 0.f);
-    v1 = (ok && active) ? cmul(w1, v1) : make_float2(0.f, 0.f);
-#pragma unroll
-    for (int b = 0; b < 5; ++b) {
-      if ((rmask >> b) & 1u) {
-        v0.x += __shfl_xor_sync(0xffffffffu, v0.x, 1 << b);
-        v0.y += __shfl_xor_sync(0xffffffffu, v0.y, 1 << b);
-        v1.x += __shfl_xor_sync(0xffffffffu, v1.x, 1 << b);
-        v1.y += __shfl_xor_sync(0xffffffffu, v1.y, 1 << b);
-      }
-    }
-    if (leader) {
-      const int slot = (warp * nl + lj) * 2;
-      red[slot * LG + l] = v0;
-      red[(slot + 1) * LG + l] = v1;
-    }
-  }
-  __syncthreads();
-
   const int X = fs.xcount;
+  const int keys = C * X;
   const int per = fs.slots_per_x;
-  for (int o = tid; o < LG * X; o += kThreads) {
-    const int l = o / X;
-    const int x = o - l * X;
-    float2 sum = make_float2(0.f, 0.f);
-    for (int k = 0; k < per; ++k) {
-      const float2 v = red[static_cast<int>(a.slots[x * per + k]) * LG + l];
-      sum.x += v.x;
-      sum.y += v.y;
-    }
-    if (fs.direct) {
-      // bucket j = sigma^{-1} x mod B per dimension (paper order)
-      int64_t j = 0;
-      int cres = cls;
-      int xo[kMaxDim];
+  const uint32_t smem_base = smem_u32(smem);
+
+  int slot = 0;
+  uint32_t parity = 0u;
+  int i = 0;  // stage counter
+  for (int q = 0; q < my_units; ++q) {
+    const int u = static_cast<int>(blockIdx.x) + q * static_cast<int>(gridDim.x);
+    const int cc = u % fs.col_chunks;
+    const int rc = (u / fs.col_chunks) % fs.row_chunks;
+    const int cls0 = (u / chunks) * C;
+    unsigned long long k12a[LG], k12b[LG], k3[LG];
 #pragma unroll
-      for (int d = kMaxDim - 1; d >= 0; --d) {
-        xo[d] = 0;
-        if (d < fs.d_in) {
-          xo[d] = cres & static_cast<int>(g.b[d] - 1);
-          cres >>= g.log_b[d];
+    for (int l = 0; l < LG; ++l) {
+      k12a[l] = 0ull;
+      k12b[l] = 0ull;
+      k3[l] = 0ull;
+    }
+    for (int k = 0; k < nst; ++k, ++i) {
+      if (ok && !mbar_try_wait(full + slot, parity) && !mbar_wait(full + slot, parity, abort_flag, a.err)) ok = false;
+      if (ok && active) {
+        const float4* src = reinterpret_cast<const float4*>(smem + slot * a.slot_bytes) + tid;
+        uint32_t tr = smem_base + static_cast<uint32_t>(slot * a.slot_bytes + kStageBytes + ro * LG * 16);
+        for (int step = 0; step < spst; ++step) {
+          const float4 v = src[step * (RS * W / 2)];
+          const unsigned long long d0 = pack2(v.x + v.y, v.x);
+          const unsigned long long d1 = pack2(v.z + v.w, v.z);
+          const unsigned long long bb = pack2(v.y, v.w);
+#pragma unroll
+          for (int l = 0; l < LG; ++l) {
+            unsigned long long cw, sw;  // (c, d - c) and (c + d, c + d)
+            lds_pair64(tr + l * 16, cw, sw);
+            k12a[l] = fma2(cw, d0, k12a[l]);
+            k12b[l] = fma2(cw, d1, k12b[l]);
+            k3[l] = fma2(sw, bb, k3[l]);
+          }
+          tr += RS * LG * 16;
         }
       }
-#pragma unroll
-      for (int d = 0; d < kMaxDim; ++d) {
-        if (d < g.ndim) {
-          const int xd = d < fs.d_in ? xo[d] : static_cast<int>(a.xdig[x * 4 + (d - fs.d_in)]);
-          const int jd = (a.sinvb[l * kMaxDim + d] * xd) & static_cast<int>(g.b[d] - 1);
-          j += static_cast<int64_t>(jd) << g.b_shift[d];
+      __syncwarp();
+      if (lane == 0 && i + ring < total) {
+        __threadfence_block();  // this warp's reads of the slot are done before it is counted
+        if (atomicAdd(released + slot, 1) == kWarps - 1) {
+          released[slot] = 0;
+          if (ok) issue(i + ring);
         }
       }
-      a.folded[static_cast<int64_t>(a.loop0 + l) * g.total_b + j] = sum;
-    } else {
-      const int ch = rc * fs.col_chunks + cc;
-      a.partial[((static_cast<int64_t>(l) * fs.classes + cls) * chunks + ch) * X + x] = sum;
+      if (++slot == ring) {
+        slot = 0;
+        parity ^= 1u;
+      }
     }
+
+    // ---- epilogue: column weights, shuffle over lane bits that keep (class, residue), then across warps
+    const float2* cw_g = a.colw + static_cast<int64_t>(cc) * LG * W;
+#pragma unroll
+    for (int l = 0; l < LG; ++l) {
+      const float2 pa = unpack2(k12a[l]), pb = unpack2(k12b[l]), p3 = unpack2(k3[l]);
+      float2 v0 = make_float2(pa.x - p3.x, pa.x + pa.y);
+      float2 v1 = make_float2(pb.x - p3.y, pb.x + pb.y);
+      const float2 w0 = smem_colw ? colw[l * W + cp] : __ldg(cw_g + l * W + cp);
+      const float2 w1 = smem_colw ? colw[l * W + cp + 1] : __ldg(cw_g + l * W + cp + 1);
+      v0 = (ok && active) ? cmul(w0, v0) : make_float2(0.f, 0.f);
+      v1 = (ok && active) ? cmul(w1, v1) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b < 5; ++b) {
+        if ((rmask >> b) & 1u) {
+          v0.x += __shfl_xor_sync(0xffffffffu, v0.x, 1 << b);
+          v0.y += __shfl_xor_sync(0xffffffffu, v0.y, 1 << b);
+          v1.x += __shfl_xor_sync(0xffffffffu, v1.x, 1 << b);
+          v1.y += __shfl_xor_sync(0xffffffffu, v1.y, 1 << b);
+        }
+      }
+      if (leader) {
+        const int sl = (warp * nl + lj) * 2;
+        red[sl * LG + l] = v0;
+        red[(sl + 1) * LG + l] = v1;
+      }
+    }
+    __syncthreads();
+    for (int o = tid; o < LG * keys; o += kThreads) {
+      const int l = o / keys;
+      const int key = o - l * keys;
+      const int x = key % X;
+      const int cls = cls0 + key / X;
+      float2 sum = make_float2(0.f, 0.f);
+      for (int k = 0; k < per; ++k) {
+        const float2 v = red[static_cast<int>(a.slots[key * per + k]) * LG + l];
+        sum.x += v.x;
+        sum.y += v.y;
+      }
+      if (fs.direct) {
+        // bucket j = sigma^{-1} x mod B per dimension (paper order)
+        int64_t j = 0;
+        int cres = cls;
+        int xo[kMaxDim];
+#pragma unroll
+        for (int d = kMaxDim - 1; d >= 0; --d) {
+          xo[d] = 0;
+          if (d < fs.d_in) {
+            xo[d] = cres & static_cast<int>(g.b[d] - 1);
+            cres >>= g.log_b[d];
+          }
+        }
+#pragma unroll
+        for (int d = 0; d < kMaxDim; ++d) {
+          if (d < g.ndim) {
+            const int xd = d < fs.d_in ? xo[d] : static_cast<int>(a.xdig[x * 4 + (d - fs.d_in)]);
+            const int jd = (a.sinvb[l * kMaxDim + d] * xd) & static_cast<int>(g.b[d] - 1);
+            j += static_cast<int64_t>(jd) << g.b_shift[d];
+          }
+        }
+        a.folded[static_cast<int64_t>(a.loop0 + l) * g.total_b + j] = sum;
+      } else {
+        const int ch = rc * fs.col_chunks + cc;
+        a.partial[((static_cast<int64_t>(l) * fs.classes + cls) * chunks + ch) * X + x] = sum;
+      }
+    }
+    __syncthreads();  // the partials are read before the next unit writes them
   }
 }
 
@@ -414,16 +473,27 @@ __global__ void fold_reduce_kernel(const ReduceArgs a) {
 template <int LG>
 cudaError_t launch_fold_lg(const FoldArgs& args, int smem, cudaStream_t stream) {
   static int cached_smem[64] = {0};
+  static int cached_grid[64] = {0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 64 || cached_smem[dev] != smem) {
     e = cudaFuncSetAttribute(fold_kernel<LG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    if (dev < 64) cached_smem[dev] = smem;
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fold_kernel<LG>, kThreads, smem);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (dev < 64) {
+      cached_smem[dev] = smem;
+      cached_grid[dev] = per_sm * sms;
+    }
   }
-  const int units = args.fs.classes * args.fs.row_chunks * args.fs.col_chunks;
-  fold_kernel<LG><<<units, kThreads, smem, stream>>>(args);
+  const int units = args.fs.groups * args.fs.row_chunks * args.fs.col_chunks;
+  const int resident = dev < 64 ? cached_grid[dev] : 2 * 152;
+  const int grid = units < resident ? units : resident;
+  fold_kernel<LG><<<grid, kThreads, smem, stream>>>(args);
   return cudaGetLastError();
 }
 
@@ -431,8 +501,8 @@ cudaError_t launch_fold_lg(const FoldArgs& args, int smem, cudaStream_t stream) 
 
 int fold_smem_bytes(const Geometry& g, const FoldSchedule& fs, int lg) {
   (void)g;
-  int a, b, c, d;
-  return fold_layout(fs, lg, &a, &b, &c, &d);
+  int a, b, c, d, e;
+  return fold_layout(fs, lg, &a, &b, &c, &d, &e);
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -463,10 +533,9 @@ int encode_fold_map(const Geometry& g, const FoldSchedule& fs, const float2* cub
   if (fs.d_in < 1 || fs.d_in > 2 || fs.width > 256) return 0;
   EncodeTiledFn fn = encode_tiled();
   if (!fn) return 0;
-  const int RS = (2 * kFoldConsumers) / fs.width;
-  const int rows_per_step = fs.rows_per_chunk < RS ? fs.rows_per_chunk : RS;
-  const int steps = fs.rows_per_chunk < RS ? 1 : fs.rows_per_chunk / RS;
-  const int nrows = (steps < kStepsPerStage ? steps : kStepsPerStage) * rows_per_step;
+  const int steps = fs.rows_per_chunk / fs.crow;
+  const int nrows = (steps < kStepsPerStage ? steps : kStepsPerStage) * fs.crow;  // rows per class per stage
+  if (fs.cps > 256) return 0;
   cuuint64_t dims[5], strides[4];
   cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
   dims[0] = static_cast<cuuint64_t>(fs.row_len);
@@ -480,7 +549,7 @@ int encode_fold_map(const Geometry& g, const FoldSchedule& fs, const float2* cub
     if (bm > 256) return 0;
     dims[rank] = static_cast<cuuint64_t>(g.b[d]);
     strides[rank - 1] = static_cast<cuuint64_t>(sd * 8);
-    box[rank] = 1;
+    box[rank] = d == fs.d_in - 1 ? static_cast<cuuint32_t>(fs.cps) : 1u;  // the C classes of a unit
     ++rank;
     dims[rank] = static_cast<cuuint64_t>(md);
     strides[rank - 1] = static_cast<cuuint64_t>(sd * g.b[d] * 8);
@@ -516,14 +585,14 @@ cudaError_t launch_fold(const Geometry& g, const FoldSchedule& fs, const DeviceT
   const int64_t rows_tab = static_cast<int64_t>(fs.classes) * fs.row_chunks * fs.rows_per_chunk;
   args.table = t.ftable + static_cast<int64_t>(loop0) * rows_tab;
   args.colw = t.fcolw + static_cast<int64_t>(loop0) * fs.col_chunks * fs.width;
-  args.small_colw = colw_in_smem(fs, lg) ? 1 : 0;
+  args.smem_colw = colw_staged(fs, lg) ? 1 : 0;
   for (int l = 0; l < kMaxLoopGroup; ++l)
     for (int d = 0; d < kMaxDim; ++d)
       args.sinvb[l * kMaxDim + d] = (l < lg && d < g.ndim) ? t.h_sinvb[(loop0 + l) * g.ndim + d] : 0;
-  const int nslots = fs.slots_per_x * fs.xcount;
+  const int nslots = fs.slots_per_x * fs.cps * fs.xcount;  // one list per (class in step, residue)
   for (int i = 0; i < nslots && i < 512; ++i) args.slots[i] = t.h_slots[i];
   for (int i = 0; i < fs.xcount * 4 && i < 2048; ++i) args.xdig[i] = t.h_xdig[i];
-  const int smem = fold_layout(fs, lg, &args.table_off, &args.colw_off, &args.red_off, &args.bar_off);
+  const int smem = fold_layout(fs, lg, &args.ring, &args.slot_bytes, &args.colw_off, &args.red_off, &args.bar_off);
   switch (lg) {
     case 1: return launch_fold_lg<1>(args, smem, stream);
     case 2: return launch_fold_lg<2>(args, smem, stream);
