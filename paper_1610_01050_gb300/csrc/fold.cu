@@ -11,23 +11,25 @@
 // the permutation only selects the weight and relabels the B outputs.
 //
 // Work split (FoldSchedule): dimensions [0, d_in) index rows, [d_in, D) columns.
-// A unit is one residue class of the row dimensions, a chunk of that class's
-// rows and a chunk of W columns.  Each consumer thread keeps two fixed adjacent
-// columns and walks the rows, so its column weights factor out of the row loop:
+// A unit is C consecutive residue classes of the row dimensions (side by side), a
+// chunk of their rows and a chunk of W columns.  Each thread keeps two fixed adjacent
+// columns of one class and walks that class's rows, so its column weights factor out
+// of the row loop:
 //     acc_l(c) = sum_rows a_l^{row}(row) r(row, c),   contribution a_l^{col}(c) acc_l(c).
 // A complex multiply-add w x r (w = c + jd, r = a + jb) is done with three real
 // multiply-adds, K1 += c (a + b), K2 += (d - c) a, K3 += (c + d) b, and
-// Re = K1 - K3, Im = K1 + K2 at the end; the row table holds (c, d - c, c + d).
+// Re = K1 - K3, Im = K1 + K2 at the end; the row table holds (c, d - c, c + d, c + d) so
+// that (K1, K2) and the K3 of both columns advance with paired FP32 multiply-adds.
 //
-// One CTA per unit, two or more CTAs per SM.  At its start a CTA requests the
-// unit's rows with TMA -- one tensor-map box per stage of a shared-memory ring
-// (the strided rows of a residue class form one box), or one 1-D bulk copy per
-// row when rows are long -- and builds the unit's row table while the copies
-// fly; mbarriers signal each stage.  The epilogue applies the column weights,
-// sums threads of equal residue with warp shuffles over the lane bits that do
-// not change the residue, then across warps in a fixed order (deterministic
-// results).  Every barrier wait is bounded in time; a wait that gives up sets
-// the plan's error flag and the CTA skips its remaining work.
+// Persistent CTAs (as many as fit, two per SM) walk the units.  TMA brings each
+// stage of a shared-memory ring -- one tensor-map box holding a few rows of the C
+// classes (or one 1-D bulk copy per row when rows are long) plus the matching slice
+// of the row table -- and an mbarrier per slot signals its arrival; the last warp to
+// finish with a slot refills it, so the next unit's rows arrive during an epilogue.
+// The epilogue applies the column weights, sums threads of equal (class, residue)
+// with warp shuffles over the lane bits that keep both, then across warps in a fixed
+// order (deterministic results).  Every barrier wait is bounded in time; a wait that
+// gives up sets the plan's error flag and the CTA skips its remaining work.
 #include <cuda.h>
 
 #include "device.cuh"
@@ -35,25 +37,6 @@
 
 namespace rsft {
 namespace {
-
-__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-
-__device__ __forceinline__ float2 unpack2(unsigned long long v) {
-  float2 r;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
-  return r;
-}
-
-__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
-                                                   unsigned long long c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
 
 __host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -170,11 +153,6 @@ __host__ __device__ __forceinline__ int fold_layout(const FoldSchedule& fs, int 
   *bar_off = off;
   off += bars;
   return off;
-}
-
-// Two 64-bit shared-memory words (a table entry as two packed float pairs).
-__device__ __forceinline__ void lds_pair64(uint32_t addr, unsigned long long& lo, unsigned long long& hi) {
-  asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(lo), "=l"(hi) : "r"(addr));
 }
 
 // Persistent fold: CTA b folds units b, b + grid, b + 2 grid, ... (a unit: C classes side by
@@ -299,7 +277,6 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
   const int X = fs.xcount;
   const int keys = C * X;
   const int per = fs.slots_per_x;
-  const uint32_t smem_base = smem_u32(smem);
 
   int slot = 0;
   uint32_t parity = 0u;
@@ -309,32 +286,34 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
     const int cc = u % fs.col_chunks;
     const int rc = (u / fs.col_chunks) % fs.row_chunks;
     const int cls0 = (u / chunks) * C;
-    unsigned long long k12a[LG], k12b[LG], k3[LG];
+    float2 k12a[LG], k12b[LG], k3[LG];
 #pragma unroll
     for (int l = 0; l < LG; ++l) {
-      k12a[l] = 0ull;
-      k12b[l] = 0ull;
-      k3[l] = 0ull;
+      k12a[l] = make_float2(0.f, 0.f);
+      k12b[l] = make_float2(0.f, 0.f);
+      k3[l] = make_float2(0.f, 0.f);
     }
     for (int k = 0; k < nst; ++k, ++i) {
       if (ok && !mbar_try_wait(full + slot, parity) && !mbar_wait(full + slot, parity, abort_flag, a.err)) ok = false;
       if (ok && active) {
         const float4* src = reinterpret_cast<const float4*>(smem + slot * a.slot_bytes) + tid;
-        uint32_t tr = smem_base + static_cast<uint32_t>(slot * a.slot_bytes + kStageBytes + ro * LG * 16);
-        for (int step = 0; step < spst; ++step) {
-          const float4 v = src[step * (RS * W / 2)];
-          const unsigned long long d0 = pack2(v.x + v.y, v.x);
-          const unsigned long long d1 = pack2(v.z + v.w, v.z);
-          const unsigned long long bb = pack2(v.y, v.w);
+        // row-table entries (c, d - c, c + d, c + d): pairs for the paired multiply-adds
+        const float4* tr = reinterpret_cast<const float4*>(smem + slot * a.slot_bytes + kStageBytes) + ro * LG;
 #pragma unroll
-          for (int l = 0; l < LG; ++l) {
-            unsigned long long cw, sw;  // (c, d - c) and (c + d, c + d)
-            lds_pair64(tr + l * 16, cw, sw);
-            k12a[l] = fma2(cw, d0, k12a[l]);
-            k12b[l] = fma2(cw, d1, k12b[l]);
-            k3[l] = fma2(sw, bb, k3[l]);
+        for (int step = 0; step < kStepsPerStage; ++step) {
+          if (step < spst) {
+            const float4 v = src[step * (RS * W / 2)];
+            const float2 d0 = make_float2(v.x + v.y, v.x);
+            const float2 d1 = make_float2(v.z + v.w, v.z);
+            const float2 bb = make_float2(v.y, v.w);
+#pragma unroll
+            for (int l = 0; l < LG; ++l) {
+              const float4 w = tr[step * RS * LG + l];
+              k12a[l] = __ffma2_rn(make_float2(w.x, w.y), d0, k12a[l]);
+              k12b[l] = __ffma2_rn(make_float2(w.x, w.y), d1, k12b[l]);
+              k3[l] = __ffma2_rn(make_float2(w.z, w.w), bb, k3[l]);
+            }
           }
-          tr += RS * LG * 16;
         }
       }
       __syncwarp();
@@ -355,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
     const float2* cw_g = a.colw + static_cast<int64_t>(cc) * LG * W;
 #pragma unroll
     for (int l = 0; l < LG; ++l) {
-      const float2 pa = unpack2(k12a[l]), pb = unpack2(k12b[l]), p3 = unpack2(k3[l]);
+      const float2 pa = k12a[l], pb = k12b[l], p3 = k3[l];
       float2 v0 = make_float2(pa.x - p3.x, pa.x + pa.y);
       float2 v1 = make_float2(pb.x - p3.y, pb.x + pb.y);
       const float2 w0 = smem_colw ? colw[l * W + cp] : __ldg(cw_g + l * W + cp);
