@@ -189,10 +189,11 @@ bool choose_vote_rows(const rsft::Geometry& g, rsft::VoteRowSchedule& vs) {
       vs.b_in = static_cast<int>(b_in);
       vs.m_in = static_cast<int>(m_in);
     }
-    // the kernel keeps a [L][N_d] bucket-offset table of each row dimension in shared memory
+    // the kernel keeps a [L][N_d] bucket-offset table (u16) of each row dimension in shared memory
     int64_t kb_words = 0;
     for (int d = 0; best >= 0 && d < vs.d_v; ++d) kb_words += static_cast<int64_t>(g.loops) * g.n[d];
-    if (best >= 0 && vs.n_in >= 16 && kb_words <= 24576) {
+    if (best >= 0 && vs.n_in >= 16 && kb_words <= 49152 && g.total_b <= 65536 &&
+        rsft::vote_rows_small_smem(g, vs, (g.total_b + 31) / 32) <= 200 * 1024) {
       vs.small = 1;
       vs.rows = g.total_n / vs.n_in;
       vs.rows_per_warp = 64;
@@ -491,7 +492,7 @@ rsft_status build_device(rsft_plan* p) {
     p->tables.fcolw = f2p;
   }
   p->tables.rowmask = nullptr;
-  p->tables.kbtab = nullptr;
+  p->tables.kb16 = nullptr;
   if (p->rows_mode && p->rows.small) {
     // candidate masks of the inner buckets of a row: bit i_in of mask[l][b] set iff the
     // inner candidates R(b, sigma_l^{-1}) (Def. 4, trailing dimensions) contain i_in
@@ -511,21 +512,31 @@ rsft_status build_device(rsft_plan* p) {
           }
           masks[static_cast<size_t>(l) * vs.b_in + b] |= 1ull << iin;
         }
+    if (vs.b_in <= 8) {
+      // per loop, the union of the candidate masks of every detection pattern of a plane
+      const int np = 1 << vs.b_in;
+      std::vector<uint64_t> pat(static_cast<size_t>(L) * np, 0ull);
+      for (int l = 0; l < L; ++l)
+        for (int q = 1; q < np; ++q)
+          for (int b = 0; b < vs.b_in; ++b)
+            if ((q >> b) & 1) pat[static_cast<size_t>(l) * np + q] |= masks[static_cast<size_t>(l) * vs.b_in + b];
+      masks.swap(pat);
+    }
     uint64_t* mp = nullptr;
     if (masks.size() % 2) masks.push_back(0ull);  // whole 16-byte units for the bulk copy
     if ((st = upload(p, &mp, masks)) != RSFT_OK) return st;
     p->tables.rowmask = mp;
-    // bucket-plane offsets of the row dimensions: ((sigma i mod N_d) >> log M_d) << b_shift_d
-    std::vector<uint32_t> kb;
+    // bucket-plane offsets of the row dimensions: ((sigma i mod N_d) >> log M_d) << b_shift_d (< B <= 65536)
+    std::vector<uint16_t> kb;
     for (int d = 0; d < vs.d_v; ++d)
       for (int l = 0; l < L; ++l)
         for (int64_t i = 0; i < h.n[d]; ++i)
-          kb.push_back(static_cast<uint32_t>((((h.sigma[l * D + d] * i) & (h.n[d] - 1)) >> p->geom.log_m[d])
+          kb.push_back(static_cast<uint16_t>((((h.sigma[l * D + d] * i) & (h.n[d] - 1)) >> p->geom.log_m[d])
                                              << p->geom.b_shift[d]));
-    while (kb.empty() || kb.size() % 4 != 0) kb.push_back(0u);  // whole 16-byte units for the bulk copy
-    uint32_t* kp = nullptr;
+    while (kb.empty() || kb.size() % 8 != 0) kb.push_back(0u);  // whole 16-byte units for the bulk copy
+    uint16_t* kp = nullptr;
     if ((st = upload(p, &kp, kb)) != RSFT_OK) return st;
-    p->tables.kbtab = kp;
+    p->tables.kb16 = kp;
   }
   // workspace
   rsft::Workspace& ws = p->ws;
@@ -567,8 +578,11 @@ rsft_status build_device(rsft_plan* p) {
   if (p->rows_mode) {
     if ((st = dev_alloc(p, &ws.warp_count, static_cast<size_t>(p->rows.warps) * 4)) != RSFT_OK) return st;
     if ((st = dev_alloc(p, &ws.warp_offset, static_cast<size_t>(p->rows.warps + 1) * 8)) != RSFT_OK) return st;
-    if (p->rows.small && (st = dev_alloc(p, &ws.row_gt, static_cast<size_t>(p->rows.rows) * 8)) != RSFT_OK)
-      return st;
+    if (p->rows.small) {
+      const size_t entries = static_cast<size_t>(p->rows.warps) * p->rows.rows_per_warp;
+      if ((st = dev_alloc(p, &ws.row_list, entries * 16)) != RSFT_OK) return st;
+      if ((st = dev_alloc(p, &ws.warp_rows, static_cast<size_t>(p->rows.warps) * 4)) != RSFT_OK) return st;
+    }
   }
   if ((st = dev_alloc(p, &p->d_count, 16)) != RSFT_OK) return st;
   ws.err_flag = reinterpret_cast<int*>(p->d_count + 1);  // [1] of the count block
@@ -674,7 +688,7 @@ rsft_status run(rsft_plan* p, const void* d_cube, cudaStream_t stream, uint64_t*
     mark(3);
     e = rsft::launch_vote_rows(g, p->rows, p->tables, ws.det_bits, ws.words_b, p->host.mu, ws.warp_count,
                                ws.warp_offset, d_located, d_located_votes, d_votes_out, p->host.desc.max_located,
-                               d_count, ws.err_flag, ws.row_gt, stream);
+                               d_count, ws.err_flag, ws.row_list, ws.warp_rows, stream);
     if (e != cudaSuccess) return cuda_fail(e, "vote_rows");
   } else {
     p->votes_dirty = true;

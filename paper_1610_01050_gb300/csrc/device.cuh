@@ -90,8 +90,9 @@ struct DeviceTables {
   const unsigned short* h_slots;
   const unsigned short* h_xdig;
   const unsigned short* x_digits;   // [X][4]: inner residue digit per inner dimension
-  const uint64_t* rowmask;          // [L][b_in]: candidate mask of each inner bucket (rows <= 64)
-  const uint32_t* kbtab;            // per row dimension d < d_v: [L][N_d] bucket offset (Def. 3) of index i_d
+  const uint64_t* rowmask;          // rows <= 64: per loop, the candidate mask of every detection pattern of a
+                                    // plane ([L][2^b_in], b_in <= 8) or of each inner bucket ([L][b_in])
+  const uint16_t* kb16;             // per row dimension d < d_v: [L][N_d] bucket offset (Def. 3) of index i_d
 };
 
 struct Workspace {
@@ -106,7 +107,8 @@ struct Workspace {
   int* err_flag;         // set by a bounded device wait that gave up
   uint32_t* warp_count;  // [row warps] vote_rows hits per warp
   uint64_t* warp_offset; // [row warps + 1]
-  uint64_t* row_gt;      // [rows] small-row vote kernel: per-row mask of votes > mu
+  ulonglong2* row_list;  // small-row vote kernel: per warp [rows_per_warp] (row, votes > mu mask)
+  uint32_t* warp_rows;   // [row warps] entries of each warp's row list
   int64_t words_b;
   int64_t segments;
   int64_t vote_words;
@@ -135,8 +137,9 @@ cudaError_t launch_vote_rows(const Geometry& g, const VoteRowSchedule& vs, const
                              const uint32_t* det_bits, int64_t words_b, int mu, uint32_t* warp_count,
                              uint64_t* warp_offset, uint64_t* located, uint8_t* located_votes,
                              uint8_t* votes_out, int64_t capacity, int64_t* d_count, int* err,
-                             uint64_t* row_gt, cudaStream_t stream);
-// Resident blocks per SM of the small-row vote kernel at this plan's shared-memory size.
+                             ulonglong2* row_list, uint32_t* warp_rows, cudaStream_t stream);
+// Shared memory and resident blocks per SM of the small-row vote kernel.
+size_t vote_rows_small_smem(const Geometry& g, const VoteRowSchedule& vs, int64_t words_b);
 cudaError_t vote_rows_small_residency(const Geometry& g, const VoteRowSchedule& vs, int64_t words_b,
                                       int* blocks_per_sm);
 

@@ -409,7 +409,9 @@ struct RowArgs {
   uint8_t* located_votes;
   uint8_t* votes_out;
   int64_t capacity;
-  uint64_t* row_gt;         // small rows: [rows] locations of the row with votes > mu (pass 0 -> pass 1)
+  int64_t* d_count;         // small rows: the total located count (written by the emit kernel)
+  ulonglong2* row_list;     // small rows, per warp [rows_per_warp]: (row, its votes > mu mask) of emitting rows
+  uint32_t* warp_rows;      // small rows: [warps] entries in the warp's row list
 };
 
 constexpr int kRowWarps = 8;
@@ -585,52 +587,160 @@ __global__ void __launch_bounds__(kRowWarps * 32) vote_rows_kernel(const RowArgs
 // [0, 16) barrier, then the bucket-offset tables, then (staged) the candidate masks
 // and the detection bitmaps.  Copy sizes are rounded up to 16 bytes; the plan pads
 // the three device arrays to match.
+// Shared-memory layout of the small-row kernels (byte offsets, all multiples of 16):
+// [0, 16) barrier, the bucket-offset tables (u16), the candidate table, the detection
+// bitmaps.  Copy sizes are rounded up to 16 bytes; the plan pads the device arrays.
 struct SmallRowLayout {
-  uint32_t kb_bytes, mask_bytes, bit_bytes;
-  uint32_t kb_off, mask_off, bit_off, queue_off, total;
-  int kb_words;
+  uint32_t kb_bytes, cand_bytes, bit_bytes;
+  uint32_t kb_off, cand_off, bit_off, total;
 };
 
 __host__ __device__ __forceinline__ uint32_t round16(uint64_t v) { return static_cast<uint32_t>((v + 15) & ~15ull); }
 
-__host__ __device__ inline SmallRowLayout small_row_layout(const Geometry& g, int d_v, int b_in, int64_t words_b,
-                                                           int staged) {
+// Candidate table: with B_in <= 8 inner buckets, per loop the union of the candidate masks
+// of every detection pattern of a plane ([L][2^B_in]); otherwise one mask per bucket.
+__host__ __device__ __forceinline__ bool pattern_table(int b_in) { return b_in <= 8; }
+
+__host__ __device__ inline SmallRowLayout small_row_layout(const Geometry& g, int d_v, int b_in, int64_t words_b) {
   SmallRowLayout s{};
-  s.kb_words = 0;
-  for (int d = 0; d < d_v; ++d) s.kb_words += g.loops * static_cast<int>(g.n[d]);
-  s.kb_bytes = round16(static_cast<uint64_t>(s.kb_words) * 4);
-  s.mask_bytes = round16(static_cast<uint64_t>(g.loops) * b_in * 8);
+  int64_t kb_words = 0;
+  for (int d = 0; d < d_v; ++d) kb_words += static_cast<int64_t>(g.loops) * g.n[d];
+  s.kb_bytes = round16(static_cast<uint64_t>(kb_words) * 2);
+  s.cand_bytes = round16(static_cast<uint64_t>(g.loops) * (pattern_table(b_in) ? (1 << b_in) : b_in) * 8);
   s.bit_bytes = round16(static_cast<uint64_t>(g.loops) * words_b * 4);
   s.kb_off = 16;
-  s.mask_off = s.kb_off + s.kb_bytes;
-  s.bit_off = s.mask_off + (staged ? s.mask_bytes : 0);
-  s.queue_off = s.bit_off + (staged ? s.bit_bytes : 0);
-  s.total = s.queue_off + kRowWarps * 64 * 8;  // per-warp FIFO of 64 row indices
+  s.cand_off = s.kb_off + s.kb_bytes;
+  s.bit_off = s.cand_off + s.cand_bytes;
+  s.total = s.bit_off + s.bit_bytes;
   return s;
 }
 
-template <int PASS>
-__global__ void __launch_bounds__(kRowWarps * 32) vote_rows_small_kernel(const RowArgs a, const uint64_t* masks,
-                                                                         const uint32_t* kbtab, int staged) {
-  extern __shared__ __align__(16) unsigned char smem_small[];
+// The tables a row count reads (shared memory, or global memory in the emit kernel).
+struct RowTables {
+  const uint16_t* kb;      // per row dimension d < d_v: [L][N_d] bucket offset of index i_d
+  const uint64_t* cand;    // [L][2^B_in] pattern unions, or [L][B_in] per-bucket masks
+  const uint32_t* bits;    // [L][words_b] detection bitmaps
+};
+
+// Votes of the n_in locations of output row `row` as 8 bit-planes (bit i of c[p] = bit p
+// of the votes of inner location i): loop l adds one vote to every candidate of the
+// detected buckets of the row's plane (Def. 4; candidates of one loop are distinct, Prop. 4).
+__device__ __forceinline__ void count_row(const RowArgs& a, const RowTables& t, int64_t row, uint64_t* c) {
   const Geometry& g = a.g;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int L = g.loops;
-  const SmallRowLayout lay = small_row_layout(g, a.d_v, a.b_in, a.words_b, staged);
-  // bucket-plane offsets of the row dimensions: kbtab[d] = [L][N_d] ((sigma i mod N_d) >> log M_d) << b_shift_d
-  int kb_off[kMaxDim];
+  const bool wide = a.b_in > 32;
+  const uint32_t pat_mask = a.b_in < 32 ? ((1u << a.b_in) - 1u) : 0xffffffffu;
+  const bool table = pattern_table(a.b_in);
+  // this row's index in each row dimension and its table row
+  int kbase[kMaxDim];
   {
+    uint64_t r = static_cast<uint64_t>(row);
     int off = 0;
 #pragma unroll
+    for (int d = 0; d < kMaxDim; ++d) kbase[d] = 0;
+#pragma unroll
+    for (int d = kMaxDim - 1; d >= 0; --d) {
+      if (d < a.d_v) {
+        kbase[d] = static_cast<int>(static_cast<uint32_t>(r) & static_cast<uint32_t>(g.n[d] - 1));
+        r >>= g.log_n[d];
+      }
+    }
+#pragma unroll
     for (int d = 0; d < kMaxDim; ++d) {
-      kb_off[d] = off;
-      if (d < a.d_v) off += L * static_cast<int>(g.n[d]);
+      if (d < a.d_v) {
+        kbase[d] += off;
+        off += L * static_cast<int>(g.n[d]);
+      }
     }
   }
+#pragma unroll
+  for (int p = 0; p < 8; ++p) c[p] = 0ull;
+  for (int l = 0; l < L; ++l) {
+    uint32_t kb = 0u;
+#pragma unroll
+    for (int d = 0; d < kMaxDim; ++d)
+      if (d < a.d_v) kb += t.kb[kbase[d] + l * static_cast<int>(g.n[d])];
+    const uint32_t* bl = t.bits + static_cast<int64_t>(l) * a.words_b;
+    uint64_t pat = (bl[kb >> 5] >> (kb & 31u)) & pat_mask;
+    if (wide) pat |= static_cast<uint64_t>(bl[(kb >> 5) + 1]) << 32;
+    if (!pat) continue;
+    uint64_t m;
+    if (table) {
+      m = t.cand[(l << a.b_in) + static_cast<int>(pat)];
+    } else {
+      m = 0ull;
+      const uint64_t* ml = t.cand + static_cast<int64_t>(l) * a.b_in;
+      while (pat) {
+        m |= ml[__ffsll(static_cast<long long>(pat)) - 1];
+        pat &= pat - 1;
+      }
+    }
+    uint64_t carry = m;
+    for (int p = 0; p < 8 && carry; ++p) {
+      const uint64_t tt = c[p] & carry;
+      c[p] ^= carry;
+      carry = tt;
+    }
+  }
+}
+
+// Locations of the row with votes > mu, bit-sliced.
+__device__ __forceinline__ uint64_t above_mu(const RowArgs& a, const uint64_t* c) {
+  uint64_t eq = ~0ull, gt = 0ull;
+#pragma unroll
+  for (int p = 7; p >= 0; --p) {
+    if ((a.mu >> p) & 1) {
+      eq &= c[p];
+    } else {
+      gt |= eq & c[p];
+      eq &= ~c[p];
+    }
+  }
+  return gt & (a.n_in >= 64 ? ~0ull : ((1ull << a.n_in) - 1ull));
+}
+
+__device__ __forceinline__ uint8_t votes_of(const uint64_t* c, int bit) {
+  uint32_t v = 0;
+#pragma unroll
+  for (int p = 0; p < 8; ++p) v |= static_cast<uint32_t>((c[p] >> bit) & 1ull) << p;
+  return static_cast<uint8_t>(v);
+}
+
+// Write the located indices (and votes) of one row per lane, in lane order, from `pos`.
+__device__ __forceinline__ uint64_t write_rows(const RowArgs& a, int lane, int64_t row, uint64_t gt, const uint64_t* c,
+                                               uint64_t pos) {
+  const int h = __popcll(gt);
+  int incl = h;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int tot = __shfl_sync(0xffffffffu, incl, 31);
+  uint64_t out = pos + static_cast<uint64_t>(incl - h);
+  uint64_t rem = gt;
+  while (rem) {
+    const int bit = __ffsll(static_cast<long long>(rem)) - 1;
+    rem &= rem - 1;
+    if (out < static_cast<uint64_t>(a.capacity)) {
+      a.located[out] = static_cast<uint64_t>(row * a.n_in + bit);
+      if (a.located_votes) a.located_votes[out] = votes_of(c, bit);
+    }
+    ++out;
+  }
+  return pos + static_cast<uint64_t>(tot);
+}
+
+// Small rows (<= 64 locations), one lane per row with 8 bit-planes of u64 counters.
+// PASS 0: count every row, list the rows with votes > mu (row, mask) per warp, count hits.
+// PASS 1 (the full vote array only): recount every row, write located indices in order
+// from the scanned warp offsets, and every row's votes.
+template <int PASS>
+__global__ void __launch_bounds__(kRowWarps * 32) vote_rows_small_kernel(const RowArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_small[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const SmallRowLayout lay = small_row_layout(a.g, a.d_v, a.b_in, a.words_b);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_small);
-  const uint32_t* skb = reinterpret_cast<const uint32_t*>(smem_small + lay.kb_off);
-  const uint32_t* bits = staged ? reinterpret_cast<const uint32_t*>(smem_small + lay.bit_off) : a.det_bits;
-  const uint64_t* mk = staged ? reinterpret_cast<const uint64_t*>(smem_small + lay.mask_off) : masks;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     mbar_init_fence();
@@ -638,175 +748,90 @@ __global__ void __launch_bounds__(kRowWarps * 32) vote_rows_small_kernel(const R
   __syncthreads();
   if (threadIdx.x == 0) {
     const uint64_t pol = policy_evict_last();
-    const uint32_t bytes = lay.kb_bytes + (staged ? lay.mask_bytes + lay.bit_bytes : 0u);
-    mbar_arrive_expect_tx(bar, bytes);
-    if (lay.kb_bytes) bulk_g2s(smem_small + lay.kb_off, kbtab, lay.kb_bytes, bar, pol);  // none when d_v == 0
-    if (staged) {
-      bulk_g2s(smem_small + lay.mask_off, masks, lay.mask_bytes, bar, pol);
-      bulk_g2s(smem_small + lay.bit_off, a.det_bits, lay.bit_bytes, bar, pol);
-    }
+    mbar_arrive_expect_tx(bar, lay.kb_bytes + lay.cand_bytes + lay.bit_bytes);
+    if (lay.kb_bytes) bulk_g2s(smem_small + lay.kb_off, a.t.kb16, lay.kb_bytes, bar, pol);  // none when d_v == 0
+    bulk_g2s(smem_small + lay.cand_off, a.t.rowmask, lay.cand_bytes, bar, pol);
+    bulk_g2s(smem_small + lay.bit_off, a.det_bits, lay.bit_bytes, bar, pol);
   }
   if (!mbar_wait_bounded(bar, 0u, a.err)) return;  // no block-wide barriers below
   const int64_t gw = static_cast<int64_t>(blockIdx.x) * kRowWarps + wid;
   if (gw >= a.warps) return;
-  int64_t* queue = reinterpret_cast<int64_t*>(smem_small + lay.queue_off) + wid * 64;
-  const uint64_t valid_bits = a.n_in >= 64 ? ~0ull : ((1ull << a.n_in) - 1ull);
-  const bool full = PASS == 1 && a.votes_out != nullptr;
-  const bool wide = a.b_in > 32;
-  const uint32_t pat_mask = a.b_in < 32 ? ((1u << a.b_in) - 1u) : 0xffffffffu;
-
-  // bucket-plane offset of `row` in loop l, from the per-dimension tables
-  auto plane = [&](int64_t row, int l) -> uint32_t {
-    uint64_t r = static_cast<uint64_t>(row);
-    uint32_t kb = 0u;
-#pragma unroll
-    for (int d = kMaxDim - 1; d >= 0; --d) {
-      if (d < a.d_v) {
-        kb += skb[kb_off[d] + l * static_cast<int>(g.n[d]) +
-                  (static_cast<uint32_t>(r) & static_cast<uint32_t>(g.n[d] - 1))];
-        r >>= g.log_n[d];
-      }
-    }
-    return kb;
-  };
-  // bit-sliced vote counters of the row's n_in locations (bit p of every location in c[p])
-  auto count = [&](int64_t row, uint64_t* c) {
-#pragma unroll
-    for (int p = 0; p < 8; ++p) c[p] = 0ull;
-    for (int l = 0; l < L; ++l) {
-      const uint32_t kb = plane(row, l);
-      const uint32_t* bl = bits + static_cast<int64_t>(l) * a.words_b;
-      uint64_t pat = (bl[kb >> 5] >> (kb & 31u)) & pat_mask;
-      if (wide) pat |= static_cast<uint64_t>(bl[(kb >> 5) + 1]) << 32;
-      if (!pat) continue;
-      uint64_t m = 0ull;
-      const uint64_t* ml = mk + static_cast<int64_t>(l) * a.b_in;
-      while (pat) {
-        m |= ml[__ffsll(static_cast<long long>(pat)) - 1];
-        pat &= pat - 1;
-      }
-      uint64_t carry = m;
-      for (int p = 0; p < 8 && carry; ++p) {
-        const uint64_t t = c[p] & carry;
-        c[p] ^= carry;
-        carry = t;
-      }
-    }
-  };
-  // votes > mu, bit-sliced
-  auto above = [&](const uint64_t* c) -> uint64_t {
-    uint64_t eq = ~0ull, gt = 0ull;
-#pragma unroll
-    for (int p = 7; p >= 0; --p) {
-      if ((a.mu >> p) & 1) {
-        eq &= c[p];
-      } else {
-        gt |= eq & c[p];
-        eq &= ~c[p];
-      }
-    }
-    return gt & valid_bits;
-  };
-
-  uint64_t pos = PASS == 1 ? a.warp_offset[gw] : 0ull;
-  uint32_t hits = 0;
-  int head = 0, queued = 0;  // FIFO of rows (ascending) that need their votes counted
-  // Count the votes of up to 32 queued rows, one per lane, in queue order.
-  auto drain = [&](int take) {
-    const bool act = lane < take;
-    const int64_t row = act ? queue[(head + lane) & 63] : 0;
-    uint64_t c[8];
-    uint64_t gt = 0ull;
-    if (PASS == 0) {
-      if (act) {
-        count(row, c);
-        gt = above(c);
-        a.row_gt[row] = gt;
-      }
-      hits += static_cast<uint32_t>(__popcll(gt));
-    } else {
-      if (act) {
-        gt = full ? 0ull : a.row_gt[row];
-        if (full || a.located_votes) {
-          count(row, c);
-          if (full) gt = above(c);
-        }
-      }
-      const int h = __popcll(gt);
-      int incl = h;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const int tot = __shfl_sync(0xffffffffu, incl, 31);
-      uint64_t out = pos + static_cast<uint64_t>(incl - h);
-      uint64_t rem = gt;
-      while (rem) {
-        const int bit = __ffsll(static_cast<long long>(rem)) - 1;
-        rem &= rem - 1;
-        if (out < static_cast<uint64_t>(a.capacity)) {
-          a.located[out] = static_cast<uint64_t>(row * a.n_in + bit);
-          if (a.located_votes) {
-            uint32_t v = 0;
-#pragma unroll
-            for (int p = 0; p < 8; ++p) v |= static_cast<uint32_t>((c[p] >> bit) & 1ull) << p;
-            a.located_votes[out] = static_cast<uint8_t>(v);
-          }
-        }
-        ++out;
-      }
-      pos += static_cast<uint64_t>(tot);
-      if (full && act) {
-        for (int bit = 0; bit < a.n_in; ++bit) {
-          uint32_t v = 0;
-#pragma unroll
-          for (int p = 0; p < 8; ++p) v |= static_cast<uint32_t>((c[p] >> bit) & 1ull) << p;
-          a.votes_out[row * a.n_in + bit] = static_cast<uint8_t>(v);
-        }
-      }
-    }
-    head = (head + take) & 63;
-    queued -= take;
-  };
-
+  RowTables t;
+  t.kb = reinterpret_cast<const uint16_t*>(smem_small + lay.kb_off);
+  t.cand = reinterpret_cast<const uint64_t*>(smem_small + lay.cand_off);
+  t.bits = reinterpret_cast<const uint32_t*>(smem_small + lay.bit_off);
   const int64_t row0 = gw * a.rows_per_warp;
+  ulonglong2* list = a.row_list + row0;
+  uint64_t pos = PASS == 1 ? a.warp_offset[gw] : 0ull;
+  uint32_t hits = 0, nlist = 0;
   for (int rb = 0; rb < a.rows_per_warp; rb += 32) {
     const int64_t row = row0 + rb + lane;
     const bool valid = rb + lane < a.rows_per_warp && row < a.rows;
-    bool take = false;
-    if (PASS == 0) {
-      // how many loops hold a detection in this row's planes; a row with at most mu
-      // of them cannot pass the second stage
-      int nz = 0;
-      if (valid) {
-        for (int l = 0; l < L; ++l) {
-          const uint32_t kb = plane(row, l);
-          const uint32_t* bl = bits + static_cast<int64_t>(l) * a.words_b;
-          bool any = ((bl[kb >> 5] >> (kb & 31u)) & pat_mask) != 0u;
-          if (wide) any = any || bl[(kb >> 5) + 1] != 0u;
-          nz += any ? 1 : 0;
-        }
-      }
-      take = valid && nz > a.mu;
-      if (valid && !take) a.row_gt[row] = 0ull;
-    } else {
-      take = valid && (full || a.row_gt[row] != 0ull);
+    uint64_t c[8];
+    uint64_t gt = 0ull;
+    if (valid) {
+      count_row(a, t, row, c);
+      gt = above_mu(a, c);
     }
-    const unsigned bal = __ballot_sync(0xffffffffu, take);
-    if (take) queue[(head + queued + __popc(bal & ((1u << lane) - 1u))) & 63] = row;
-    __syncwarp();
-    queued += __popc(bal);
-    if (queued >= 32) {
-      drain(32);
-      __syncwarp();
+    if (PASS == 0) {
+      hits += static_cast<uint32_t>(__popcll(gt));
+      const unsigned emit = __ballot_sync(0xffffffffu, gt != 0ull);
+      if (gt != 0ull) list[nlist + __popc(emit & ((1u << lane) - 1u))] = make_ulonglong2(static_cast<uint64_t>(row), gt);
+      nlist += static_cast<uint32_t>(__popc(emit));
+    } else {
+      pos = write_rows(a, lane, row, gt, c, pos);
+      if (valid)
+        for (int bit = 0; bit < a.n_in; ++bit) a.votes_out[row * a.n_in + bit] = votes_of(c, bit);
     }
   }
-  if (queued > 0) drain(queued);
   if (PASS == 0) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) hits += __shfl_xor_sync(0xffffffffu, hits, o);
-    if (lane == 0) a.warp_count[gw] = hits;
+    if (lane == 0) {
+      a.warp_count[gw] = hits;
+      a.warp_rows[gw] = nlist;
+    }
+  }
+}
+
+// Second stage of the small-row path: block b writes the located indices of warps
+// [8b, 8b + 8) of the count pass, in ascending order.  Its output offset is the sum of the
+// counts of all earlier warps (each block sums them itself: no separate scan).  Votes of
+// the located indices, when asked for, are recounted from the global tables.
+__global__ void __launch_bounds__(kRowWarps * 32) emit_rows_kernel(const RowArgs a, RowTables gt_tables) {
+  __shared__ unsigned long long red[kRowWarps];
+  __shared__ unsigned long long warp_pos[kRowWarps];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t first = static_cast<int64_t>(blockIdx.x) * kRowWarps;
+  unsigned long long s = 0ull;
+  for (int64_t w = threadIdx.x; w < first; w += kRowWarps * 32) s += a.warp_count[w];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) red[wid] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long base = 0ull;
+    for (int w = 0; w < kRowWarps; ++w) base += red[w];
+    for (int w = 0; w < kRowWarps; ++w) {
+      warp_pos[w] = base;
+      if (first + w < a.warps) base += a.warp_count[first + w];
+    }
+    if (first + kRowWarps >= a.warps) *a.d_count = static_cast<int64_t>(base);  // the last block: the total
+  }
+  __syncthreads();
+  const int64_t gw = first + wid;
+  if (gw >= a.warps) return;
+  const int n = static_cast<int>(a.warp_rows[gw]);
+  const ulonglong2* list = a.row_list + gw * a.rows_per_warp;
+  uint64_t pos = warp_pos[wid];
+  for (int base = 0; base < n; base += 32) {
+    const bool act = base + lane < n;
+    const ulonglong2 e = act ? list[base + lane] : make_ulonglong2(0ull, 0ull);
+    uint64_t c[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) c[p] = 0ull;
+    if (act && a.located_votes) count_row(a, gt_tables, static_cast<int64_t>(e.x), c);
+    pos = write_rows(a, lane, static_cast<int64_t>(e.x), e.y, c, pos);
   }
 }
 
@@ -849,13 +874,9 @@ cudaError_t launch_stage2(const Geometry& g, int mu, Workspace& ws, uint64_t* lo
   return cudaGetLastError();
 }
 
-// Shared memory of the small-row kernel (staging the masks and bitmaps when they fit),
-// with the kernels' dynamic shared-memory limit raised to match.
-static cudaError_t small_rows_smem(const Geometry& g, const VoteRowSchedule& vs, int64_t words_b, int* staged,
-                            size_t* smem) {
-  const SmallRowLayout full = small_row_layout(g, vs.d_v, vs.b_in, words_b, 1);
-  *staged = full.total <= 160 * 1024 ? 1 : 0;
-  *smem = *staged ? full.total : small_row_layout(g, vs.d_v, vs.b_in, words_b, 0).total;
+// Shared memory of the small-row kernels, with their dynamic shared-memory limit raised to match.
+static cudaError_t small_rows_smem(const Geometry& g, const VoteRowSchedule& vs, int64_t words_b, size_t* smem) {
+  *smem = small_row_layout(g, vs.d_v, vs.b_in, words_b).total;
   cudaError_t e = cudaFuncSetAttribute(vote_rows_small_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(*smem));
   if (e == cudaSuccess)
@@ -864,13 +885,16 @@ static cudaError_t small_rows_smem(const Geometry& g, const VoteRowSchedule& vs,
   return e;
 }
 
+size_t vote_rows_small_smem(const Geometry& g, const VoteRowSchedule& vs, int64_t words_b) {
+  return small_row_layout(g, vs.d_v, vs.b_in, words_b).total;
+}
+
 cudaError_t vote_rows_small_residency(const Geometry& g, const VoteRowSchedule& vs, int64_t words_b,
                                       int* blocks_per_sm) {
-  int staged = 0;
   size_t smem = 0;
-  cudaError_t e = small_rows_smem(g, vs, words_b, &staged, &smem);
+  cudaError_t e = small_rows_smem(g, vs, words_b, &smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, vote_rows_small_kernel<1>, kRowWarps * 32,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, vote_rows_small_kernel<0>, kRowWarps * 32,
                                                        smem);
 }
 
@@ -878,7 +902,7 @@ cudaError_t launch_vote_rows(const Geometry& g, const VoteRowSchedule& vs, const
                              const uint32_t* det_bits, int64_t words_b, int mu, uint32_t* warp_count,
                              uint64_t* warp_offset, uint64_t* located, uint8_t* located_votes,
                              uint8_t* votes_out, int64_t capacity, int64_t* d_count, int* err,
-                             uint64_t* row_gt, cudaStream_t stream) {
+                             ulonglong2* row_list, uint32_t* warp_rows, cudaStream_t stream) {
   if (vs.small) {
     RowArgs a;
     a.g = g;
@@ -900,19 +924,29 @@ cudaError_t launch_vote_rows(const Geometry& g, const VoteRowSchedule& vs, const
     a.votes_out = votes_out;
     a.capacity = capacity;
     a.err = err;
-    a.row_gt = row_gt;
+    a.row_list = row_list;
+    a.warp_rows = warp_rows;
+    a.d_count = d_count;
     const unsigned blocks = static_cast<unsigned>((vs.warps + kRowWarps - 1) / kRowWarps);
-    int staged = 0;
     size_t smem = 0;
-    cudaError_t e = small_rows_smem(g, vs, words_b, &staged, &smem);
+    cudaError_t e = small_rows_smem(g, vs, words_b, &smem);
     if (e != cudaSuccess) return e;
-    vote_rows_small_kernel<0><<<blocks, kRowWarps * 32, smem, stream>>>(a, t.rowmask, t.kbtab, staged);
+    vote_rows_small_kernel<0><<<blocks, kRowWarps * 32, smem, stream>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    stage2_scan_kernel<<<1, 1024, 0, stream>>>(warp_count, vs.warps, warp_offset, d_count);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    vote_rows_small_kernel<1><<<blocks, kRowWarps * 32, smem, stream>>>(a, t.rowmask, t.kbtab, staged);
+    if (votes_out) {
+      // the full vote array: scan the warp counts, recount and write every row
+      stage2_scan_kernel<<<1, 1024, 0, stream>>>(warp_count, vs.warps, warp_offset, d_count);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      vote_rows_small_kernel<1><<<blocks, kRowWarps * 32, smem, stream>>>(a);
+      return cudaGetLastError();
+    }
+    RowTables gtab;
+    gtab.kb = t.kb16;
+    gtab.cand = t.rowmask;
+    gtab.bits = det_bits;
+    emit_rows_kernel<<<blocks, kRowWarps * 32, 0, stream>>>(a, gtab);
     return cudaGetLastError();
   }
   RowArgs a;
