@@ -569,7 +569,7 @@ rsft_status build_device(rsft_plan* p) {
     cudaError_t oe = rsft::vote_rows_small_residency(g, p->rows, ws.words_b, &per_sm);
     if (oe == cudaSuccess) oe = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
     if (oe != cudaSuccess) return cuda_fail(oe, "vote kernel residency");
-    const int64_t resident_warps = static_cast<int64_t>(std::max(per_sm, 1)) * sms * 8;
+    const int64_t resident_warps = static_cast<int64_t>(std::max(per_sm, 8)) * sms;
     int64_t rpw = (p->rows.rows + resident_warps - 1) / resident_warps;
     rpw = std::max<int64_t>(32, (rpw + 31) / 32 * 32);
     p->rows.rows_per_warp = static_cast<int>(rpw);

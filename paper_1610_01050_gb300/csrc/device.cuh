@@ -141,7 +141,7 @@ cudaError_t launch_vote_rows(const Geometry& g, const VoteRowSchedule& vs, const
 // Shared memory and resident blocks per SM of the small-row vote kernel.
 size_t vote_rows_small_smem(const Geometry& g, const VoteRowSchedule& vs, int64_t words_b);
 cudaError_t vote_rows_small_residency(const Geometry& g, const VoteRowSchedule& vs, int64_t words_b,
-                                      int* blocks_per_sm);
+                                      int* warps_per_sm);
 
 int fold_smem_bytes(const Geometry& g, const FoldSchedule& fs, int lg);
 

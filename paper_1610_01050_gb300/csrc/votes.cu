@@ -622,45 +622,45 @@ struct RowTables {
   const uint32_t* bits;    // [L][words_b] detection bitmaps
 };
 
-// Votes of the n_in locations of output row `row` as 8 bit-planes (bit i of c[p] = bit p
-// of the votes of inner location i): loop l adds one vote to every candidate of the
-// detected buckets of the row's plane (Def. 4; candidates of one loop are distinct, Prop. 4).
+// Votes of the n_in locations of output row `row` as bit-planes (bit i of c[p] = bit p of
+// the votes of inner location i; NP planes are counted, the rest stay 0): loop l adds one
+// vote to every candidate of the detected buckets of the row's plane (Def. 4; candidates
+// of one loop are distinct, Prop. 4).  DV = number of row dimensions.
+template <int DV, int NP>
 __device__ __forceinline__ void count_row(const RowArgs& a, const RowTables& t, int64_t row, uint64_t* c) {
   const Geometry& g = a.g;
   const int L = g.loops;
   const bool wide = a.b_in > 32;
   const uint32_t pat_mask = a.b_in < 32 ? ((1u << a.b_in) - 1u) : 0xffffffffu;
   const bool table = pattern_table(a.b_in);
-  // this row's index in each row dimension and its table row
-  int kbase[kMaxDim];
+  const uint16_t* kp[DV > 0 ? DV : 1];
+  int kn[DV > 0 ? DV : 1];
   {
     uint64_t r = static_cast<uint64_t>(row);
+    int idx[DV > 0 ? DV : 1];
+#pragma unroll
+    for (int d = DV - 1; d >= 0; --d) {
+      idx[d] = static_cast<int>(static_cast<uint32_t>(r) & static_cast<uint32_t>(g.n[d] - 1));
+      r >>= g.log_n[d];
+    }
     int off = 0;
 #pragma unroll
-    for (int d = 0; d < kMaxDim; ++d) kbase[d] = 0;
-#pragma unroll
-    for (int d = kMaxDim - 1; d >= 0; --d) {
-      if (d < a.d_v) {
-        kbase[d] = static_cast<int>(static_cast<uint32_t>(r) & static_cast<uint32_t>(g.n[d] - 1));
-        r >>= g.log_n[d];
-      }
-    }
-#pragma unroll
-    for (int d = 0; d < kMaxDim; ++d) {
-      if (d < a.d_v) {
-        kbase[d] += off;
-        off += L * static_cast<int>(g.n[d]);
-      }
+    for (int d = 0; d < DV; ++d) {
+      kp[d] = t.kb + off + idx[d];
+      kn[d] = static_cast<int>(g.n[d]);
+      off += L * kn[d];
     }
   }
 #pragma unroll
   for (int p = 0; p < 8; ++p) c[p] = 0ull;
-  for (int l = 0; l < L; ++l) {
+  const uint32_t* bl = t.bits;
+  for (int l = 0; l < L; ++l, bl += a.words_b) {
     uint32_t kb = 0u;
 #pragma unroll
-    for (int d = 0; d < kMaxDim; ++d)
-      if (d < a.d_v) kb += t.kb[kbase[d] + l * static_cast<int>(g.n[d])];
-    const uint32_t* bl = t.bits + static_cast<int64_t>(l) * a.words_b;
+    for (int d = 0; d < DV; ++d) {
+      kb += *kp[d];
+      kp[d] += kn[d];
+    }
     uint64_t pat = (bl[kb >> 5] >> (kb & 31u)) & pat_mask;
     if (wide) pat |= static_cast<uint64_t>(bl[(kb >> 5) + 1]) << 32;
     if (!pat) continue;
@@ -675,11 +675,11 @@ __device__ __forceinline__ void count_row(const RowArgs& a, const RowTables& t, 
         pat &= pat - 1;
       }
     }
-    uint64_t carry = m;
-    for (int p = 0; p < 8 && carry; ++p) {
-      const uint64_t tt = c[p] & carry;
-      c[p] ^= carry;
-      carry = tt;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const uint64_t tt = c[p] & m;
+      c[p] ^= m;
+      m = tt;
     }
   }
 }
@@ -735,8 +735,10 @@ __device__ __forceinline__ uint64_t write_rows(const RowArgs& a, int lane, int64
 // PASS 0: count every row, list the rows with votes > mu (row, mask) per warp, count hits.
 // PASS 1 (the full vote array only): recount every row, write located indices in order
 // from the scanned warp offsets, and every row's votes.
-template <int PASS>
-__global__ void __launch_bounds__(kRowWarps * 32) vote_rows_small_kernel(const RowArgs a) {
+constexpr int kSmallWarps = 16;
+
+template <int PASS, int DV, int NP>
+__global__ void __launch_bounds__(kSmallWarps * 32) vote_rows_small_kernel(const RowArgs a) {
   extern __shared__ __align__(16) unsigned char smem_small[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const SmallRowLayout lay = small_row_layout(a.g, a.d_v, a.b_in, a.words_b);
@@ -754,7 +756,7 @@ __global__ void __launch_bounds__(kRowWarps * 32) vote_rows_small_kernel(const R
     bulk_g2s(smem_small + lay.bit_off, a.det_bits, lay.bit_bytes, bar, pol);
   }
   if (!mbar_wait_bounded(bar, 0u, a.err)) return;  // no block-wide barriers below
-  const int64_t gw = static_cast<int64_t>(blockIdx.x) * kRowWarps + wid;
+  const int64_t gw = static_cast<int64_t>(blockIdx.x) * kSmallWarps + wid;
   if (gw >= a.warps) return;
   RowTables t;
   t.kb = reinterpret_cast<const uint16_t*>(smem_small + lay.kb_off);
@@ -770,7 +772,7 @@ __global__ void __launch_bounds__(kRowWarps * 32) vote_rows_small_kernel(const R
     uint64_t c[8];
     uint64_t gt = 0ull;
     if (valid) {
-      count_row(a, t, row, c);
+      count_row<DV, NP>(a, t, row, c);
       gt = above_mu(a, c);
     }
     if (PASS == 0) {
@@ -796,41 +798,55 @@ __global__ void __launch_bounds__(kRowWarps * 32) vote_rows_small_kernel(const R
 
 // Second stage of the small-row path: block b writes the located indices of warps
 // [8b, 8b + 8) of the count pass, in ascending order.  Its output offset is the sum of the
-// counts of all earlier warps (each block sums them itself: no separate scan).  Votes of
-// the located indices, when asked for, are recounted from the global tables.
+// counts of all earlier warps (each block sums them itself: no separate scan).  Every load
+// is issued up front.  Votes of the located indices, when asked for, are recounted from
+// the global tables.
+template <int DV, int NP>
 __global__ void __launch_bounds__(kRowWarps * 32) emit_rows_kernel(const RowArgs a, RowTables gt_tables) {
   __shared__ unsigned long long red[kRowWarps];
+  __shared__ unsigned int wcnt[kRowWarps];
   __shared__ unsigned long long warp_pos[kRowWarps];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t first = static_cast<int64_t>(blockIdx.x) * kRowWarps;
+  const int64_t gw = first + wid;
+  const bool live = gw < a.warps;
+  const ulonglong2* list = a.row_list + (live ? gw : 0) * a.rows_per_warp;
+  // speculative: the first 32 entries of the warp's list (the list has rows_per_warp >= 32 slots)
+  const ulonglong2 e0 = live ? list[lane] : make_ulonglong2(0ull, 0ull);
+  const unsigned int n = live ? a.warp_rows[gw] : 0u;
+  if (lane == 0) wcnt[wid] = live ? a.warp_count[gw] : 0u;
   unsigned long long s = 0ull;
+#pragma unroll 8
   for (int64_t w = threadIdx.x; w < first; w += kRowWarps * 32) s += a.warp_count[w];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) red[wid] = s;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long base = 0ull;
-    for (int w = 0; w < kRowWarps; ++w) base += red[w];
-    for (int w = 0; w < kRowWarps; ++w) {
-      warp_pos[w] = base;
-      if (first + w < a.warps) base += a.warp_count[first + w];
+  if (wid == 0) {
+    unsigned long long base = lane < kRowWarps ? red[lane] : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) base += __shfl_xor_sync(0xffffffffu, base, o);
+    const unsigned long long v = lane < kRowWarps ? wcnt[lane] : 0ull;
+    unsigned long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
     }
-    if (first + kRowWarps >= a.warps) *a.d_count = static_cast<int64_t>(base);  // the last block: the total
+    if (lane < kRowWarps) warp_pos[lane] = base + incl - v;
+    if (lane == kRowWarps - 1 && first + kRowWarps >= a.warps) *a.d_count = static_cast<int64_t>(base + incl);
   }
   __syncthreads();
-  const int64_t gw = first + wid;
-  if (gw >= a.warps) return;
-  const int n = static_cast<int>(a.warp_rows[gw]);
-  const ulonglong2* list = a.row_list + gw * a.rows_per_warp;
+  if (!live) return;
   uint64_t pos = warp_pos[wid];
-  for (int base = 0; base < n; base += 32) {
-    const bool act = base + lane < n;
-    const ulonglong2 e = act ? list[base + lane] : make_ulonglong2(0ull, 0ull);
+  for (int base = 0; base < static_cast<int>(n); base += 32) {
+    const bool act = base + lane < static_cast<int>(n);
+    const ulonglong2 e = base == 0 ? (act ? e0 : make_ulonglong2(0ull, 0ull))
+                                   : (act ? list[base + lane] : make_ulonglong2(0ull, 0ull));
     uint64_t c[8];
 #pragma unroll
     for (int p = 0; p < 8; ++p) c[p] = 0ull;
-    if (act && a.located_votes) count_row(a, gt_tables, static_cast<int64_t>(e.x), c);
+    if (act && a.located_votes) count_row<DV, NP>(a, gt_tables, static_cast<int64_t>(e.x), c);
     pos = write_rows(a, lane, static_cast<int64_t>(e.x), e.y, c, pos);
   }
 }
@@ -874,15 +890,47 @@ cudaError_t launch_stage2(const Geometry& g, int mu, Workspace& ws, uint64_t* lo
   return cudaGetLastError();
 }
 
+template <int DV, int NP>
+cudaError_t small_rows_attr(size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(vote_rows_small_kernel<0, DV, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(vote_rows_small_kernel<1, DV, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem));
+  return e;
+}
+
 // Shared memory of the small-row kernels, with their dynamic shared-memory limit raised to match.
 static cudaError_t small_rows_smem(const Geometry& g, const VoteRowSchedule& vs, int64_t words_b, size_t* smem) {
   *smem = small_row_layout(g, vs.d_v, vs.b_in, words_b).total;
-  cudaError_t e = cudaFuncSetAttribute(vote_rows_small_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(*smem));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(vote_rows_small_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(*smem));
+  cudaError_t e = small_rows_attr<0, 8>(*smem);
+  if (e == cudaSuccess) e = small_rows_attr<0, 4>(*smem);
+  if (e == cudaSuccess) e = small_rows_attr<1, 8>(*smem);
+  if (e == cudaSuccess) e = small_rows_attr<1, 4>(*smem);
+  if (e == cudaSuccess) e = small_rows_attr<2, 8>(*smem);
+  if (e == cudaSuccess) e = small_rows_attr<2, 4>(*smem);
+  if (e == cudaSuccess) e = small_rows_attr<3, 8>(*smem);
+  if (e == cudaSuccess) e = small_rows_attr<3, 4>(*smem);
   return e;
+}
+
+template <int DV, int NP>
+cudaError_t small_rows_run(const RowArgs& a, const RowTables& gtab, size_t smem, bool full, cudaStream_t stream) {
+  const unsigned blocks = static_cast<unsigned>((a.warps + kSmallWarps - 1) / kSmallWarps);
+  vote_rows_small_kernel<0, DV, NP><<<blocks, kSmallWarps * 32, smem, stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (full) {
+    // the full vote array: scan the warp counts, recount and write every row
+    stage2_scan_kernel<<<1, 1024, 0, stream>>>(a.warp_count, a.warps, const_cast<uint64_t*>(a.warp_offset), a.d_count);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    vote_rows_small_kernel<1, DV, NP><<<blocks, kSmallWarps * 32, smem, stream>>>(a);
+    return cudaGetLastError();
+  }
+  const unsigned eblocks = static_cast<unsigned>((a.warps + kRowWarps - 1) / kRowWarps);
+  emit_rows_kernel<DV, NP><<<eblocks, kRowWarps * 32, 0, stream>>>(a, gtab);
+  return cudaGetLastError();
 }
 
 size_t vote_rows_small_smem(const Geometry& g, const VoteRowSchedule& vs, int64_t words_b) {
@@ -890,12 +938,14 @@ size_t vote_rows_small_smem(const Geometry& g, const VoteRowSchedule& vs, int64_
 }
 
 cudaError_t vote_rows_small_residency(const Geometry& g, const VoteRowSchedule& vs, int64_t words_b,
-                                      int* blocks_per_sm) {
+                                      int* warps_per_sm) {
   size_t smem = 0;
   cudaError_t e = small_rows_smem(g, vs, words_b, &smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, vote_rows_small_kernel<0>, kRowWarps * 32,
-                                                       smem);
+  int blocks = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, vote_rows_small_kernel<0, 2, 4>, kSmallWarps * 32, smem);
+  *warps_per_sm = blocks * kSmallWarps;
+  return e;
 }
 
 cudaError_t launch_vote_rows(const Geometry& g, const VoteRowSchedule& vs, const DeviceTables& t,
@@ -927,27 +977,25 @@ cudaError_t launch_vote_rows(const Geometry& g, const VoteRowSchedule& vs, const
     a.row_list = row_list;
     a.warp_rows = warp_rows;
     a.d_count = d_count;
-    const unsigned blocks = static_cast<unsigned>((vs.warps + kRowWarps - 1) / kRowWarps);
     size_t smem = 0;
     cudaError_t e = small_rows_smem(g, vs, words_b, &smem);
     if (e != cudaSuccess) return e;
-    vote_rows_small_kernel<0><<<blocks, kRowWarps * 32, smem, stream>>>(a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if (votes_out) {
-      // the full vote array: scan the warp counts, recount and write every row
-      stage2_scan_kernel<<<1, 1024, 0, stream>>>(warp_count, vs.warps, warp_offset, d_count);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-      vote_rows_small_kernel<1><<<blocks, kRowWarps * 32, smem, stream>>>(a);
-      return cudaGetLastError();
-    }
     RowTables gtab;
     gtab.kb = t.kb16;
     gtab.cand = t.rowmask;
     gtab.bits = det_bits;
-    emit_rows_kernel<<<blocks, kRowWarps * 32, 0, stream>>>(a, gtab);
-    return cudaGetLastError();
+    const bool few = g.loops <= 15;  // four counter planes hold the votes
+    switch (vs.d_v * 2 + (few ? 1 : 0)) {
+      case 0: return small_rows_run<0, 8>(a, gtab, smem, votes_out != nullptr, stream);
+      case 1: return small_rows_run<0, 4>(a, gtab, smem, votes_out != nullptr, stream);
+      case 2: return small_rows_run<1, 8>(a, gtab, smem, votes_out != nullptr, stream);
+      case 3: return small_rows_run<1, 4>(a, gtab, smem, votes_out != nullptr, stream);
+      case 4: return small_rows_run<2, 8>(a, gtab, smem, votes_out != nullptr, stream);
+      case 5: return small_rows_run<2, 4>(a, gtab, smem, votes_out != nullptr, stream);
+      case 6: return small_rows_run<3, 8>(a, gtab, smem, votes_out != nullptr, stream);
+      case 7: return small_rows_run<3, 4>(a, gtab, smem, votes_out != nullptr, stream);
+      default: return cudaErrorInvalidValue;
+    }
   }
   RowArgs a;
   a.g = g;
