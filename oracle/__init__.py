@@ -10,6 +10,9 @@ it: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 the CUDA library; both sides only read the same seeded cubes from
 ``rsft_inputs``.
 
+``bartlett.py`` is the dense comparison system of Appendix A (Algorithm 2, one
+segment): window, full N-D DFT, exact NP threshold on the bin power.
+
 Parity pins (tests marked ``not gpu``) tie every function here to something
 other than itself: published constants, closed forms, library routines,
 exhaustive brute force and the identities the paper states.  The one function
@@ -23,6 +26,7 @@ from .windows import (chebyshev_window, flat_window, flat_gain, window_6db_bins,
 from .pipeline import (OraclePlan, make_plan, rsft, fold_loop, bucket_spectrum,
                        fold_bucket_direct, reverse_map, mapping, estimate_amplitudes,
                        permute, alias)
+from .bartlett import bartlett, bartlett_window, bartlett_gamma, bartlett_pd_swerling1
 from .design import (beta_sigma, alpha_sigma, mean_alpha, mean_beta, q_func,
                      solve_pd_bar, solve_pfa1, optimal_thresholds,
                      complexity_rsft, complexity_bartlett, first_stage_gamma)
@@ -36,4 +40,5 @@ __all__ = [
     "beta_sigma", "alpha_sigma", "mean_alpha", "mean_beta", "q_func",
     "solve_pd_bar", "solve_pfa1", "optimal_thresholds", "complexity_rsft",
     "complexity_bartlett", "first_stage_gamma",
+    "bartlett", "bartlett_window", "bartlett_gamma", "bartlett_pd_swerling1",
 ]
