@@ -245,6 +245,58 @@ rsft_status rsft_stage2_static(uint8_t* d_votes, int64_t n, int32_t mu, uint64_t
                                uint8_t* d_located_votes, int64_t capacity, int64_t* d_count,
                                void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Dense comparison detector: the Bartlett method of Appendix A (Algorithm 2)
+ * with one data segment.  The whole cube is windowed with the same pre-window
+ * as the RSFT (product of the per-dimension windows, §III-C), transformed by
+ * the full N-point N-D FFT (forward, unnormalised) and every bin's power is
+ * tested against the exact one-segment Neyman-Pearson threshold
+ *     gamma = -sigma_n^2 ||w||^2 ln P_fa
+ * (under H0 the bin power is exponential with mean sigma_n^2 ||w||^2).
+ * Detected bins are returned in ascending row-major order with the amplitude
+ * estimate u-hat_k / prod_d sum_t w_d(t) (the amplitude of an on-grid tone).
+ * The FFT is cuFFT's; windowing, power, threshold and the ordered compaction
+ * are this library's kernels.
+ */
+typedef struct rsft_bartlett_plan rsft_bartlett_plan;
+
+/* Plan for the dense detector.  Uses desc->ndim, n, window, atten_db, p_fa,
+ * noise_var, max_located and device (b, loops and the RSFT design fields are
+ * ignored).  Owns the windowed-spectrum buffer (8 N bytes), cuFFT's plan and
+ * workspace.  Errors: INVALID_ARG (NULL, n not a power of two, ndim out of
+ * 1..4, p_fa outside (0, 1), noise_var <= 0), UNSUPPORTED (more than 2^31 - 1
+ * points), OOM, CUDA (cuFFT plan failure). */
+rsft_status rsft_bartlett_plan_create(const rsft_desc* desc, rsft_bartlett_plan** plan);
+
+/* Frees the plan and its device memory (NULL is a no-op). */
+void rsft_bartlett_plan_destroy(rsft_bartlett_plan* plan);
+
+/* One dense detection of the device cube d_cube (complex64, row-major,
+ * 16-byte aligned, not modified) on `stream`.  Writes at most max_located
+ * ascending detected linear indices to d_located and, when d_amp is not NULL,
+ * their amplitudes (complex64) to d_amp.  *n_located (host) receives the full
+ * count after a synchronisation of `stream`; CAPACITY when it exceeds
+ * max_located (the outputs hold the first max_located). */
+rsft_status rsft_bartlett_execute(rsft_bartlett_plan* plan, const void* d_cube, void* stream, uint64_t* d_located,
+                                  void* d_amp, int64_t* n_located);
+
+/* Stream-ordered variant: the full count lands in device memory (*d_n_located). */
+rsft_status rsft_bartlett_execute_async(rsft_bartlett_plan* plan, const void* d_cube, void* stream,
+                                        uint64_t* d_located, void* d_amp, int64_t* d_n_located);
+
+/* Plan items: GAMMA (double, the threshold), GAIN (double, prod_d sum_t w_d),
+ * WINDOW (double[sum_d N_d], the per-dimension windows), WORKSPACE_BYTES (int64). */
+enum {
+  RSFT_BARTLETT_GAMMA = 1,
+  RSFT_BARTLETT_GAIN = 2,
+  RSFT_BARTLETT_WINDOW = 3,
+  RSFT_BARTLETT_WORKSPACE_BYTES = 4
+};
+rsft_status rsft_bartlett_get(const rsft_bartlett_plan* plan, int32_t what, void* out, size_t bytes);
+
+/* Copies the last execute's spectrum (N complex64, row-major) to d_out. */
+rsft_status rsft_bartlett_copy_spectrum(const rsft_bartlett_plan* plan, void* d_out, void* stream);
+
 /* Static description of a status code (never NULL). */
 const char* rsft_status_string(rsft_status status);
 

@@ -44,8 +44,10 @@ C_SYMBOLS = (
     "rsft_desc_init", "rsft_plan_create", "rsft_plan_destroy", "rsft_execute",
     "rsft_execute_async", "rsft_execute_host", "rsft_plan_get", "rsft_plan_timing", "rsft_copy_buckets",
     "rsft_copy_detections", "rsft_refine", "rsft_stage2_static", "rsft_status_string",
-    "rsft_last_error",
+    "rsft_last_error", "rsft_bartlett_plan_create", "rsft_bartlett_plan_destroy", "rsft_bartlett_execute",
+    "rsft_bartlett_execute_async", "rsft_bartlett_get", "rsft_bartlett_copy_spectrum",
 )
+RSFT_BARTLETT_GAMMA, RSFT_BARTLETT_GAIN, RSFT_BARTLETT_WINDOW, RSFT_BARTLETT_WORKSPACE_BYTES = 1, 2, 3, 4
 
 
 class RsftDesc(ctypes.Structure):
@@ -96,6 +98,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                 c_void_p]
     lib.rsft_stage2_static.argtypes = [c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_int64, c_void_p,
                                        c_void_p]
+    lib.rsft_bartlett_plan_create.argtypes = [POINTER(RsftDesc), POINTER(c_void_p)]
+    lib.rsft_bartlett_plan_destroy.argtypes = [c_void_p]
+    lib.rsft_bartlett_plan_destroy.restype = None
+    lib.rsft_bartlett_execute.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_int64)]
+    lib.rsft_bartlett_execute_async.argtypes = [c_void_p] * 6
+    lib.rsft_bartlett_get.argtypes = [c_void_p, c_int32, c_void_p, c_size_t]
+    lib.rsft_bartlett_copy_spectrum.argtypes = [c_void_p, c_void_p, c_void_p]
     lib.rsft_status_string.argtypes = [c_int32]
     lib.rsft_status_string.restype = c_char_p
     lib.rsft_last_error.argtypes = []
@@ -305,3 +314,65 @@ def rsft_status_string(status: int) -> str:
 
 def rsft_last_error() -> str:
     return load_library().rsft_last_error().decode()
+
+
+class BartlettPlan:
+    """Owning handle of an ``rsft_bartlett_plan`` (the dense comparison detector)."""
+
+    def __init__(self, handle: c_void_p, desc: RsftDesc):
+        self.handle = handle
+        self.desc = desc
+
+    @property
+    def shape(self):
+        return tuple(int(self.desc.n[i]) for i in range(self.desc.ndim))
+
+    def close(self):
+        if self.handle:
+            load_library().rsft_bartlett_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rsft_bartlett_plan_create(desc: RsftDesc) -> BartlettPlan:
+    h = c_void_p()
+    _check(load_library().rsft_bartlett_plan_create(ctypes.byref(desc), ctypes.byref(h)))
+    return BartlettPlan(h, desc)
+
+
+def rsft_bartlett_plan_destroy(plan: BartlettPlan) -> None:
+    plan.close()
+
+
+def rsft_bartlett_execute(plan: BartlettPlan, cube, located=None, amp=None, stream=None, allow_capacity=False) -> int:
+    """Dense detection of a device cube; returns the number of detected bins."""
+    n = c_int64(0)
+    st = load_library().rsft_bartlett_execute(plan.handle, _ptr(cube), _stream(stream), _ptr(located), _ptr(amp),
+                                              ctypes.byref(n))
+    _check(st, allow=(RSFT_ERR_CAPACITY,) if allow_capacity else ())
+    return int(n.value)
+
+
+def rsft_bartlett_execute_async(plan: BartlettPlan, cube, count, located=None, amp=None, stream=None) -> None:
+    _check(load_library().rsft_bartlett_execute_async(plan.handle, _ptr(cube), _stream(stream), _ptr(located),
+                                                      _ptr(amp), _ptr(count)))
+
+
+def rsft_bartlett_get(plan: BartlettPlan, what: int):
+    if what == RSFT_BARTLETT_WINDOW:
+        out = np.zeros(sum(plan.shape), dtype=np.float64)
+    elif what == RSFT_BARTLETT_WORKSPACE_BYTES:
+        out = np.zeros(1, dtype=np.int64)
+    else:
+        out = np.zeros(1, dtype=np.float64)
+    _check(load_library().rsft_bartlett_get(plan.handle, what, out.ctypes.data_as(c_void_p), out.nbytes))
+    return out
+
+
+def rsft_bartlett_copy_spectrum(plan: BartlettPlan, out, stream=None) -> None:
+    _check(load_library().rsft_bartlett_copy_spectrum(plan.handle, _ptr(out), _stream(stream)))

@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT, "librsft.so")
 
-CU_SOURCES = ["capi.cu", "fold.cu", "spectrum.cu", "votes.cu"]
+CU_SOURCES = ["capi.cu", "fold.cu", "spectrum.cu", "votes.cu", "bartlett.cu"]
 CPP_SOURCES = ["plan_host.cpp"]
 HEADERS = ["device.cuh", "tma.cuh", "plan_host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -83,7 +83,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             f.result()
     if jobs or not os.path.exists(LIB):
         tmp = LIB + ".tmp"
-        _run([nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs], verbose)
+        _run([nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-lcufft"], verbose)
         os.replace(tmp, LIB)
     return LIB
 

@@ -115,6 +115,9 @@ struct Workspace {
 };
 
 // Launchers (return cudaSuccess or the launch error).
+// Exclusive scan of n u32 counts into offsets[0..n] (offsets[n] = total), total also to *total.
+cudaError_t launch_count_scan(const uint32_t* counts, int64_t n, uint64_t* offsets, int64_t* total,
+                              cudaStream_t stream);
 cudaError_t launch_fold(const Geometry& g, const FoldSchedule& fs, const DeviceTables& t,
                         const float2* cube, int loop0, int lg, float2* folded, float2* partial, int* err,
                         int* copy_mode, cudaStream_t stream);

@@ -853,6 +853,12 @@ __global__ void __launch_bounds__(kRowWarps * 32) emit_rows_kernel(const RowArgs
 
 }  // namespace
 
+cudaError_t launch_count_scan(const uint32_t* counts, int64_t n, uint64_t* offsets, int64_t* total,
+                              cudaStream_t stream) {
+  stage2_scan_kernel<<<1, 1024, 0, stream>>>(counts, n, offsets, total);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_vote_scatter(const Geometry& g, const DeviceTables& t, const uint32_t* det_bits,
                                 int64_t words_b, uint32_t* votes, cudaStream_t stream) {
   VoteArgs args;

@@ -130,3 +130,20 @@ def test_host_plan_cannot_execute(lib):
 def test_sparsity_limit_warning(lib):
     p = R.rsft_plan_create(R.make_desc((64, 64), (4, 4), 8, k_max=64, p_fa1=0.01, mu=3, device=-1))
     assert int(R.rsft_plan_get(p, R.RSFT_GET_WARNINGS)[0]) & R.RSFT_WARN_SPARSITY_LIMIT
+
+
+@pytest.mark.parametrize("field,value", [("p_fa", 0.0), ("p_fa", 1.0), ("noise_var", 0.0), ("ndim", 5)])
+def test_bartlett_plan_rejects_invalid_descriptors(field, value):
+    d = R.make_desc((64, 64), (8, 8), 4)
+    setattr(d, field, value)
+    with pytest.raises(R.RsftError) as ei:
+        R.rsft_bartlett_plan_create(d)
+    assert ei.value.status == R.RSFT_ERR_INVALID_ARG
+
+
+def test_bartlett_plan_rejects_non_power_of_two():
+    d = R.make_desc((64, 64), (8, 8), 4)
+    d.n[1] = 48
+    with pytest.raises(R.RsftError) as ei:
+        R.rsft_bartlett_plan_create(d)
+    assert ei.value.status == R.RSFT_ERR_INVALID_ARG
