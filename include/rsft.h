@@ -245,6 +245,33 @@ rsft_status rsft_stage2_static(uint8_t* d_votes, int64_t n, int32_t mu, uint64_t
                                uint8_t* d_located_votes, int64_t capacity, int64_t* d_count,
                                void* stream);
 
+/* Batched executes of n_frames equally shaped device cubes (this plan's shape):
+ * frame f reads d_cubes[f] (a host array of device pointers, each 16-byte
+ * aligned), writes its located list to d_located + f * max_located, its
+ * amplitudes (when d_amp is not NULL) to d_amp + f * max_located, and its full
+ * located count to d_counts[f] (device int64).  Frames go round-robin to
+ * `lanes` execution lanes (1..8), each with its own workspace (created on
+ * first use, kept by the plan) and stream.  The lanes start after the work
+ * already queued on `stream`, and `stream` waits for all of them, so the call
+ * is stream-ordered like rsft_execute_async; concurrent lanes overlap one
+ * frame's fold with another frame's bucket FFT, votes and estimate.  Per-frame
+ * stage timing is not recorded.  The paper has no counterpart (it processes one
+ * cube at a time).  Errors: INVALID_ARG (NULL pointers, n_frames < 0, lanes
+ * outside 1..8, a misaligned cube), OOM, CUDA. */
+rsft_status rsft_execute_batch(rsft_plan* plan, const void* const* d_cubes, int64_t n_frames, int32_t lanes,
+                               void* stream, uint64_t* d_located, void* d_amp, int64_t* d_counts);
+
+/* Host-buffer batch: frame f reads the host cube h_cubes[f] (pinned memory gets
+ * the full copy bandwidth).  Returns when every frame's results are in host
+ * memory: h_counts[f] (full count), the first min(count, max_located) entries
+ * of h_located + f * max_located and (when h_amp is not NULL) of
+ * h_amp + f * max_located.  Two lanes alternate so that the host-to-device copy
+ * of frame f + 1 overlaps the RSFT of frame f; each lane keeps a device cube
+ * buffer.  CAPACITY when some count exceeds max_located; TIMEOUT when a device
+ * wait gave up.  The paper has no counterpart. */
+rsft_status rsft_execute_host_batch(rsft_plan* plan, const void* const* h_cubes, int64_t n_frames, void* stream,
+                                    uint64_t* h_located, void* h_amp, int64_t* h_counts);
+
 /* ---------------------------------------------------------------------------
  * Dense comparison detector: the Bartlett method of Appendix A (Algorithm 2)
  * with one data segment.  The whole cube is windowed with the same pre-window

@@ -44,7 +44,7 @@ C_SYMBOLS = (
     "rsft_desc_init", "rsft_plan_create", "rsft_plan_destroy", "rsft_execute",
     "rsft_execute_async", "rsft_execute_host", "rsft_plan_get", "rsft_plan_timing", "rsft_copy_buckets",
     "rsft_copy_detections", "rsft_refine", "rsft_stage2_static", "rsft_status_string",
-    "rsft_last_error", "rsft_bartlett_plan_create", "rsft_bartlett_plan_destroy", "rsft_bartlett_execute",
+    "rsft_last_error", "rsft_execute_batch", "rsft_execute_host_batch", "rsft_bartlett_plan_create", "rsft_bartlett_plan_destroy", "rsft_bartlett_execute",
     "rsft_bartlett_execute_async", "rsft_bartlett_get", "rsft_bartlett_copy_spectrum",
 )
 RSFT_BARTLETT_GAMMA, RSFT_BARTLETT_GAIN, RSFT_BARTLETT_WINDOW, RSFT_BARTLETT_WORKSPACE_BYTES = 1, 2, 3, 4
@@ -98,6 +98,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                 c_void_p]
     lib.rsft_stage2_static.argtypes = [c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_int64, c_void_p,
                                        c_void_p]
+    lib.rsft_execute_batch.argtypes = [c_void_p, POINTER(c_void_p), c_int64, c_int32, c_void_p, c_void_p, c_void_p,
+                                       c_void_p]
+    lib.rsft_execute_host_batch.argtypes = [c_void_p, POINTER(c_void_p), c_int64, c_void_p, c_void_p, c_void_p,
+                                            c_void_p]
     lib.rsft_bartlett_plan_create.argtypes = [POINTER(RsftDesc), POINTER(c_void_p)]
     lib.rsft_bartlett_plan_destroy.argtypes = [c_void_p]
     lib.rsft_bartlett_plan_destroy.restype = None
@@ -268,6 +272,24 @@ _GET_SHAPES = {
     RSFT_GET_SNR_DB: ("float64", "1"), RSFT_GET_WORKSPACE_BYTES: ("int64", "1"),
     RSFT_GET_STAGE_MS: ("float64", "8"), RSFT_GET_FOLD_BYTES: ("int64", "1"), RSFT_GET_FOLD_COPY: ("int32", "1"),
 }
+
+
+def _ptr_array(xs):
+    return (c_void_p * max(1, len(xs)))(*[_ptr(x).value for x in xs])
+
+
+def rsft_execute_batch(plan: Plan, cubes, counts, lanes: int = 2, located=None, amp=None, stream=None) -> None:
+    """Stream-ordered batch of device cubes over `lanes` lanes; frame f's count lands in
+    counts[f], its located list in located[f * max_located:], its amplitudes likewise."""
+    _check(load_library().rsft_execute_batch(plan.handle, _ptr_array(cubes), len(cubes), lanes, _stream(stream),
+                                             _ptr(located), _ptr(amp), _ptr(counts)))
+
+
+def rsft_execute_host_batch(plan: Plan, h_cubes, located, counts, amp=None, stream=None, allow_capacity=False) -> None:
+    """Host cubes in, host results out (counts[f], located[f * max_located:], amp likewise)."""
+    st = load_library().rsft_execute_host_batch(plan.handle, _ptr_array(h_cubes), len(h_cubes), _stream(stream),
+                                                _ptr(located), _ptr(amp), _ptr(counts))
+    _check(st, allow=(RSFT_ERR_CAPACITY,) if allow_capacity else ())
 
 
 def rsft_plan_get(plan: Plan, what: int) -> np.ndarray:

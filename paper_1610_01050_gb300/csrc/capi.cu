@@ -17,6 +17,20 @@
 
 using rsft::cplx;
 
+// An extra execution lane of a plan: its own workspace, count block and stream, so
+// frames of a batch run concurrently (lane 0 is the plan's own workspace).
+struct rsft_lane {
+  rsft::Workspace ws{};
+  int64_t* d_count = nullptr;   // count, error flag
+  int64_t* h_count = nullptr;   // pinned mirror
+  bool votes_dirty = false;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  void* staging = nullptr;      // host batches: this lane's cube buffer
+  uint64_t* d_loc_stage = nullptr;
+  float2* d_amp_stage = nullptr;
+};
+
 struct rsft_plan {
   rsft::HostPlan host;
   bool has_device = false;
@@ -29,6 +43,8 @@ struct rsft_plan {
   rsft::DeviceTables tables{};
   rsft::Workspace ws{};
   std::vector<void*> allocations;
+  std::vector<rsft_lane> lanes;     // extra lanes of batched executes (created on demand)
+  cudaEvent_t fork = nullptr;       // batch fork point on the caller's stream
   int64_t* d_count = nullptr;       // located count of the last execute
   int64_t* h_count = nullptr;       // pinned mirror of d_count
   void* staging = nullptr;          // cube staging buffer of rsft_execute_host
@@ -259,6 +275,51 @@ bool plan_fft_passes(const rsft::Geometry& g, std::vector<rsft::FftPass>& passes
     db = da;
   }
   return true;
+}
+
+// Device workspace of one execution lane (buckets, detections, votes, row lists) and its
+// 16-byte count block (located count, error flag).
+rsft_status alloc_workspace(rsft_plan* p, rsft::Workspace& ws, int64_t** d_count) {
+  const rsft::HostPlan& h = p->host;
+  const int L = h.loops;
+  rsft_status st;
+  const size_t lb = static_cast<size_t>(L) * h.total_b;
+  if ((st = dev_alloc(p, &ws.folded, lb * sizeof(float2))) != RSFT_OK) return st;
+  if ((st = dev_alloc(p, &ws.spectrum, lb * sizeof(float2))) != RSFT_OK) return st;
+  ws.partial = nullptr;
+  if (!p->fold.direct) {
+    const size_t np = static_cast<size_t>(std::min(L, rsft::kMaxLoopGroup)) * p->fold.classes *
+                      p->fold.row_chunks * p->fold.col_chunks * p->fold.xcount;
+    if ((st = dev_alloc(p, &ws.partial, np * sizeof(float2))) != RSFT_OK) return st;
+  }
+  ws.words_b = (h.total_b + 31) / 32;
+  // rounded up to 16 bytes: the vote kernel stages the bitmaps with one bulk copy
+  if ((st = dev_alloc(p, &ws.det_bits, (static_cast<size_t>(L) * ws.words_b * 4 + 15) & ~static_cast<size_t>(15))) !=
+      RSFT_OK)
+    return st;
+  if ((st = dev_alloc(p, &ws.det_count, static_cast<size_t>(L) * 4)) != RSFT_OK) return st;
+  ws.segments = rsft::stage2_segments(h.total_n);
+  const size_t vote_bytes = static_cast<size_t>(ws.segments) * 16 * 1024;
+  ws.vote_words = static_cast<int64_t>(vote_bytes / 4);
+  if ((st = dev_alloc(p, &ws.votes, vote_bytes)) != RSFT_OK) return st;
+  cudaError_t e = cudaMemset(ws.votes, 0, vote_bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(votes)");
+  if ((st = dev_alloc(p, &ws.seg_count, static_cast<size_t>(ws.segments) * 4)) != RSFT_OK) return st;
+  if ((st = dev_alloc(p, &ws.seg_offset, static_cast<size_t>(ws.segments + 1) * 8)) != RSFT_OK) return st;
+  if (p->rows_mode) {
+    if ((st = dev_alloc(p, &ws.warp_count, static_cast<size_t>(p->rows.warps) * 4)) != RSFT_OK) return st;
+    if ((st = dev_alloc(p, &ws.warp_offset, static_cast<size_t>(p->rows.warps + 1) * 8)) != RSFT_OK) return st;
+    if (p->rows.small) {
+      const size_t entries = static_cast<size_t>(p->rows.warps) * p->rows.rows_per_warp;
+      if ((st = dev_alloc(p, &ws.row_list, entries * 16)) != RSFT_OK) return st;
+      if ((st = dev_alloc(p, &ws.warp_rows, static_cast<size_t>(p->rows.warps) * 4)) != RSFT_OK) return st;
+    }
+  }
+  if ((st = dev_alloc(p, d_count, 16)) != RSFT_OK) return st;
+  ws.err_flag = reinterpret_cast<int*>(*d_count + 1);  // [1] of the count block
+  e = cudaMemset(*d_count, 0, 16);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(flags)");
+  return RSFT_OK;
 }
 
 rsft_status build_device(rsft_plan* p) {
@@ -538,35 +599,12 @@ rsft_status build_device(rsft_plan* p) {
     if ((st = upload(p, &kp, kb)) != RSFT_OK) return st;
     p->tables.kb16 = kp;
   }
-  // workspace
-  rsft::Workspace& ws = p->ws;
-  const size_t lb = static_cast<size_t>(L) * h.total_b;
-  if ((st = dev_alloc(p, &ws.folded, lb * sizeof(float2))) != RSFT_OK) return st;
-  if ((st = dev_alloc(p, &ws.spectrum, lb * sizeof(float2))) != RSFT_OK) return st;
-  ws.partial = nullptr;
-  if (!p->fold.direct) {
-    const size_t np = static_cast<size_t>(std::min(L, rsft::kMaxLoopGroup)) * p->fold.classes *
-                      p->fold.row_chunks * p->fold.col_chunks * p->fold.xcount;
-    if ((st = dev_alloc(p, &ws.partial, np * sizeof(float2))) != RSFT_OK) return st;
-  }
-  ws.words_b = (h.total_b + 31) / 32;
-  // rounded up to 16 bytes: the vote kernel stages the bitmaps with one bulk copy
-  if ((st = dev_alloc(p, &ws.det_bits, (static_cast<size_t>(L) * ws.words_b * 4 + 15) & ~static_cast<size_t>(15))) !=
-      RSFT_OK)
-    return st;
-  if ((st = dev_alloc(p, &ws.det_count, static_cast<size_t>(L) * 4)) != RSFT_OK) return st;
-  ws.segments = rsft::stage2_segments(h.total_n);
-  const size_t vote_bytes = static_cast<size_t>(ws.segments) * 16 * 1024;
-  ws.vote_words = static_cast<int64_t>(vote_bytes / 4);
-  if ((st = dev_alloc(p, &ws.votes, vote_bytes)) != RSFT_OK) return st;
-  cudaError_t e = cudaMemset(ws.votes, 0, vote_bytes);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(votes)");
-  if ((st = dev_alloc(p, &ws.seg_count, static_cast<size_t>(ws.segments) * 4)) != RSFT_OK) return st;
-  if ((st = dev_alloc(p, &ws.seg_offset, static_cast<size_t>(ws.segments + 1) * 8)) != RSFT_OK) return st;
+  // workspace of lane 0
+  p->ws.words_b = (h.total_b + 31) / 32;
   if (p->rows_mode && p->rows.small) {
     // one wave of resident blocks: each block stages its tables once
     int per_sm = 0, sms = 0;
-    cudaError_t oe = rsft::vote_rows_small_residency(g, p->rows, ws.words_b, &per_sm);
+    cudaError_t oe = rsft::vote_rows_small_residency(g, p->rows, p->ws.words_b, &per_sm);
     if (oe == cudaSuccess) oe = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
     if (oe != cudaSuccess) return cuda_fail(oe, "vote kernel residency");
     const int64_t resident_warps = static_cast<int64_t>(std::max(per_sm, 8)) * sms;
@@ -575,19 +613,8 @@ rsft_status build_device(rsft_plan* p) {
     p->rows.rows_per_warp = static_cast<int>(rpw);
     p->rows.warps = (p->rows.rows + rpw - 1) / rpw;
   }
-  if (p->rows_mode) {
-    if ((st = dev_alloc(p, &ws.warp_count, static_cast<size_t>(p->rows.warps) * 4)) != RSFT_OK) return st;
-    if ((st = dev_alloc(p, &ws.warp_offset, static_cast<size_t>(p->rows.warps + 1) * 8)) != RSFT_OK) return st;
-    if (p->rows.small) {
-      const size_t entries = static_cast<size_t>(p->rows.warps) * p->rows.rows_per_warp;
-      if ((st = dev_alloc(p, &ws.row_list, entries * 16)) != RSFT_OK) return st;
-      if ((st = dev_alloc(p, &ws.warp_rows, static_cast<size_t>(p->rows.warps) * 4)) != RSFT_OK) return st;
-    }
-  }
-  if ((st = dev_alloc(p, &p->d_count, 16)) != RSFT_OK) return st;
-  ws.err_flag = reinterpret_cast<int*>(p->d_count + 1);  // [1] of the count block
-  e = cudaMemset(p->d_count, 0, 16);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(flags)");
+  if ((st = alloc_workspace(p, p->ws, &p->d_count)) != RSFT_OK) return st;
+  cudaError_t e;
   e = cudaMallocHost(reinterpret_cast<void**>(&p->h_count), 16);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
   e = cudaDeviceSynchronize();
@@ -640,6 +667,12 @@ void release(rsft_plan* p) {
     cudaDeviceSynchronize();
     p->pending.clear();
     for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
+    for (rsft_lane& ln : p->lanes) {
+      if (ln.stream) cudaStreamDestroy(ln.stream);
+      if (ln.done) cudaEventDestroy(ln.done);
+      if (ln.h_count) cudaFreeHost(ln.h_count);
+    }
+    if (p->fork) cudaEventDestroy(p->fork);
     for (void* a : p->allocations) cudaFree(a);
     if (p->h_count) cudaFreeHost(p->h_count);
     cudaGetLastError();
@@ -647,19 +680,20 @@ void release(rsft_plan* p) {
   delete p;
 }
 
-rsft_status run(rsft_plan* p, const void* d_cube, cudaStream_t stream, uint64_t* d_located,
-                uint8_t* d_located_votes, float2* d_amp, uint8_t* d_votes_out, int64_t* d_count) {
+rsft_status run_lane(rsft_plan* p, rsft::Workspace& ws, bool& votes_dirty, bool timed, const void* d_cube,
+                     cudaStream_t stream, uint64_t* d_located, uint8_t* d_located_votes, float2* d_amp,
+                     uint8_t* d_votes_out, int64_t* d_count) {
   const rsft::Geometry& g = p->geom;
-  rsft::Workspace& ws = p->ws;
   cudaError_t e;
   if (reinterpret_cast<uintptr_t>(d_cube) % 16 != 0) return fail(RSFT_ERR_INVALID_ARG, "cube must be 16-byte aligned");
   std::array<cudaEvent_t, 6> ev{};
-  if (p->timing)
+  timed = timed && p->timing;
+  if (timed)
     for (auto& x : ev) x = take_event(p);
   auto mark = [&](int i) {
-    if (p->timing && ev[i]) cudaEventRecord(ev[i], stream);
+    if (timed && ev[i]) cudaEventRecord(ev[i], stream);
   };
-  if (p->votes_dirty) {
+  if (votes_dirty) {
     e = cudaMemsetAsync(ws.votes, 0, static_cast<size_t>(ws.vote_words) * 4, stream);
     if (e != cudaSuccess) return cuda_fail(e, "clear votes");
   }
@@ -691,14 +725,14 @@ rsft_status run(rsft_plan* p, const void* d_cube, cudaStream_t stream, uint64_t*
                                d_count, ws.err_flag, ws.row_list, ws.warp_rows, stream);
     if (e != cudaSuccess) return cuda_fail(e, "vote_rows");
   } else {
-    p->votes_dirty = true;
+    votes_dirty = true;
     e = rsft::launch_vote_scatter(g, p->tables, ws.det_bits, ws.words_b, ws.votes, stream);
     if (e != cudaSuccess) return cuda_fail(e, "vote_scatter");
     mark(3);
     e = rsft::launch_stage2(g, p->host.mu, ws, d_located, d_located_votes, d_votes_out, p->host.desc.max_located,
                             d_count, stream);
     if (e != cudaSuccess) return cuda_fail(e, "stage2_compact");
-    p->votes_dirty = false;
+    votes_dirty = false;
   }
   mark(4);
   if (d_amp && p->host.desc.max_located > 0) {
@@ -706,8 +740,14 @@ rsft_status run(rsft_plan* p, const void* d_cube, cudaStream_t stream, uint64_t*
     if (e != cudaSuccess) return cuda_fail(e, "median_estimate");
   }
   mark(5);
-  if (p->timing) p->pending.push_back(ev);
+  if (timed) p->pending.push_back(ev);
   return RSFT_OK;
+}
+
+rsft_status run(rsft_plan* p, const void* d_cube, cudaStream_t stream, uint64_t* d_located,
+                uint8_t* d_located_votes, float2* d_amp, uint8_t* d_votes_out, int64_t* d_count) {
+  return run_lane(p, p->ws, p->votes_dirty, true, d_cube, stream, d_located, d_located_votes, d_amp, d_votes_out,
+                  d_count);
 }
 
 }  // namespace
@@ -788,6 +828,142 @@ rsft_status rsft_plan_create(const rsft_desc* desc, rsft_plan** plan) {
 }
 
 void rsft_plan_destroy(rsft_plan* plan) { release(plan); }
+
+}  // extern "C"
+
+namespace {
+
+// Extra lanes 0..n-1 of batched executes (workspace, count block, stream), and with
+// `staging` their device cube and output buffers.
+rsft_status ensure_lanes(rsft_plan* p, int n, bool staging) {
+  rsft_status st;
+  cudaError_t e;
+  if (!p->fork && (e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(e, "batch event");
+  while (static_cast<int>(p->lanes.size()) < n) {
+    rsft_lane ln;
+    if ((st = alloc_workspace(p, ln.ws, &ln.d_count)) != RSFT_OK) return st;
+    if ((e = cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "lane stream");
+    if ((e = cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming)) != cudaSuccess) {
+      cudaStreamDestroy(ln.stream);
+      return cuda_fail(e, "lane event");
+    }
+    if ((e = cudaMallocHost(reinterpret_cast<void**>(&ln.h_count), 16)) != cudaSuccess) {
+      cudaStreamDestroy(ln.stream);
+      cudaEventDestroy(ln.done);
+      return cuda_fail(e, "lane count");
+    }
+    p->lanes.push_back(ln);
+  }
+  if (staging) {
+    const int64_t cap = std::max<int64_t>(p->host.desc.max_located, 1);
+    for (int i = 0; i < n; ++i) {
+      rsft_lane& ln = p->lanes[i];
+      if (ln.staging) continue;
+      if ((st = dev_alloc(p, &ln.staging, static_cast<size_t>(p->host.total_n) * 8)) != RSFT_OK) return st;
+      if ((st = dev_alloc(p, &ln.d_loc_stage, static_cast<size_t>(cap) * 8)) != RSFT_OK) return st;
+      if ((st = dev_alloc(p, &ln.d_amp_stage, static_cast<size_t>(cap) * 8)) != RSFT_OK) return st;
+    }
+  }
+  return RSFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rsft_status rsft_execute_batch(rsft_plan* plan, const void* const* d_cubes, int64_t n_frames, int32_t lanes,
+                               void* stream, uint64_t* d_located, void* d_amp, int64_t* d_counts) {
+  if (!plan || (n_frames > 0 && (!d_cubes || !d_counts)) || n_frames < 0)
+    return fail(RSFT_ERR_INVALID_ARG, "NULL plan, cubes or counts, or negative frame count");
+  if (!plan->has_device) return fail(RSFT_ERR_INVALID_ARG, "host-only plan cannot execute");
+  if (lanes < 1 || lanes > 8) return fail(RSFT_ERR_INVALID_ARG, "lanes must be 1..8");
+  const int64_t cap = plan->host.desc.max_located;
+  if (cap > 0 && n_frames > 0 && !d_located) return fail(RSFT_ERR_INVALID_ARG, "d_located is NULL");
+  for (int64_t f = 0; f < n_frames; ++f)
+    if (!d_cubes[f] || reinterpret_cast<uintptr_t>(d_cubes[f]) % 16 != 0)
+      return fail(RSFT_ERR_INVALID_ARG, "every cube must be non-NULL and 16-byte aligned");
+  if (n_frames == 0) return RSFT_OK;
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return fail(RSFT_ERR_CUDA, "cudaSetDevice failed");
+  const int nl = static_cast<int>(std::min<int64_t>(lanes, n_frames));
+  rsft_status st = ensure_lanes(plan, nl, false);
+  if (st != RSFT_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaEventRecord(plan->fork, s);
+  for (int i = 0; e == cudaSuccess && i < nl; ++i) e = cudaStreamWaitEvent(plan->lanes[i].stream, plan->fork, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "batch fork");
+  for (int64_t f = 0; f < n_frames; ++f) {
+    rsft_lane& ln = plan->lanes[f % nl];
+    st = run_lane(plan, ln.ws, ln.votes_dirty, false, d_cubes[f], ln.stream, d_located ? d_located + f * cap : nullptr,
+                  nullptr, d_amp ? static_cast<float2*>(d_amp) + f * cap : nullptr, nullptr, d_counts + f);
+    if (st != RSFT_OK) return st;
+  }
+  for (int i = 0; e == cudaSuccess && i < nl; ++i) {
+    e = cudaEventRecord(plan->lanes[i].done, plan->lanes[i].stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->lanes[i].done, 0);
+  }
+  return e == cudaSuccess ? RSFT_OK : cuda_fail(e, "batch join");
+}
+
+rsft_status rsft_execute_host_batch(rsft_plan* plan, const void* const* h_cubes, int64_t n_frames, void* stream,
+                                    uint64_t* h_located, void* h_amp, int64_t* h_counts) {
+  if (!plan || n_frames < 0 || (n_frames > 0 && (!h_cubes || !h_counts)))
+    return fail(RSFT_ERR_INVALID_ARG, "NULL plan, cubes or counts, or negative frame count");
+  if (!plan->has_device) return fail(RSFT_ERR_INVALID_ARG, "host-only plan cannot execute");
+  const int64_t cap = plan->host.desc.max_located;
+  if (cap > 0 && n_frames > 0 && !h_located) return fail(RSFT_ERR_INVALID_ARG, "h_located is NULL");
+  for (int64_t f = 0; f < n_frames; ++f)
+    if (!h_cubes[f]) return fail(RSFT_ERR_INVALID_ARG, "NULL host cube");
+  if (n_frames == 0) return RSFT_OK;
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return fail(RSFT_ERR_CUDA, "cudaSetDevice failed");
+  rsft_status st = ensure_lanes(plan, 2, true);
+  if (st != RSFT_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaEventRecord(plan->fork, s);
+  for (int i = 0; e == cudaSuccess && i < 2; ++i) e = cudaStreamWaitEvent(plan->lanes[i].stream, plan->fork, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "batch fork");
+  const size_t cube_bytes = static_cast<size_t>(plan->host.total_n) * 8;
+  // frame f on lane f % 2: copy in, RSFT, count out; its lists follow once the count is known
+  auto enqueue = [&](int64_t f) -> rsft_status {
+    rsft_lane& ln = plan->lanes[f % 2];
+    cudaError_t ce = cudaMemcpyAsync(ln.staging, h_cubes[f], cube_bytes, cudaMemcpyHostToDevice, ln.stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "copy cube to device");
+    rsft_status rs = run_lane(plan, ln.ws, ln.votes_dirty, false, ln.staging, ln.stream, ln.d_loc_stage, nullptr,
+                              h_amp ? ln.d_amp_stage : nullptr, nullptr, ln.d_count);
+    if (rs != RSFT_OK) return rs;
+    ce = cudaMemcpyAsync(ln.h_count, ln.d_count, 16, cudaMemcpyDeviceToHost, ln.stream);
+    if (ce == cudaSuccess) ce = cudaEventRecord(ln.done, ln.stream);
+    return ce == cudaSuccess ? RSFT_OK : cuda_fail(ce, "copy count to host");
+  };
+  if ((st = enqueue(0)) != RSFT_OK) return st;
+  rsft_status result = RSFT_OK;
+  for (int64_t f = 0; f < n_frames; ++f) {
+    if (f + 1 < n_frames && (st = enqueue(f + 1)) != RSFT_OK) return st;
+    rsft_lane& ln = plan->lanes[f % 2];
+    if ((e = cudaEventSynchronize(ln.done)) != cudaSuccess) return cuda_fail(e, "rsft_execute_host_batch");
+    if (reinterpret_cast<const int*>(ln.h_count + 1)[0] != 0) {
+      cudaMemsetAsync(ln.ws.err_flag, 0, sizeof(int), ln.stream);
+      result = fail(RSFT_ERR_TIMEOUT, "a device wait gave up (error flag set)");
+    }
+    const int64_t c = ln.h_count[0];
+    h_counts[f] = c;
+    const int64_t k = std::min(c, cap);
+    if (k > 0) {
+      e = cudaMemcpyAsync(h_located + f * cap, ln.d_loc_stage, static_cast<size_t>(k) * 8, cudaMemcpyDeviceToHost,
+                          ln.stream);
+      if (e == cudaSuccess && h_amp)
+        e = cudaMemcpyAsync(static_cast<float2*>(h_amp) + f * cap, ln.d_amp_stage, static_cast<size_t>(k) * 8,
+                            cudaMemcpyDeviceToHost, ln.stream);
+      if (e != cudaSuccess) return cuda_fail(e, "copy results to host");
+    }
+    if (c > cap && result == RSFT_OK) result = fail(RSFT_ERR_CAPACITY, "a located list was truncated to max_located");
+  }
+  for (int i = 0; i < 2; ++i)
+    if ((e = cudaStreamSynchronize(plan->lanes[i].stream)) != cudaSuccess) return cuda_fail(e, "rsft_execute_host_batch");
+  return result;
+}
 
 rsft_status rsft_execute_async(rsft_plan* plan, const void* d_cube, void* stream, uint64_t* d_located,
                                uint8_t* d_located_votes, void* d_amp, uint8_t* d_votes_out,

@@ -147,3 +147,12 @@ def test_bartlett_plan_rejects_non_power_of_two():
     with pytest.raises(R.RsftError) as ei:
         R.rsft_bartlett_plan_create(d)
     assert ei.value.status == R.RSFT_ERR_INVALID_ARG
+
+
+def test_batches_need_a_device_plan():
+    d = R.make_desc((64, 64), (8, 8), 4, device=-1, p_fa1=0.05, mu=1)
+    plan = R.rsft_plan_create(d)
+    counts = np.zeros(1, dtype=np.int64)
+    with pytest.raises(R.RsftError) as ei:
+        R.rsft_execute_host_batch(plan, [np.zeros(64 * 64, np.complex64)], np.zeros(8, np.int64), counts)
+    assert ei.value.status == R.RSFT_ERR_INVALID_ARG
