@@ -180,14 +180,23 @@ def estimate_amplitudes(plan: OraclePlan, spectra: np.ndarray, located: np.ndarr
     return out
 
 
-def rsft(plan: OraclePlan, r: np.ndarray, estimate: bool = True, keep: bool = True) -> dict:
-    """Run Algorithm 1 on cube r, then second-stage detection and estimation."""
-    if tuple(r.shape) != plan.n:
+def rsft(plan: OraclePlan, r, estimate: bool = True, keep: bool = True) -> dict:
+    """Run Algorithm 1 on cube r, then second-stage detection and estimation.
+
+    ``r`` is one cube (every loop re-permutes the same data) or a list of L cubes, one
+    segment per loop (§III-C: each iteration may process its own data segment r_s of the
+    signal model of §IV-A, with sigma_s drawn per segment).
+    """
+    segments = isinstance(r, (list, tuple))
+    if segments:
+        if len(r) != plan.loops or any(tuple(np.shape(x)) != plan.n for x in r):
+            raise ValueError("segment mode needs one cube of the plan's shape per loop")
+    elif tuple(r.shape) != plan.n:
         raise ValueError("cube shape does not match the plan")
     votes = np.zeros(plan.n, dtype=np.int64)
     folded, spectra, detected = [], [], []
     for l in range(plan.loops):
-        f = fold_loop(plan, r, l)
+        f = fold_loop(plan, r[l] if segments else r, l)
         fh = bucket_spectrum(f)
         c = np.abs(fh) ** 2 > plan.gamma[l]
         for j in np.argwhere(c):

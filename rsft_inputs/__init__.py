@@ -223,3 +223,20 @@ def workload_frame(name: str, frame: int = 0, shape: Sequence[int] | None = None
                       amp_model=wl.amp_model, min_sep_bins=wl.min_sep_bins)
     cube = tone_cube(shp, tg, noise_var if with_noise else 0.0, seed)
     return cube, tg, wl, noise_var
+
+
+def segment_cubes(shape: Sequence[int], targets: Targets, noise_var: float, seed: int, segments: int,
+                  buckets_total: int) -> list:
+    """One cube per data segment (the signal model of §IV-A): the tones keep their
+    frequencies, their complex amplitudes are redrawn for every segment as
+    b_{i,s} ~ CN(0, sigma_bi^2) (Swerling-I), with sigma_bi^2 set from the target's SNR
+    (read after the B-point bucket FFT, like ``draw_targets``), and every segment gets its
+    own noise.  Seeds: (seed, segment) keyed."""
+    out = []
+    sb2 = noise_var * 10.0 ** ((np.asarray(targets.snr_db, dtype=np.float64) - 10.0 * np.log10(buckets_total)) / 10.0)
+    for s in range(segments):
+        rng = np.random.default_rng([seed, 7919, s])
+        amps = (rng.standard_normal(len(sb2)) + 1j * rng.standard_normal(len(sb2))) * np.sqrt(sb2 / 2.0)
+        tg = Targets(targets.freqs, amps, targets.snr_db)
+        out.append(tone_cube(shape, tg, noise_var, seed * 1000 + 17 * s + 1))
+    return out
