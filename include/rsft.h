@@ -245,6 +245,19 @@ rsft_status rsft_stage2_static(uint8_t* d_votes, int64_t n, int32_t mu, uint64_t
                                uint8_t* d_located_votes, int64_t capacity, int64_t* d_count,
                                void* stream);
 
+/* Segment mode (§III-C: each iteration processes its own data segment of the signal
+ * model of §IV-A, with sigma_l drawn per segment): loop l folds the device cube
+ * d_segments[l] (a host array of L device pointers, each 16-byte aligned, all of the
+ * plan's shape); bucket FFT, detection, votes, second stage and estimate are those of
+ * rsft_execute, over the L segments' buckets.  The fold reads every segment once (L
+ * cubes per call).  Outputs, counts and errors as for rsft_execute / rsft_execute_async;
+ * the first call builds one-loop fold tables (kept by the plan). */
+rsft_status rsft_execute_segments(rsft_plan* plan, const void* const* d_segments, void* stream, uint64_t* d_located,
+                                  uint8_t* d_located_votes, void* d_amp, uint8_t* d_votes_out, int64_t* n_located);
+rsft_status rsft_execute_segments_async(rsft_plan* plan, const void* const* d_segments, void* stream,
+                                        uint64_t* d_located, uint8_t* d_located_votes, void* d_amp,
+                                        uint8_t* d_votes_out, int64_t* d_n_located);
+
 /* Batched executes of n_frames equally shaped device cubes (this plan's shape):
  * frame f reads d_cubes[f] (a host array of device pointers, each 16-byte
  * aligned), writes its located list to d_located + f * max_located, its

@@ -44,7 +44,8 @@ C_SYMBOLS = (
     "rsft_desc_init", "rsft_plan_create", "rsft_plan_destroy", "rsft_execute",
     "rsft_execute_async", "rsft_execute_host", "rsft_plan_get", "rsft_plan_timing", "rsft_copy_buckets",
     "rsft_copy_detections", "rsft_refine", "rsft_stage2_static", "rsft_status_string",
-    "rsft_last_error", "rsft_execute_batch", "rsft_execute_host_batch", "rsft_bartlett_plan_create", "rsft_bartlett_plan_destroy", "rsft_bartlett_execute",
+    "rsft_last_error", "rsft_execute_batch", "rsft_execute_host_batch", "rsft_execute_segments",
+    "rsft_execute_segments_async", "rsft_bartlett_plan_create", "rsft_bartlett_plan_destroy", "rsft_bartlett_execute",
     "rsft_bartlett_execute_async", "rsft_bartlett_get", "rsft_bartlett_copy_spectrum",
 )
 RSFT_BARTLETT_GAMMA, RSFT_BARTLETT_GAIN, RSFT_BARTLETT_WINDOW, RSFT_BARTLETT_WORKSPACE_BYTES = 1, 2, 3, 4
@@ -98,6 +99,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                 c_void_p]
     lib.rsft_stage2_static.argtypes = [c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_int64, c_void_p,
                                        c_void_p]
+    lib.rsft_execute_segments.argtypes = [c_void_p, POINTER(c_void_p), c_void_p, c_void_p, c_void_p, c_void_p,
+                                          c_void_p, POINTER(c_int64)]
+    lib.rsft_execute_segments_async.argtypes = [c_void_p, POINTER(c_void_p)] + [c_void_p] * 6
     lib.rsft_execute_batch.argtypes = [c_void_p, POINTER(c_void_p), c_int64, c_int32, c_void_p, c_void_p, c_void_p,
                                        c_void_p]
     lib.rsft_execute_host_batch.argtypes = [c_void_p, POINTER(c_void_p), c_int64, c_void_p, c_void_p, c_void_p,
@@ -276,6 +280,23 @@ _GET_SHAPES = {
 
 def _ptr_array(xs):
     return (c_void_p * max(1, len(xs)))(*[_ptr(x).value for x in xs])
+
+
+def rsft_execute_segments(plan: Plan, segments, stream=None, located=None, located_votes=None, amp=None,
+                          votes_out=None, allow_capacity=False) -> int:
+    """Segment mode: loop l folds segments[l] (one device cube per loop); returns the count."""
+    n = c_int64(0)
+    st = load_library().rsft_execute_segments(plan.handle, _ptr_array(segments), _stream(stream), _ptr(located),
+                                              _ptr(located_votes), _ptr(amp), _ptr(votes_out), ctypes.byref(n))
+    _check(st, allow=(RSFT_ERR_CAPACITY,) if allow_capacity else ())
+    return int(n.value)
+
+
+def rsft_execute_segments_async(plan: Plan, segments, count, stream=None, located=None, located_votes=None,
+                                amp=None, votes_out=None) -> None:
+    _check(load_library().rsft_execute_segments_async(plan.handle, _ptr_array(segments), _stream(stream),
+                                                      _ptr(located), _ptr(located_votes), _ptr(amp),
+                                                      _ptr(votes_out), _ptr(count)))
 
 
 def rsft_execute_batch(plan: Plan, cubes, counts, lanes: int = 2, located=None, amp=None, stream=None) -> None:

@@ -44,6 +44,8 @@ struct rsft_plan {
   rsft::Workspace ws{};
   std::vector<void*> allocations;
   std::vector<rsft_lane> lanes;     // extra lanes of batched executes (created on demand)
+  rsft::DeviceTables seg_tables{};  // segment mode: fold tables grouped one loop per launch
+  bool seg_ready = false;
   cudaEvent_t fork = nullptr;       // batch fork point on the caller's stream
   int64_t* d_count = nullptr;       // located count of the last execute
   int64_t* h_count = nullptr;       // pinned mirror of d_count
@@ -322,6 +324,71 @@ rsft_status alloc_workspace(rsft_plan* p, rsft::Workspace& ws, int64_t** d_count
   return RSFT_OK;
 }
 
+// Fold tables in FP64, rounded once: per row the product of the row dimensions' weights
+// a_{l,d}(s_d) as (c, d - c, c + d, c + d) of w = c + jd, and per column the product of the
+// rest; loops grouped by `group` (one fold launch per group).
+rsft_status build_fold_tables(rsft_plan* p, int group, const float4** ftable, const float2** fcolw) {
+  const rsft::HostPlan& h = p->host;
+  const int L = h.loops, D = h.ndim;
+  rsft_status st;
+  {
+    const rsft::FoldSchedule& fs = p->fold;
+    auto weight = [&](int l, int d, int64_t sd) {
+      return h.wbar[d][(h.sigma_inv[l * D + d] * sd) & (h.n[d] - 1)] * h.w[d][sd];
+    };
+    // layout [class group][row chunk][row][class in group][loop]: a stage's rows are contiguous
+    const int64_t R = fs.rows_per_chunk, C = fs.cps;
+    const int64_t tunits = static_cast<int64_t>(fs.groups) * fs.row_chunks;
+    std::vector<float4> ft(static_cast<size_t>(L) * tunits * R * C);
+    std::vector<float2> fc(static_cast<size_t>(L) * fs.col_chunks * fs.width);
+    for (int l0 = 0; l0 < L; l0 += group) {
+      const int lg = std::min(group, L - l0);
+      const size_t tbase = static_cast<size_t>(l0) * tunits * R * C;
+      for (int64_t e = 0; e < tunits * R * C; ++e) {
+        const int64_t ci = e % C, r = (e / C) % R, tu = e / (C * R);
+        const int64_t cls = (tu / fs.row_chunks) * C + ci, rc = tu % fs.row_chunks;
+        {
+          int64_t sdig[rsft::kMaxDim] = {0, 0, 0, 0};
+          int64_t rr = rc * R + r, cres = cls;
+          for (int d = fs.d_in - 1; d >= 0; --d) {
+            const int64_t md = rr % h.m[d], xd = cres % h.b[d];
+            rr /= h.m[d];
+            cres /= h.b[d];
+            sdig[d] = xd + h.b[d] * md;
+          }
+          for (int l = 0; l < lg; ++l) {
+            cplx wv(1.0, 0.0);
+            for (int d = 0; d < fs.d_in; ++d) wv *= weight(l0 + l, d, sdig[d]);
+            ft[tbase + static_cast<size_t>(e) * lg + l] =
+                make_float4(static_cast<float>(wv.real()), static_cast<float>(wv.imag() - wv.real()),
+                            static_cast<float>(wv.real() + wv.imag()), static_cast<float>(wv.real() + wv.imag()));
+          }
+        }
+      }
+      const size_t cbase = static_cast<size_t>(l0) * fs.col_chunks * fs.width;
+      for (int cc = 0; cc < fs.col_chunks; ++cc)
+        for (int l = 0; l < lg; ++l)
+          for (int c = 0; c < fs.width; ++c) {
+            int64_t col = static_cast<int64_t>(cc) * fs.width + c;
+            cplx wv(1.0, 0.0);
+            for (int d = D - 1; d >= fs.d_in; --d) {
+              const int64_t sd = col % h.n[d];
+              col /= h.n[d];
+              wv *= weight(l0 + l, d, sd);
+            }
+            fc[cbase + (static_cast<size_t>(cc) * lg + l) * fs.width + c] = to_f2(wv);
+          }
+    }
+    float4* f4 = nullptr;
+    if ((st = upload(p, &f4, ft)) != RSFT_OK) return st;
+    *ftable = f4;
+    float2* f2p = nullptr;
+    if ((st = upload(p, &f2p, fc)) != RSFT_OK) return st;
+    *fcolw = f2p;
+  }
+  return RSFT_OK;
+}
+
 rsft_status build_device(rsft_plan* p) {
   const rsft::HostPlan& h = p->host;
   rsft::Geometry& g = p->geom;
@@ -495,63 +562,7 @@ rsft_status build_device(rsft_plan* p) {
     if (rsft::fold_smem_bytes(g, fs, std::min(L, rsft::kMaxLoopGroup)) > 227 * 1024)
       return fail(RSFT_ERR_UNSUPPORTED, "fold schedule needs more shared memory than a CTA has");
   }
-  // fold tables in FP64, rounded once: per row the product of the row dimensions' weights
-  // a_{l,d}(s_d) as (c, d - c, c + d, c + d) of w = c + jd, and per column the product of the rest
-  {
-    const rsft::FoldSchedule& fs = p->fold;
-    auto weight = [&](int l, int d, int64_t sd) {
-      return h.wbar[d][(h.sigma_inv[l * D + d] * sd) & (h.n[d] - 1)] * h.w[d][sd];
-    };
-    // layout [class group][row chunk][row][class in group][loop]: a stage's rows are contiguous
-    const int64_t R = fs.rows_per_chunk, C = fs.cps;
-    const int64_t tunits = static_cast<int64_t>(fs.groups) * fs.row_chunks;
-    std::vector<float4> ft(static_cast<size_t>(L) * tunits * R * C);
-    std::vector<float2> fc(static_cast<size_t>(L) * fs.col_chunks * fs.width);
-    for (int l0 = 0; l0 < L; l0 += rsft::kMaxLoopGroup) {
-      const int lg = std::min(rsft::kMaxLoopGroup, L - l0);
-      const size_t tbase = static_cast<size_t>(l0) * tunits * R * C;
-      for (int64_t e = 0; e < tunits * R * C; ++e) {
-        const int64_t ci = e % C, r = (e / C) % R, tu = e / (C * R);
-        const int64_t cls = (tu / fs.row_chunks) * C + ci, rc = tu % fs.row_chunks;
-        {
-          int64_t sdig[rsft::kMaxDim] = {0, 0, 0, 0};
-          int64_t rr = rc * R + r, cres = cls;
-          for (int d = fs.d_in - 1; d >= 0; --d) {
-            const int64_t md = rr % h.m[d], xd = cres % h.b[d];
-            rr /= h.m[d];
-            cres /= h.b[d];
-            sdig[d] = xd + h.b[d] * md;
-          }
-          for (int l = 0; l < lg; ++l) {
-            cplx wv(1.0, 0.0);
-            for (int d = 0; d < fs.d_in; ++d) wv *= weight(l0 + l, d, sdig[d]);
-            ft[tbase + static_cast<size_t>(e) * lg + l] =
-                make_float4(static_cast<float>(wv.real()), static_cast<float>(wv.imag() - wv.real()),
-                            static_cast<float>(wv.real() + wv.imag()), static_cast<float>(wv.real() + wv.imag()));
-          }
-        }
-      }
-      const size_t cbase = static_cast<size_t>(l0) * fs.col_chunks * fs.width;
-      for (int cc = 0; cc < fs.col_chunks; ++cc)
-        for (int l = 0; l < lg; ++l)
-          for (int c = 0; c < fs.width; ++c) {
-            int64_t col = static_cast<int64_t>(cc) * fs.width + c;
-            cplx wv(1.0, 0.0);
-            for (int d = D - 1; d >= fs.d_in; --d) {
-              const int64_t sd = col % h.n[d];
-              col /= h.n[d];
-              wv *= weight(l0 + l, d, sd);
-            }
-            fc[cbase + (static_cast<size_t>(cc) * lg + l) * fs.width + c] = to_f2(wv);
-          }
-    }
-    float4* f4 = nullptr;
-    if ((st = upload(p, &f4, ft)) != RSFT_OK) return st;
-    p->tables.ftable = f4;
-    float2* f2p = nullptr;
-    if ((st = upload(p, &f2p, fc)) != RSFT_OK) return st;
-    p->tables.fcolw = f2p;
-  }
+  if ((st = build_fold_tables(p, rsft::kMaxLoopGroup, &p->tables.ftable, &p->tables.fcolw)) != RSFT_OK) return st;
   p->tables.rowmask = nullptr;
   p->tables.kb16 = nullptr;
   if (p->rows_mode && p->rows.small) {
@@ -682,10 +693,16 @@ void release(rsft_plan* p) {
 
 rsft_status run_lane(rsft_plan* p, rsft::Workspace& ws, bool& votes_dirty, bool timed, const void* d_cube,
                      cudaStream_t stream, uint64_t* d_located, uint8_t* d_located_votes, float2* d_amp,
-                     uint8_t* d_votes_out, int64_t* d_count) {
+                     uint8_t* d_votes_out, int64_t* d_count, const void* const* d_segments = nullptr) {
   const rsft::Geometry& g = p->geom;
   cudaError_t e;
-  if (reinterpret_cast<uintptr_t>(d_cube) % 16 != 0) return fail(RSFT_ERR_INVALID_ARG, "cube must be 16-byte aligned");
+  if (d_segments) {
+    for (int l = 0; l < g.loops; ++l)
+      if (!d_segments[l] || reinterpret_cast<uintptr_t>(d_segments[l]) % 16 != 0)
+        return fail(RSFT_ERR_INVALID_ARG, "every segment must be non-NULL and 16-byte aligned");
+  } else if (reinterpret_cast<uintptr_t>(d_cube) % 16 != 0) {
+    return fail(RSFT_ERR_INVALID_ARG, "cube must be 16-byte aligned");
+  }
   std::array<cudaEvent_t, 6> ev{};
   timed = timed && p->timing;
   if (timed)
@@ -701,13 +718,18 @@ rsft_status run_lane(rsft_plan* p, rsft::Workspace& ws, bool& votes_dirty, bool 
   if (e == cudaSuccess) e = cudaMemsetAsync(ws.det_count, 0, static_cast<size_t>(g.loops) * 4, stream);
   if (e != cudaSuccess) return cuda_fail(e, "clear detections");
   mark(0);
-  for (int l0 = 0; l0 < g.loops; l0 += rsft::kMaxLoopGroup) {
-    const int lg = std::min(rsft::kMaxLoopGroup, g.loops - l0);
-    e = rsft::launch_fold(g, p->fold, p->tables, static_cast<const float2*>(d_cube), l0, lg, ws.folded,
-                          ws.partial, ws.err_flag, &p->fold_copy_mode, stream);
+  // segment mode: loop l folds its own segment (one loop per launch); otherwise every loop
+  // group folds the same cube in one pass
+  const int group = d_segments ? 1 : rsft::kMaxLoopGroup;
+  const rsft::DeviceTables& ft = d_segments ? p->seg_tables : p->tables;
+  for (int l0 = 0; l0 < g.loops; l0 += group) {
+    const int lg = std::min(group, g.loops - l0);
+    const void* cube = d_segments ? d_segments[l0] : d_cube;
+    e = rsft::launch_fold(g, p->fold, ft, static_cast<const float2*>(cube), l0, lg, ws.folded, ws.partial,
+                          ws.err_flag, &p->fold_copy_mode, stream);
     if (e != cudaSuccess) return cuda_fail(e, "permute_window_fold");
     if (!p->fold.direct) {
-      e = rsft::launch_fold_reduce(g, p->fold, p->tables, l0, lg, ws.partial, ws.folded, stream);
+      e = rsft::launch_fold_reduce(g, p->fold, ft, l0, lg, ws.partial, ws.folded, stream);
       if (e != cudaSuccess) return cuda_fail(e, "fold reduce");
     }
   }
@@ -906,6 +928,36 @@ rsft_status rsft_execute_batch(rsft_plan* plan, const void* const* d_cubes, int6
   return e == cudaSuccess ? RSFT_OK : cuda_fail(e, "batch join");
 }
 
+static rsft_status finish_count(rsft_plan* plan, cudaStream_t s, int64_t* n_located, const char* what);
+
+rsft_status rsft_execute_segments_async(rsft_plan* plan, const void* const* d_segments, void* stream,
+                                        uint64_t* d_located, uint8_t* d_located_votes, void* d_amp,
+                                        uint8_t* d_votes_out, int64_t* d_n_located) {
+  if (!plan || !d_segments || !d_n_located) return fail(RSFT_ERR_INVALID_ARG, "NULL plan, segments or count");
+  if (!plan->has_device) return fail(RSFT_ERR_INVALID_ARG, "host-only plan cannot execute");
+  if (plan->host.desc.max_located > 0 && !d_located) return fail(RSFT_ERR_INVALID_ARG, "d_located is NULL");
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return fail(RSFT_ERR_CUDA, "cudaSetDevice failed");
+  if (!plan->seg_ready) {
+    plan->seg_tables = plan->tables;
+    rsft_status st = build_fold_tables(plan, 1, &plan->seg_tables.ftable, &plan->seg_tables.fcolw);
+    if (st != RSFT_OK) return st;
+    plan->seg_ready = true;
+  }
+  return run_lane(plan, plan->ws, plan->votes_dirty, true, nullptr, static_cast<cudaStream_t>(stream), d_located,
+                  d_located_votes, static_cast<float2*>(d_amp), d_votes_out, d_n_located, d_segments);
+}
+
+rsft_status rsft_execute_segments(rsft_plan* plan, const void* const* d_segments, void* stream, uint64_t* d_located,
+                                  uint8_t* d_located_votes, void* d_amp, uint8_t* d_votes_out, int64_t* n_located) {
+  if (!plan || !n_located) return fail(RSFT_ERR_INVALID_ARG, "NULL plan or n_located");
+  if (!plan->has_device) return fail(RSFT_ERR_INVALID_ARG, "host-only plan cannot execute");
+  rsft_status st = rsft_execute_segments_async(plan, d_segments, stream, d_located, d_located_votes, d_amp,
+                                               d_votes_out, plan->d_count);
+  if (st != RSFT_OK) return st;
+  return finish_count(plan, static_cast<cudaStream_t>(stream), n_located, "rsft_execute_segments");
+}
+
 rsft_status rsft_execute_host_batch(rsft_plan* plan, const void* const* h_cubes, int64_t n_frames, void* stream,
                                     uint64_t* h_located, void* h_amp, int64_t* h_counts) {
   if (!plan || n_frames < 0 || (n_frames > 0 && (!h_cubes || !h_counts)))
@@ -977,18 +1029,13 @@ rsft_status rsft_execute_async(rsft_plan* plan, const void* d_cube, void* stream
              static_cast<float2*>(d_amp), d_votes_out, d_n_located);
 }
 
-rsft_status rsft_execute(rsft_plan* plan, const void* d_cube, void* stream, uint64_t* d_located,
-                         uint8_t* d_located_votes, void* d_amp, uint8_t* d_votes_out, int64_t* n_located) {
-  if (!plan || !n_located) return fail(RSFT_ERR_INVALID_ARG, "NULL plan or n_located");
-  if (!plan->has_device) return fail(RSFT_ERR_INVALID_ARG, "host-only plan cannot execute");
-  rsft_status st = rsft_execute_async(plan, d_cube, stream, d_located, d_located_votes, d_amp, d_votes_out,
-                                      plan->d_count);
-  if (st != RSFT_OK) return st;
+// Reads the located count (and error flag) of the plan's own lane after an execute queued
+// on `s`: TIMEOUT when a device wait gave up, CAPACITY when the list was truncated.
+static rsft_status finish_count(rsft_plan* plan, cudaStream_t s, int64_t* n_located, const char* what) {
   DeviceGuard guard(plan->device);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemcpyAsync(plan->h_count, plan->d_count, 16, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(e, "rsft_execute");
+  if (e != cudaSuccess) return cuda_fail(e, what);
   *n_located = *plan->h_count;
   if (reinterpret_cast<const int*>(plan->h_count + 1)[0] != 0) {
     cudaMemsetAsync(plan->ws.err_flag, 0, sizeof(int), s);
@@ -997,6 +1044,16 @@ rsft_status rsft_execute(rsft_plan* plan, const void* d_cube, void* stream, uint
   if (*n_located > plan->host.desc.max_located)
     return fail(RSFT_ERR_CAPACITY, "located list truncated to max_located");
   return RSFT_OK;
+}
+
+rsft_status rsft_execute(rsft_plan* plan, const void* d_cube, void* stream, uint64_t* d_located,
+                         uint8_t* d_located_votes, void* d_amp, uint8_t* d_votes_out, int64_t* n_located) {
+  if (!plan || !n_located) return fail(RSFT_ERR_INVALID_ARG, "NULL plan or n_located");
+  if (!plan->has_device) return fail(RSFT_ERR_INVALID_ARG, "host-only plan cannot execute");
+  rsft_status st = rsft_execute_async(plan, d_cube, stream, d_located, d_located_votes, d_amp, d_votes_out,
+                                      plan->d_count);
+  if (st != RSFT_OK) return st;
+  return finish_count(plan, static_cast<cudaStream_t>(stream), n_located, "rsft_execute");
 }
 
 rsft_status rsft_execute_host(rsft_plan* plan, const void* h_cube, void* stream, uint64_t* h_located,
