@@ -278,6 +278,29 @@ def dense_comparator(R, torch, wl, nv, cubes, targets, stream, dev, ws, steps, w
             "rsft_speedup": rsft_value / val}
 
 
+def segment_mode(R, torch, plan, wl, cubes, stream, dev, ws, located, amp, count, frames):
+    """Segment mode (loop l folds its own data segment): frames of L segments each, the
+    segments taken round-robin from the ring of cubes; the fold reads L cubes per frame."""
+    F = len(cubes)
+    segs = [cubes[l % F] for l in range(wl.loops)]
+    for _ in range(2):
+        R.rsft_execute_segments_async(plan, segs, count, stream=stream, located=located, amp=amp)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for k in range(frames):
+        segs = [cubes[(k + l) % F] for l in range(wl.loops)]
+        R.rsft_execute_segments_async(plan, segs, count, stream=stream, located=located, amp=amp)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), ws, dev)
+    cube_bytes = int(np.prod(wl.shape)) * 8
+    return {"value": whole_job_rate(ws, frames, ms), "unit": "frames/s", "frames": frames,
+            "ms_per_frame": ms / frames, "segments_per_frame": wl.loops,
+            "hbm_gbs": wl.loops * cube_bytes * frames / (ms / 1e3) / 1e9,
+            "note": "one 1024x256x64 segment per loop, taken round-robin from the ring of frames"}
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -419,6 +442,8 @@ def run_ours(args):
     e2e_val = whole_job_rate(ws, e2e_steps, t_e2e * 1e3)
 
     bplan.close()
+    seg = segment_mode(R, torch, plan, wl, cubes, stream, dev, ws, located, amp, count,
+                       max(1, min(args.steps // 20, 50)))
     dense = dense_comparator(R, torch, wl, nv, cubes, targets, stream, dev, ws, max(1, min(args.steps, 200)),
                              max(3, min(args.warmup, 10)), cap, value)
 
@@ -455,6 +480,7 @@ def run_ours(args):
                       "note": "one frame per rsft_execute_async, back to back on one stream",
                       "batched_speedup": value / plain_value, "lanes_tuning_frames_per_s": tune},
             "dense_fft": dense,
+            "segment_mode": seg,
             "gpu_launches": int(stage[7]) * args.steps,
             "clocks": clocks,
         }

@@ -10,6 +10,9 @@ it: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 the CUDA library; both sides only read the same seeded cubes from
 ``rsft_inputs``.
 
+``refine.py`` is the bucket-domain refinement loss of off-grid tones and its gradient
+(beyond the paper), pinned by central finite differences.
+
 ``bartlett.py`` is the dense comparison system of Appendix A (Algorithm 2, one
 segment): window, full N-D DFT, exact NP threshold on the bin power.
 
@@ -26,6 +29,7 @@ from .windows import (chebyshev_window, flat_window, flat_gain, window_6db_bins,
 from .pipeline import (OraclePlan, make_plan, rsft, fold_loop, bucket_spectrum,
                        fold_bucket_direct, reverse_map, mapping, estimate_amplitudes,
                        permute, alias)
+from .refine import tone_field, refine_loss, refine_grad
 from .bartlett import bartlett, bartlett_window, bartlett_gamma, bartlett_pd_swerling1
 from .design import (beta_sigma, alpha_sigma, mean_alpha, mean_beta, q_func,
                      solve_pd_bar, solve_pfa1, optimal_thresholds,
@@ -41,4 +45,5 @@ __all__ = [
     "solve_pd_bar", "solve_pfa1", "optimal_thresholds", "complexity_rsft",
     "complexity_bartlett", "first_stage_gamma",
     "bartlett", "bartlett_window", "bartlett_gamma", "bartlett_pd_swerling1",
+    "tone_field", "refine_loss", "refine_grad",
 ]
