@@ -204,13 +204,32 @@ rsft_status rsft_copy_buckets(rsft_plan* plan, int32_t which, void* d_out, void*
 rsft_status rsft_copy_detections(rsft_plan* plan, void* d_out, void* stream);
 
 /*
- * Gradient refinement of located tones (beyond the paper, which recovers only
- * grid locations, §I): minimises the bucket-domain residual between the
- * cube's folded buckets and those of K synthesised tones over `steps`
- * gradient steps of size lr.  d_freq: device float [K][D] in cycles/sample
- * (in/out); d_amp: device complex64 [K] (in/out).  Requires a prior execute
- * on the same cube.
+ * Refinement of off-grid tones in the bucket domain (beyond the paper, which
+ * recovers grid locations only, §I).  A K-tone model s(t) = sum_k a_k
+ * exp(j 2 pi f_k . t) (f_k in cycles/sample per dimension) is compared, loop by
+ * loop, with the cube through the RSFT's own fold (Algorithm 1: pre-window,
+ * permutation, flat window, aliasing):
+ *     E = sum_l sum_j |F_l[j] - fold_l(s)[j]|^2,   F_l = fold_l(cube).
+ * The fold is linear and separable over dimensions, so E, its gradient and the
+ * Gauss-Newton diagonal need per-dimension tone responses only (no N-point
+ * fields).  Tones: d_freq device float [K][D] (wrapped into [0, 1)), d_amp
+ * device complex64 [K].
+ *
+ * rsft_refine_prepare: folds d_cube into the plan's buckets F_l (all loops).
+ * rsft_refine_eval: E (device double *d_loss, may be NULL), dE/df (device float
+ *   [K][D]), (dE/da_re, dE/da_im) as device complex64 [K], and the Gauss-Newton
+ *   diagonal (device float [K][D + 1]: amplitude term, then one per frequency;
+ *   NULL allowed) of the tones against the buckets of the last prepare or
+ *   execute.  Stream-ordered.
+ * rsft_refine: prepare, then `steps` Levenberg-Marquardt updates per tone
+ *   (the Gauss-Newton matrix of a tone's amplitude and D frequencies, damped by
+ *   1e-3 of its diagonal; theta += lr * delta), in place on d_freq and d_amp.
+ * Errors: INVALID_ARG (NULL, k < 1, steps < 0, lr <= 0, misaligned cube),
+ * UNSUPPORTED (K > 2^20), OOM, CUDA.
  */
+rsft_status rsft_refine_prepare(rsft_plan* plan, const void* d_cube, void* stream);
+rsft_status rsft_refine_eval(rsft_plan* plan, int64_t k, const float* d_freq, const void* d_amp, double* d_loss,
+                             float* d_grad_freq, void* d_grad_amp, float* d_hdiag, void* stream);
 rsft_status rsft_refine(rsft_plan* plan, const void* d_cube, int64_t k,
                         float* d_freq, void* d_amp, int32_t steps, float lr,
                         void* stream);

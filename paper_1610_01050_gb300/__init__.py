@@ -43,7 +43,7 @@ RSFT_BUCKETS_FOLDED, RSFT_BUCKETS_SPECTRUM = 0, 1
 C_SYMBOLS = (
     "rsft_desc_init", "rsft_plan_create", "rsft_plan_destroy", "rsft_execute",
     "rsft_execute_async", "rsft_execute_host", "rsft_plan_get", "rsft_plan_timing", "rsft_copy_buckets",
-    "rsft_copy_detections", "rsft_refine", "rsft_stage2_static", "rsft_status_string",
+    "rsft_copy_detections", "rsft_refine", "rsft_refine_prepare", "rsft_refine_eval", "rsft_stage2_static", "rsft_status_string",
     "rsft_last_error", "rsft_execute_batch", "rsft_execute_host_batch", "rsft_execute_segments",
     "rsft_execute_segments_async", "rsft_bartlett_plan_create", "rsft_bartlett_plan_destroy", "rsft_bartlett_execute",
     "rsft_bartlett_execute_async", "rsft_bartlett_get", "rsft_bartlett_copy_spectrum",
@@ -97,6 +97,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rsft_copy_detections.argtypes = [c_void_p, c_void_p, c_void_p]
     lib.rsft_refine.argtypes = [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_int32, ctypes.c_float,
                                 c_void_p]
+    lib.rsft_refine_prepare.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.rsft_refine_eval.argtypes = [c_void_p, c_int64] + [c_void_p] * 7
     lib.rsft_stage2_static.argtypes = [c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_int64, c_void_p,
                                        c_void_p]
     lib.rsft_execute_segments.argtypes = [c_void_p, POINTER(c_void_p), c_void_p, c_void_p, c_void_p, c_void_p,
@@ -339,8 +341,24 @@ def rsft_copy_detections(plan: Plan, out, stream=None) -> None:
 
 
 def rsft_refine(plan: Plan, cube, k, freq, amp, steps, lr, stream=None) -> None:
+    """Fold the cube, then `steps` Levenberg-Marquardt updates of the K tones in place
+    (freq: device float32 [K, D] cycles/sample, amp: device complex64 [K])."""
     _check(load_library().rsft_refine(plan.handle, _ptr(cube), int(k), _ptr(freq), _ptr(amp), int(steps),
                                       ctypes.c_float(lr), _stream(stream)))
+
+
+def rsft_refine_prepare(plan: Plan, cube, stream=None) -> None:
+    """Fold the cube into the plan's buckets (the data side of the refinement loss)."""
+    _check(load_library().rsft_refine_prepare(plan.handle, _ptr(cube), _stream(stream)))
+
+
+def rsft_refine_eval(plan: Plan, freq, amp, loss=None, grad_freq=None, grad_amp=None, hdiag=None,
+                     stream=None) -> None:
+    """Loss (device float64 [1]), gradients (float32 [K, D], complex64 [K] holding (dE/da_re,
+    dE/da_im)) and Gauss-Newton diagonal (float32 [K, D + 1]) of the tones."""
+    k = int(amp.shape[0])
+    _check(load_library().rsft_refine_eval(plan.handle, k, _ptr(freq), _ptr(amp), _ptr(loss), _ptr(grad_freq),
+                                           _ptr(grad_amp), _ptr(hdiag), _stream(stream)))
 
 
 def rsft_stage2_static(votes, n, mu, located, count, located_votes=None, capacity=None, stream=None) -> None:

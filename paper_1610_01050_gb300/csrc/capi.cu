@@ -44,6 +44,8 @@ struct rsft_plan {
   rsft::Workspace ws{};
   std::vector<void*> allocations;
   std::vector<rsft_lane> lanes;     // extra lanes of batched executes (created on demand)
+  rsft::RefineWork refine{};         // bucket-domain refinement scratch (grown on demand)
+  rsft::RefineGeom refine_geom{};
   rsft::DeviceTables seg_tables{};  // segment mode: fold tables grouped one loop per launch
   bool seg_ready = false;
   cudaEvent_t fork = nullptr;       // batch fork point on the caller's stream
@@ -1240,17 +1242,110 @@ rsft_status rsft_copy_detections(rsft_plan* plan, void* d_out, void* stream) {
   return RSFT_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Refinement geometry and scratch for K tones (kept and grown by the plan).
+rsft_status ensure_refine(rsft_plan* p, int64_t k) {
+  rsft::RefineGeom& rg = p->refine_geom;
+  const rsft::HostPlan& h = p->host;
+  rg.ndim = h.ndim;
+  rg.loops = h.loops;
+  rg.total_b = h.total_b;
+  rg.sumb = 0;
+  for (int d = 0; d < rsft::kMaxDim; ++d) {
+    rg.n[d] = p->geom.n[d];
+    rg.b[d] = p->geom.b[d];
+    rg.m[d] = p->geom.m[d];
+    rg.b_shift[d] = p->geom.b_shift[d];
+    rg.boff[d] = rg.sumb;
+    if (d < h.ndim) rg.sumb += static_cast<int>(h.b[d]);
+  }
+  rsft::RefineWork& w = p->refine;
+  if (w.k_cap >= k && w.gres) return RSFT_OK;
+  const int64_t kk = std::max<int64_t>(k, 16);
+  rsft_status st;
+  const size_t resp = static_cast<size_t>(h.loops) * kk * rg.sumb * sizeof(float2);
+  if ((st = dev_alloc(p, &w.gres, resp)) != RSFT_OK) return st;
+  if ((st = dev_alloc(p, &w.gder, resp)) != RSFT_OK) return st;
+  if (!w.resid) {
+    if ((st = dev_alloc(p, &w.resid, static_cast<size_t>(h.loops) * h.total_b * sizeof(float2))) != RSFT_OK)
+      return st;
+    w.parts = 152 * 4;
+    if ((st = dev_alloc(p, &w.partial, static_cast<size_t>(w.parts) * sizeof(double))) != RSFT_OK) return st;
+  }
+  const int vals = 3 + 5 * rsft::kMaxDim + rsft::kMaxDim * (rsft::kMaxDim - 1);
+  if ((st = dev_alloc(p, &w.contr, static_cast<size_t>(h.loops) * kk * vals * sizeof(float))) != RSFT_OK)
+    return st;
+  w.k_cap = kk;
+  return RSFT_OK;
+}
+
+// The folded buckets F_l of the cube in the plan's workspace (the RSFT's own fold, all loops).
+rsft_status fold_cube(rsft_plan* p, const void* d_cube, cudaStream_t stream) {
+  if (reinterpret_cast<uintptr_t>(d_cube) % 16 != 0) return fail(RSFT_ERR_INVALID_ARG, "cube must be 16-byte aligned");
+  const rsft::Geometry& g = p->geom;
+  rsft::Workspace& ws = p->ws;
+  for (int l0 = 0; l0 < g.loops; l0 += rsft::kMaxLoopGroup) {
+    const int lg = std::min(rsft::kMaxLoopGroup, g.loops - l0);
+    cudaError_t e = rsft::launch_fold(g, p->fold, p->tables, static_cast<const float2*>(d_cube), l0, lg, ws.folded,
+                                      ws.partial, ws.err_flag, &p->fold_copy_mode, stream);
+    if (e == cudaSuccess && !p->fold.direct)
+      e = rsft::launch_fold_reduce(g, p->fold, p->tables, l0, lg, ws.partial, ws.folded, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "permute_window_fold");
+  }
+  return RSFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rsft_status rsft_refine_prepare(rsft_plan* plan, const void* d_cube, void* stream) {
+  if (!plan || !d_cube) return fail(RSFT_ERR_INVALID_ARG, "NULL plan or cube");
+  if (!plan->has_device) return fail(RSFT_ERR_INVALID_ARG, "host-only plan cannot execute");
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return fail(RSFT_ERR_CUDA, "cudaSetDevice failed");
+  return fold_cube(plan, d_cube, static_cast<cudaStream_t>(stream));
+}
+
+rsft_status rsft_refine_eval(rsft_plan* plan, int64_t k, const float* d_freq, const void* d_amp, double* d_loss,
+                             float* d_grad_freq, void* d_grad_amp, float* d_hdiag, void* stream) {
+  if (!plan || k < 1 || !d_freq || !d_amp) return fail(RSFT_ERR_INVALID_ARG, "NULL plan, tones, or k < 1");
+  if (!plan->has_device) return fail(RSFT_ERR_INVALID_ARG, "host-only plan cannot execute");
+  if (k > (1 << 20)) return fail(RSFT_ERR_UNSUPPORTED, "more than 2^20 tones");
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return fail(RSFT_ERR_CUDA, "cudaSetDevice failed");
+  rsft_status st = ensure_refine(plan, k);
+  if (st != RSFT_OK) return st;
+  cudaError_t e = rsft::launch_refine_eval(plan->refine_geom, plan->tables, plan->refine, plan->ws.folded,
+                                           static_cast<int>(k), const_cast<float*>(d_freq),
+                                           static_cast<float2*>(const_cast<void*>(d_amp)), d_loss, d_grad_freq,
+                                           static_cast<float2*>(d_grad_amp), d_hdiag, 0.f,
+                                           static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? RSFT_OK : cuda_fail(e, "rsft_refine_eval");
+}
+
 rsft_status rsft_refine(rsft_plan* plan, const void* d_cube, int64_t k, float* d_freq, void* d_amp,
                         int32_t steps, float lr, void* stream) {
-  (void)plan;
-  (void)d_cube;
-  (void)k;
-  (void)d_freq;
-  (void)d_amp;
-  (void)steps;
-  (void)lr;
-  (void)stream;
-  return fail(RSFT_ERR_UNSUPPORTED, "rsft_refine is not implemented yet");
+  if (!plan || !d_cube || k < 1 || !d_freq || !d_amp || steps < 0 || !(lr > 0.f))
+    return fail(RSFT_ERR_INVALID_ARG, "NULL plan, cube or tones, k < 1, steps < 0 or lr <= 0");
+  if (!plan->has_device) return fail(RSFT_ERR_INVALID_ARG, "host-only plan cannot execute");
+  if (k > (1 << 20)) return fail(RSFT_ERR_UNSUPPORTED, "more than 2^20 tones");
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return fail(RSFT_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rsft_status st = ensure_refine(plan, k);
+  if (st == RSFT_OK) st = fold_cube(plan, d_cube, s);
+  if (st != RSFT_OK) return st;
+  for (int it = 0; it < steps; ++it) {
+    cudaError_t e = rsft::launch_refine_eval(plan->refine_geom, plan->tables, plan->refine, plan->ws.folded,
+                                             static_cast<int>(k), d_freq, static_cast<float2*>(d_amp), nullptr,
+                                             nullptr, nullptr, nullptr, lr, s);
+    if (e != cudaSuccess) return cuda_fail(e, "rsft_refine");
+  }
+  return RSFT_OK;
 }
 
 const char* rsft_status_string(rsft_status s) {

@@ -115,7 +115,32 @@ struct Workspace {
   int64_t vote_words;
 };
 
+// Bucket-domain refinement: geometry and scratch (see refine.cu).
+struct RefineGeom {
+  int ndim, loops;
+  int64_t n[kMaxDim], b[kMaxDim], m[kMaxDim];
+  int b_shift[kMaxDim];
+  int boff[kMaxDim];  // offset of dimension d in a tone's sum_d B_d responses
+  int sumb;
+  int64_t total_b;
+};
+
+struct RefineWork {
+  float2* gres = nullptr;   // [L][K][sum B_d] per-dimension tone responses g
+  float2* gder = nullptr;   // [L][K][sum B_d] their frequency derivatives g'
+  float2* resid = nullptr;  // [L][B] residual buckets, source residue order
+  double* partial = nullptr;
+  int parts = 0;            // residual blocks (loss partial sums)
+  float* contr = nullptr;   // [L][K][3 + 5 kMaxDim + kMaxDim (kMaxDim - 1)] contractions
+  int64_t k_cap = 0;
+};
+
 // Launchers (return cudaSuccess or the launch error).
+// Loss, gradient and Gauss-Newton diagonal of K tones against the folded buckets; with lr > 0
+// the tones are also updated in place by a damped diagonal Gauss-Newton step.
+cudaError_t launch_refine_eval(const RefineGeom& rg, const DeviceTables& t, const RefineWork& w,
+                               const float2* folded, int K, float* freq, float2* amp, double* loss,
+                               float* grad_freq, float2* grad_amp, float* hdiag, float lr, cudaStream_t stream);
 // Exclusive scan of n u32 counts into offsets[0..n] (offsets[n] = total), total also to *total.
 cudaError_t launch_count_scan(const uint32_t* counts, int64_t n, uint64_t* offsets, int64_t* total,
                               cudaStream_t stream);

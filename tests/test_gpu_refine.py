@@ -1,0 +1,126 @@
+"""Bucket-domain refinement on the GPU: loss and gradients against the FP64 oracle, the
+autograd Function against the C call, central differences of the GPU loss, and the
+refinement loop reducing off-grid frequency error."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_1610_01050_gb300 as R
+from paper_1610_01050_gb300.autograd import BucketResidual
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1610_01050_gb300 import build as B
+    B.build()
+    R.load_library()
+
+
+def _setup(n, b, loops, true_f, true_a, noise, seed, df):
+    rng = np.random.default_rng(seed)
+    cube = O.tone_field(n, true_f, true_a)
+    cube = cube + noise * (rng.standard_normal(n) + 1j * rng.standard_normal(n))
+    cube64 = cube.astype(np.complex64)
+    f0 = (np.asarray(true_f) + df).astype(np.float32)
+    a0 = (np.asarray(true_a) * (0.9 + 0.1j)).astype(np.complex64)
+    plan = R.rsft_plan_create(R.make_desc(n, b, loops, seed=seed, atten_db=50.0, p_fa1=0.05, mu=1))
+    x = torch.from_numpy(cube64).cuda()
+    R.rsft_refine_prepare(plan, x)
+    op = O.make_plan(n, b, loops, seed=seed, atten_db=50.0, pfa1=0.05, mu=1)
+    return plan, x, cube64.astype(np.complex128), f0, a0, op
+
+
+def _eval(plan, f0, a0):
+    f = torch.from_numpy(f0).cuda()
+    a = torch.from_numpy(a0).cuda()
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    gf = torch.zeros_like(f)
+    ga = torch.zeros_like(a)
+    hd = torch.zeros((len(a0), f0.shape[1] + 1), dtype=torch.float32, device="cuda")
+    R.rsft_refine_eval(plan, f, a, loss=loss, grad_freq=gf, grad_amp=ga, hdiag=hd)
+    torch.cuda.synchronize()
+    return float(loss.item()), gf.cpu().numpy(), ga.cpu().numpy(), hd.cpu().numpy()
+
+
+CASES = [
+    ("2d", (32, 16), (8, 4), 3, [[0.2031, 0.4106], [0.6719, 0.0833]], [1.3 - 0.4j, 0.6 + 0.9j]),
+    ("3d", (16, 16, 8), (4, 4, 2), 4, [[0.11, 0.52, 0.33], [0.71, 0.27, 0.81], [0.43, 0.91, 0.05]],
+     [1.0 + 0.2j, -0.5 + 0.7j, 0.8 - 0.8j]),
+    ("2d_wide", (128, 64), (16, 8), 5, [[0.301, 0.627], [0.702, 0.114]], [2.0 + 0.0j, 0.0 - 1.5j]),
+]
+
+
+@pytest.mark.parametrize("name,n,b,loops,tf,ta", CASES, ids=[c[0] for c in CASES])
+def test_loss_and_gradient_match_the_oracle(name, n, b, loops, tf, ta):
+    df = 0.6 / np.asarray(n, dtype=np.float64)  # 0.6 bin off in every dimension
+    plan, _, cube, f0, a0, op = _setup(n, b, loops, np.asarray(tf), np.asarray(ta), 0.05, 3, df)
+    loss, gf, ga, hd = _eval(plan, f0, a0)
+    ref_loss = O.refine_loss(op, cube, f0.astype(np.float64), a0.astype(np.complex128))
+    rgf, rgre, rgim = O.refine_grad(op, cube, f0.astype(np.float64), a0.astype(np.complex128))
+    assert loss == pytest.approx(ref_loss, rel=1e-4)
+    np.testing.assert_allclose(gf, rgf, rtol=0, atol=1e-3 * np.abs(rgf).max())
+    ramp = np.stack([rgre, rgim], axis=1)
+    np.testing.assert_allclose(np.stack([ga.real, ga.imag], axis=1), ramp, rtol=0, atol=1e-3 * np.abs(ramp).max())
+    assert np.all(hd > 0)
+
+
+def test_autograd_function_returns_the_library_gradient():
+    n, b, loops, tf, ta = CASES[1][1:]
+    plan, _, _, f0, a0, _ = _setup(n, b, loops, np.asarray(tf), np.asarray(ta), 0.05, 4, 0.02)
+    loss, gf, ga, _ = _eval(plan, f0, a0)
+    f = torch.from_numpy(f0).cuda().requires_grad_(True)
+    ari = torch.view_as_real(torch.from_numpy(a0).cuda()).clone().requires_grad_(True)
+    e = BucketResidual.apply(f, ari, plan)
+    (g1, g2) = torch.autograd.grad(e, [f, ari])
+    assert float(e.detach()) == pytest.approx(loss, rel=1e-6)
+    np.testing.assert_array_equal(g1.cpu().numpy(), gf)
+    np.testing.assert_array_equal(g2.cpu().numpy(), np.stack([ga.real, ga.imag], axis=1))
+
+
+def test_gpu_loss_central_differences():
+    n, b, loops, tf, ta = CASES[2][1:]
+    plan, _, _, f0, a0, _ = _setup(n, b, loops, np.asarray(tf), np.asarray(ta), 0.05, 5, 0.3 / np.asarray(n))
+    _, gf, ga, _ = _eval(plan, f0, a0)
+    for k in range(len(a0)):
+        for d in range(2):
+            h = 0.01 / n[d]  # a hundredth of a bin
+            fp, fm = f0.copy(), f0.copy()
+            fp[k, d] += h
+            fm[k, d] -= h
+            fd = (_eval(plan, fp, a0)[0] - _eval(plan, fm, a0)[0]) / (2 * h)
+            assert fd == pytest.approx(gf[k, d], rel=1e-2, abs=1e-3 * np.abs(gf).max())
+        h = 1e-3 * abs(a0[k])
+        for unit, g in ((1.0, ga[k].real), (1j, ga[k].imag)):
+            ap, am = a0.copy(), a0.copy()
+            ap[k] += h * unit
+            am[k] -= h * unit
+            fd = (_eval(plan, f0, ap)[0] - _eval(plan, f0, am)[0]) / (2 * h)
+            assert fd == pytest.approx(g, rel=1e-2, abs=1e-3 * np.abs(ga).max())
+
+
+def test_refinement_reduces_off_grid_frequency_error():
+    n, b, loops = (256, 256), (16, 16), 8
+    rng = np.random.default_rng(21)
+    k = 6
+    bins = np.stack([rng.choice(np.arange(8, 248, 40), k, replace=False),
+                     rng.choice(np.arange(8, 248, 40), k, replace=False)], axis=1).astype(np.float64)
+    true_f = (bins + rng.uniform(-0.45, 0.45, (k, 2))) / np.asarray(n)
+    true_a = (rng.uniform(1.0, 2.0, k) * np.exp(2j * np.pi * rng.uniform(0, 1, k)))
+    cube = O.tone_field(n, true_f, true_a) + 0.02 * (rng.standard_normal(n) + 1j * rng.standard_normal(n))
+    plan = R.rsft_plan_create(R.make_desc(n, b, loops, seed=21, atten_db=60.0, p_fa1=0.05, mu=1))
+    x = torch.from_numpy(cube.astype(np.complex64)).cuda()
+    f = torch.from_numpy((np.round(true_f * np.asarray(n)) / np.asarray(n)).astype(np.float32)).cuda()
+    a = torch.from_numpy((true_a * 0.8).astype(np.complex64)).cuda()
+    err0 = np.abs(f.cpu().numpy() - true_f) * np.asarray(n)
+    R.rsft_refine(plan, x, k, f, a, 20, 0.7)
+    torch.cuda.synchronize()
+    err1 = np.abs(f.cpu().numpy() - true_f) * np.asarray(n)
+    rmse0, rmse1 = math.sqrt(np.mean(err0 ** 2)), math.sqrt(np.mean(err1 ** 2))
+    assert rmse1 < 0.1 * rmse0, (rmse0, rmse1)
+    assert np.max(np.abs(a.cpu().numpy() - true_a) / np.abs(true_a)) < 0.05
