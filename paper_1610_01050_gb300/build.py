@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT, "librsft.so")
 
-CU_SOURCES = ["capi.cu", "fold.cu", "spectrum.cu", "votes.cu", "bartlett.cu", "refine.cu"]
+CU_SOURCES = ["capi.cu", "fold.cu", "fold_tc.cu", "spectrum.cu", "votes.cu", "bartlett.cu", "refine.cu"]
 CPP_SOURCES = ["plan_host.cpp"]
 HEADERS = ["device.cuh", "tma.cuh", "plan_host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <array>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -58,9 +59,12 @@ struct rsft_plan {
   bool snr_cached = false;
   double snr_db = 0.0;
   bool timing = false;
-  int fold_copy_mode = -1;          // last fold launch: 0 per-row bulk copies, 3/5 tensor box rank
+  int fold_copy_mode = -1;          // last fold launch: 0 per-row bulk copies, 3/5 tensor box rank,
+                                    // 100 + rank on the tensor cores
+  bool fold_tc = false;             // the fold runs on the tensor cores (fold_tc.cu)
   std::vector<int> h_sinvb;                 // [L][D] sigma^{-1} mod B_d (fold kernel parameters)
   std::vector<unsigned short> h_slots, h_xdig;
+  std::vector<unsigned char> h_xres;        // residue index of each column of a 64-column chunk
   std::vector<cudaEvent_t> event_pool;
   std::vector<std::array<cudaEvent_t, 6>> pending;  // events of timed executes not yet summed
   double stage_ms[6] = {0, 0, 0, 0, 0, 0};
@@ -563,6 +567,12 @@ rsft_status build_device(rsft_plan* p) {
     p->tables.h_sinvb = p->h_sinvb.data();
     if (rsft::fold_smem_bytes(g, fs, std::min(L, rsft::kMaxLoopGroup)) > 227 * 1024)
       return fail(RSFT_ERR_UNSUPPORTED, "fold schedule needs more shared memory than a CTA has");
+    // the tensor-core fold takes schedules of whole 64-column rows (RSFT_FOLD=simt keeps the SIMT fold)
+    const char* env = std::getenv("RSFT_FOLD");
+    p->fold_tc = rsft::fold_tc_supported(g, fs) && !(env && std::string(env) == "simt");
+    p->h_xres.assign(64, 0);
+    for (int c = 0; c < 64 && c < fs.width; ++c) p->h_xres[c] = static_cast<unsigned char>(residue(c));
+    p->tables.h_xres = p->h_xres.data();
   }
   if ((st = build_fold_tables(p, rsft::kMaxLoopGroup, &p->tables.ftable, &p->tables.fcolw)) != RSFT_OK) return st;
   p->tables.rowmask = nullptr;
@@ -693,6 +703,20 @@ void release(rsft_plan* p) {
   delete p;
 }
 
+// One fold launch of loops [l0, l0 + lg): the tensor-core fold where the plan has one, else
+// the SIMT fold (and its partial-sum reduction when the schedule chunks rows or columns).
+cudaError_t fold_group(rsft_plan* p, const rsft::DeviceTables& ft, bool tensor_cores, const void* cube, int l0,
+                       int lg, rsft::Workspace& ws, cudaStream_t stream) {
+  const rsft::Geometry& g = p->geom;
+  if (tensor_cores)
+    return rsft::launch_fold_tc(g, p->fold, ft, static_cast<const float2*>(cube), l0, lg, ws.folded, ws.err_flag,
+                                &p->fold_copy_mode, stream);
+  cudaError_t e = rsft::launch_fold(g, p->fold, ft, static_cast<const float2*>(cube), l0, lg, ws.folded, ws.partial,
+                                    ws.err_flag, &p->fold_copy_mode, stream);
+  if (e == cudaSuccess && !p->fold.direct) e = rsft::launch_fold_reduce(g, p->fold, ft, l0, lg, ws.partial, ws.folded, stream);
+  return e;
+}
+
 rsft_status run_lane(rsft_plan* p, rsft::Workspace& ws, bool& votes_dirty, bool timed, const void* d_cube,
                      cudaStream_t stream, uint64_t* d_located, uint8_t* d_located_votes, float2* d_amp,
                      uint8_t* d_votes_out, int64_t* d_count, const void* const* d_segments = nullptr) {
@@ -727,13 +751,8 @@ rsft_status run_lane(rsft_plan* p, rsft::Workspace& ws, bool& votes_dirty, bool 
   for (int l0 = 0; l0 < g.loops; l0 += group) {
     const int lg = std::min(group, g.loops - l0);
     const void* cube = d_segments ? d_segments[l0] : d_cube;
-    e = rsft::launch_fold(g, p->fold, ft, static_cast<const float2*>(cube), l0, lg, ws.folded, ws.partial,
-                          ws.err_flag, &p->fold_copy_mode, stream);
+    e = fold_group(p, ft, p->fold_tc && !d_segments, cube, l0, lg, ws, stream);
     if (e != cudaSuccess) return cuda_fail(e, "permute_window_fold");
-    if (!p->fold.direct) {
-      e = rsft::launch_fold_reduce(g, p->fold, ft, l0, lg, ws.partial, ws.folded, stream);
-      if (e != cudaSuccess) return cuda_fail(e, "fold reduce");
-    }
   }
   mark(1);
   for (size_t i = 0; i < p->passes.size(); ++i) {
@@ -1289,10 +1308,7 @@ rsft_status fold_cube(rsft_plan* p, const void* d_cube, cudaStream_t stream) {
   rsft::Workspace& ws = p->ws;
   for (int l0 = 0; l0 < g.loops; l0 += rsft::kMaxLoopGroup) {
     const int lg = std::min(rsft::kMaxLoopGroup, g.loops - l0);
-    cudaError_t e = rsft::launch_fold(g, p->fold, p->tables, static_cast<const float2*>(d_cube), l0, lg, ws.folded,
-                                      ws.partial, ws.err_flag, &p->fold_copy_mode, stream);
-    if (e == cudaSuccess && !p->fold.direct)
-      e = rsft::launch_fold_reduce(g, p->fold, p->tables, l0, lg, ws.partial, ws.folded, stream);
+    cudaError_t e = fold_group(p, p->tables, p->fold_tc, d_cube, l0, lg, ws, stream);
     if (e != cudaSuccess) return cuda_fail(e, "permute_window_fold");
   }
   return RSFT_OK;

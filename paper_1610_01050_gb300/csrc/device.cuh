@@ -94,6 +94,7 @@ struct DeviceTables {
   const uint64_t* rowmask;          // rows <= 64: per loop, the candidate mask of every detection pattern of a
                                     // plane ([L][2^b_in], b_in <= 8) or of each inner bucket ([L][b_in])
   const uint16_t* kb16;             // per row dimension d < d_v: [L][N_d] bucket offset (Def. 3) of index i_d
+  const unsigned char* h_xres;      // host: residue index of each column of a 64-column chunk
 };
 
 struct Workspace {
@@ -173,6 +174,12 @@ cudaError_t vote_rows_small_residency(const Geometry& g, const VoteRowSchedule& 
                                       int* warps_per_sm);
 
 int fold_smem_bytes(const Geometry& g, const FoldSchedule& fs, int lg);
+
+// Tensor-core fold (fold_tc.cu): schedules with 64-column chunks, two or more classes side
+// by side, whole classes, rows in stages of 16.
+bool fold_tc_supported(const Geometry& g, const FoldSchedule& fs);
+cudaError_t launch_fold_tc(const Geometry& g, const FoldSchedule& fs, const DeviceTables& t, const float2* cube,
+                           int loop0, int lg, float2* folded, int* err, int* copy_mode, cudaStream_t stream);
 
 // Message returned by rsft_last_error() on this thread.
 void set_last_error(const char* msg);

@@ -42,43 +42,6 @@ __host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// Tiled tensor copy global -> shared of one box (rank 3 or 5), completion counted on `bar`.
-__device__ __forceinline__ void tensor_g2s_3d(void* dst, const void* tmap, int c0, int c1, int c2, uint64_t* bar,
-                                              uint64_t pol) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(
-          smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "l"(pol)
-      : "memory");
-}
-
-__device__ __forceinline__ void tensor_g2s_5d(void* dst, const void* tmap, int c0, int c1, int c2, int c3, int c4,
-                                              uint64_t* bar, uint64_t pol) {
-  asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, %3, %4, %5, %6}], [%7], %8;" ::"r"(
-          smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar)),
-      "l"(pol)
-      : "memory");
-}
-
-// Wait until the barrier completes the phase of the given parity (try_wait suspends the
-// thread for a while on each attempt).  False if the CTA already gave up, or if this wait
-// times out (then the CTA's abort flag and the global error flag are set).
-__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (true) {
-    if (*abort_flag) return false;
-    if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - t0 > kWaitLimitNs) {
-      *abort_flag = 1;
-      atomicExch(err, 1);
-      return false;
-    }
-  }
-}
-
 constexpr int kThreads = kFoldConsumers;   // 256 threads, two columns each
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxRing = 8;                // shared-memory stages

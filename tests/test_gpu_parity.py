@@ -59,6 +59,10 @@ SMALL = [
     ("2d_flat_support", (256, 256), (16, 16), 8, dict(support=(64, 64), pfa1=0.02, mu=2)),
     ("3d_design", (128, 64, 32), (16, 8, 4), 12, dict(atten=80.0, p_fa=1e-5, k_max=4)),
     ("4d_rows_chunked", (16, 32, 64, 32), (4, 8, 8, 4), 9, dict(pfa1=0.03, mu=2)),
+    # whole 64-column rows: the tensor-core fold (rank-3 and rank-5 boxes, two loop groups)
+    ("2d_tc", (512, 64), (16, 16), 4, dict(pfa1=0.02, mu=1)),
+    ("3d_tc", (128, 32, 64), (16, 4, 8), 12, dict(pfa1=0.03, mu=3)),
+    ("3d_tc_two_groups", (32, 64, 64), (4, 8, 4), 20, dict(pfa1=0.05, mu=5)),
 ]
 
 
@@ -73,6 +77,33 @@ def test_parity_small(name, n, b, loops, extra):
     rep = compare_full(g, ref, op)
     print(f"parity {name}: {rep}")
     assert rep["detected"] > 0
+
+
+TC_CASES = [c for c in SMALL if c[0] in ("2d_tc", "3d_tc", "3d_tc_two_groups", "4d_lg16")]
+
+
+@pytest.mark.parametrize("name,n,b,loops,extra", TC_CASES, ids=[c[0] for c in TC_CASES])
+def test_tensor_core_fold_and_simt_fold(name, n, b, loops, extra, monkeypatch):
+    """Both fold kernels (tcgen05 3xTF32 and SIMT FP32) meet the oracle on the same plan geometry."""
+    seed = zlib.crc32(name.encode()) % 1000 + 3
+    nv = 1.5
+    cube, _ = tone_input(n, b, 6, seed, noise_var=nv)
+    outs = {}
+    for kind in ("tc", "simt"):
+        if kind == "simt":
+            monkeypatch.setenv("RSFT_FOLD", "simt")
+        else:
+            monkeypatch.delenv("RSFT_FOLD", raising=False)
+        d, op = make_pair(n, b, loops, seed=seed, noise_var=nv, **extra)
+        g = gpu_run(d, cube)
+        mode = int(R.rsft_plan_get(g["plan"], R.RSFT_GET_FOLD_COPY)[0])
+        assert (mode >= 100) == (kind == "tc"), (kind, mode)
+        outs[kind] = g
+    ref = O.rsft(op, cube.astype(np.complex128))
+    for kind, g in outs.items():
+        rep = compare_full(g, ref, op)
+        print(f"{name} {kind}: {rep}")
+    assert rel_err(outs["tc"]["folded"], outs["simt"]["folded"], axis_rms=True) < 2 * REL_TOL
 
 
 VOTE_CASES = [
