@@ -82,15 +82,15 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def profile_traffic(workload):
+def profile_traffic(workload, source):
     """DRAM bytes per fold launch from the committed ncu summary, if it matches the kernel source."""
     path = os.path.join(ROOT, "profiles", f"permute_window_fold_{workload}.txt")
-    src = os.path.join(ROOT, "paper_1610_01050_gb300", "csrc", "fold.cu")
+    src = os.path.join(ROOT, "paper_1610_01050_gb300", "csrc", source)
     try:
         text = open(path).read()
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         vals = dict(line.split(":", 1) for line in text.splitlines() if ":" in line)
-        if vals.get("fold_cu_sha256_16", "").strip() != digest:
+        if vals.get("source", "").strip() != source or vals.get("source_sha256_16", "").strip() != digest:
             return None
         return float(vals["dram_bytes_per_launch"].strip())
     except Exception:
@@ -462,7 +462,9 @@ def run_ours(args):
     fold_s = stage[0] / timed / 1e3
     peak, peak_kind = measured_peak()
     achieved = fold_bytes / fold_s / 1e9
-    traffic = profile_traffic(args.workload)
+    tensor_fold = int(R.rsft_plan_get(plan, R.RSFT_GET_FOLD_COPY)[0]) >= 100
+    fold_source = "fold_tc.cu" if tensor_fold else "fold.cu"
+    traffic = profile_traffic(args.workload, fold_source)
     stages = {k: stage[i] / timed * 1e3 for i, k in
               enumerate(["fold_us", "fft_detect_us", "vote_scatter_us", "stage2_us", "median_us", "execute_us"])}
 
@@ -519,7 +521,8 @@ def run_ours(args):
             "detection": {"pd": float(np.mean(pd)), "pfa": float(np.mean(pfa)), "located_per_frame": float(np.mean(n_loc)),
                           "note": "Pd: targets located within +-1 bin per dim; Pfa: located cells outside +-3-bin target boxes"},
             "stages_us_per_frame": stages,
-            "roofline": {"bound": "hbm", "kernel": "permute_window_fold", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "hbm", "kernel": "permute_window_fold (" + ("fold_tc_kernel: tcgen05 3xTF32"
+                         if tensor_fold else "fold_kernel: SIMT FP32") + ")", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_kind} (copy bandwidth)",
                          "traffic": traffic, "algorithmic_bytes_per_launch": fold_bytes},
             "e2e": {"value": e2e_val, "unit": "frames/s", "h2d_bytes_per_step": int(np.prod(wl.shape)) * 8,

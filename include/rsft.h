@@ -181,9 +181,9 @@ enum {
                              * read once per loop group plus the bucket writes               */
   RSFT_GET_FOLD_COPY = 16   /* int32 [1]     how the last fold streamed the cube: 0 one bulk copy
                              * per row, 3 or 5 one tensor-map box per stage (rank) into the SIMT
-                             * fold, 103 or 105 the same boxes into the tensor-core fold (chosen
-                             * for whole 64-column rows; environment RSFT_FOLD=simt at plan
-                             * creation keeps the SIMT fold), -1 none yet                       */
+                             * fold, 103 or 105 the same boxes into the tensor-core fold (whole
+                             * 64-column rows, chosen by environment RSFT_FOLD=tc at plan
+                             * creation), -1 none yet                                            */
 };
 rsft_status rsft_plan_get(const rsft_plan* plan, int32_t what, void* out, size_t bytes);
 

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <array>
 #include <cstdio>
 #include <cstdlib>
@@ -131,6 +132,8 @@ float2 to_f2(cplx v) { return make_float2(static_cast<float>(v.real()), static_c
 
 // Choose how the fold splits rows and columns (see fold.cu).  Costs are relative to
 // the 8 bytes each cube element costs: per-element row-weight setup and partial-sum traffic.
+constexpr int64_t kSms = 152;  // streaming multiprocessors the schedule is balanced for
+
 bool choose_fold_schedule(const rsft::Geometry& g, rsft::FoldSchedule& out) {
   const int lg = std::min(g.loops, rsft::kMaxLoopGroup);
   double best = 1e300;
@@ -155,41 +158,49 @@ bool choose_fold_schedule(const rsft::Geometry& g, rsft::FoldSchedule& out) {
     if (xcount > width || xcount > 65535) continue;
     if (classes > (int64_t(1) << 30)) continue;
     // C classes side by side in a step: consecutive residues of the innermost row dimension
-    int64_t cps = 1;
+    int64_t cmax = 1;
     if (d_in >= 1)
-      while (cps * 2 * width <= 2 * rsft::kFoldConsumers && cps * 2 <= g.b[d_in - 1] && cps * 2 <= classes) cps *= 2;
-    const int64_t rpc = rows_pc;  // whole classes per unit (direct output unless columns are chunked)
-    const int64_t crow = std::min<int64_t>(2 * rsft::kFoldConsumers / (width * cps), rpc);
-    const int64_t row_chunks = 1;
-    const int64_t col_chunks = row_len / width;
-    const int64_t units = classes / cps * row_chunks * col_chunks;
-    if (units > 0x7fffffff || rpc > (int64_t(1) << 30)) continue;
-    const double setup = static_cast<double>(lg) / static_cast<double>(width * cps * crow / 2);
-    const double partial = (row_chunks * col_chunks > 1)
-                               ? 2.0 * lg * static_cast<double>(xcount) / static_cast<double>(rpc * width)
-                               : 0.0;
-    const double idle = 1.0 - static_cast<double>(width * cps * crow) / (2 * rsft::kFoldConsumers);
-    const double fill = units < 2 * 152 ? static_cast<double>(2 * 152 - units) / (2 * 152) : 0.0;
-    // rows without a tensor map go as one bulk copy each: small ones are request-rate bound
-    const bool tensor_map = d_in >= 1 && d_in <= 2 && width <= 256;
-    const double copies = (!tensor_map && width < 256) ? 1.0 : 0.0;
-    const double cost = 0.5 * setup + partial + fill + idle + copies;
-    if (cost < best) {
-      best = cost;
-      found = true;
-      out.d_in = d_in;
-      out.row_len = row_len;
-      out.width = static_cast<int>(width);
-      out.col_chunks = static_cast<int>(col_chunks);
-      out.classes = static_cast<int>(classes);
-      out.rows_per_class = static_cast<int>(rows_pc);
-      out.rows_per_chunk = static_cast<int>(rpc);
-      out.row_chunks = static_cast<int>(row_chunks);
-      out.xcount = static_cast<int>(xcount);
-      out.direct = (row_chunks * col_chunks == 1) ? 1 : 0;
-      out.cps = static_cast<int>(cps);
-      out.crow = static_cast<int>(crow);
-      out.groups = static_cast<int>(classes / cps);
+      while (cmax * 2 * width <= 2 * rsft::kFoldConsumers && cmax * 2 <= g.b[d_in - 1] && cmax * 2 <= classes) cmax *= 2;
+    for (int64_t cps = 1; cps <= cmax; cps *= 2) {
+      const int64_t rpc = rows_pc;  // whole classes per unit (direct output unless columns are chunked)
+      const int64_t crow = std::min<int64_t>(2 * rsft::kFoldConsumers / (width * cps), rpc);
+      const int64_t row_chunks = 1;
+      const int64_t col_chunks = row_len / width;
+      const int64_t units = classes / cps * row_chunks * col_chunks;
+      if (units > 0x7fffffff || rpc > (int64_t(1) << 30)) continue;
+      const double setup = static_cast<double>(lg) / static_cast<double>(width * cps * crow / 2);
+      const double partial = (row_chunks * col_chunks > 1)
+                                 ? 2.0 * lg * static_cast<double>(xcount) / static_cast<double>(rpc * width)
+                                 : 0.0;
+      const double idle = 1.0 - static_cast<double>(width * cps * crow) / (2 * rsft::kFoldConsumers);
+      // persistent CTAs (two per SM) take units round robin and each runs at about a fixed
+      // rate: the busiest CTA's units against an even share, plus a per-unit cost (epilogue,
+      // ring refill) worth about 3072 elements of the row loop
+      const double slots = 2.0 * kSms;
+      const double per_cta = std::ceil(static_cast<double>(units) / slots);
+      const double balance = std::min(4.0, per_cta / (static_cast<double>(units) / slots) - 1.0) +
+                             3072.0 / static_cast<double>(cps * rpc * width);
+      // rows without a tensor map go as one bulk copy each: small ones are request-rate bound
+      const bool tensor_map = d_in >= 1 && d_in <= 2 && width <= 256;
+      const double copies = (!tensor_map && width < 256) ? 1.0 : 0.0;
+      const double cost = 0.5 * setup + partial + balance + idle + copies;
+      if (cost < best - 1e-9) {
+        best = cost;
+        found = true;
+        out.d_in = d_in;
+        out.row_len = row_len;
+        out.width = static_cast<int>(width);
+        out.col_chunks = static_cast<int>(col_chunks);
+        out.classes = static_cast<int>(classes);
+        out.rows_per_class = static_cast<int>(rows_pc);
+        out.rows_per_chunk = static_cast<int>(rpc);
+        out.row_chunks = static_cast<int>(row_chunks);
+        out.xcount = static_cast<int>(xcount);
+        out.direct = (row_chunks * col_chunks == 1) ? 1 : 0;
+        out.cps = static_cast<int>(cps);
+        out.crow = static_cast<int>(crow);
+        out.groups = static_cast<int>(classes / cps);
+      }
     }
   }
   return found;
@@ -567,9 +578,9 @@ rsft_status build_device(rsft_plan* p) {
     p->tables.h_sinvb = p->h_sinvb.data();
     if (rsft::fold_smem_bytes(g, fs, std::min(L, rsft::kMaxLoopGroup)) > 227 * 1024)
       return fail(RSFT_ERR_UNSUPPORTED, "fold schedule needs more shared memory than a CTA has");
-    // the tensor-core fold takes schedules of whole 64-column rows (RSFT_FOLD=simt keeps the SIMT fold)
+    // the tensor-core fold (schedules of whole 64-column rows) on request: RSFT_FOLD=tc
     const char* env = std::getenv("RSFT_FOLD");
-    p->fold_tc = rsft::fold_tc_supported(g, fs) && !(env && std::string(env) == "simt");
+    p->fold_tc = rsft::fold_tc_supported(g, fs) && env && std::string(env) == "tc";
     p->h_xres.assign(64, 0);
     for (int c = 0; c < 64 && c < fs.width; ++c) p->h_xres[c] = static_cast<unsigned char>(residue(c));
     p->tables.h_xres = p->h_xres.data();

@@ -45,7 +45,7 @@ __host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 constexpr int kThreads = kFoldConsumers;   // 256 threads, two columns each
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxRing = 8;                // shared-memory stages
-constexpr int kStepsPerStage = 4;          // row steps (2 * threads elements each) per stage
+constexpr int kStepsPerStage = 8;          // row steps (2 * threads elements each) per stage
 constexpr int kStepElems = 2 * kThreads;
 constexpr int kStageBytes = kStepsPerStage * kStepElems * 8;
 constexpr int kSmemBudget = 110 * 1024;    // two CTAs per SM

@@ -8,8 +8,11 @@
 // i.e. one real GEMM D[128 x 32] = A[128 x R] B[R x 32] per class with A = X^T and the
 // first 2 LG columns of B holding (c, d).  tcgen05.mma kind::tf32 runs it with A and the
 // accumulator in tensor memory and B in shared memory; FP32 accuracy comes from the
-// three-term split A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi with hi = the operand truncated
-// to TF32 and lo = operand - hi.  The high-low products share one instruction:
+// three-term split A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi with hi = the operand rounded to
+// the nearest TF32 value and lo = operand - hi (exact in FP32, then itself rounded to TF32:
+// the tensor core would truncate it), which leaves 2^-22 of each product.  A tensor-core
+// instruction at M = 128 takes the same time for any N up to 256, so the instruction count
+// (two per 8 rows of a class) sets the kernel's floor and the N halves are free.  The high-low products share one instruction:
 // A_hi x [B_hi | B_lo] (N = 64, the two B parts adjacent in shared memory) accumulates hh in
 // TMEM columns [0, 32) and hl in [32, 64); then A_lo x B_hi (N = 32) adds lh to [0, 32).  The
 // epilogue applies the column weights and sums the columns of equal residue in a fixed order
@@ -102,7 +105,12 @@ __host__ __device__ constexpr uint32_t tf32_idesc(int m, int n) {
          (static_cast<uint32_t>(m >> 4) << 24);
 }
 
-__device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// x rounded to the nearest TF32 value (ties away from zero); x - tf32_rn(x) is exact in FP32
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
 
 // D (TMEM) (+)= A (TMEM, lane m = row m, column k) x B (shared memory descriptor)^T
 __device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, int accumulate) {
@@ -361,8 +369,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) fold_tc_kernel(const __grid_con
 #pragma unroll
         for (int r = 0; r < kTcRows; ++r) {
           const float x = xs[(r * kTcClasses + cgrp) * kTcM + m];
-          hi[r] = tf32_trunc(x);
-          lo[r] = x - hi[r];
+          hi[r] = tf32_rn(x);
+          lo[r] = tf32_rn(x - hi[r]);
         }
         const uint32_t acol = taddr + lanes + static_cast<uint32_t>(kABase + b * kACols + cgrp * 2 * kTcRows);
         tmem_st16(acol, hi);
@@ -376,11 +384,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) fold_tc_kernel(const __grid_con
             const int kr = e & 7, l = (e >> 3) % LG, ckb = (e >> 3) / LG;
             float* bt = reinterpret_cast<float*>(bb + ckb * kBSet);
             const float2 w = wv[t];
-            const float hr = tf32_trunc(w.x), hm = tf32_trunc(w.y);
+            const float hr = tf32_rn(w.x), hm = tf32_rn(w.y);
             bt[kmajor(l, kr)] = hr;
             bt[kmajor(LG + l, kr)] = hm;
-            bt[kTileB / 4 + kmajor(l, kr)] = w.x - hr;
-            bt[kTileB / 4 + kmajor(LG + l, kr)] = w.y - hm;
+            bt[kTileB / 4 + kmajor(l, kr)] = tf32_rn(w.x - hr);
+            bt[kTileB / 4 + kmajor(LG + l, kr)] = tf32_rn(w.y - hm);
           }
         }
         // A in TMEM and B visible to the tensor core, then the slot back to the producer

@@ -84,14 +84,15 @@ TC_CASES = [c for c in SMALL if c[0] in ("2d_tc", "3d_tc", "3d_tc_two_groups", "
 
 @pytest.mark.parametrize("name,n,b,loops,extra", TC_CASES, ids=[c[0] for c in TC_CASES])
 def test_tensor_core_fold_and_simt_fold(name, n, b, loops, extra, monkeypatch):
-    """Both fold kernels (tcgen05 3xTF32 and SIMT FP32) meet the oracle on the same plan geometry."""
+    """Both fold kernels (the default SIMT FP32 and the opt-in tcgen05 3xTF32) meet the oracle on the
+    same plan geometry."""
     seed = zlib.crc32(name.encode()) % 1000 + 3
     nv = 1.5
     cube, _ = tone_input(n, b, 6, seed, noise_var=nv)
     outs = {}
     for kind in ("tc", "simt"):
-        if kind == "simt":
-            monkeypatch.setenv("RSFT_FOLD", "simt")
+        if kind == "tc":
+            monkeypatch.setenv("RSFT_FOLD", "tc")
         else:
             monkeypatch.delenv("RSFT_FOLD", raising=False)
         d, op = make_pair(n, b, loops, seed=seed, noise_var=nv, **extra)
@@ -241,6 +242,15 @@ def _full_oracle_case(name, frame=0):
 def test_parity_full_workload(name):
     rep, g, ref, tg, wl = _full_oracle_case(name)
     print(f"parity {name}: {rep}")
+    assert rep["detected"] > 0 and rep["located"] > 0
+
+
+def test_tensor_core_fold_full_workload(monkeypatch):
+    """The opt-in tcgen05 fold on the full 1024x256x64 radar workload, every stage against the oracle."""
+    monkeypatch.setenv("RSFT_FOLD", "tc")
+    rep, g, ref, tg, wl = _full_oracle_case("c2_3d_radar")
+    assert int(R.rsft_plan_get(g["plan"], R.RSFT_GET_FOLD_COPY)[0]) >= 100
+    print(f"parity c2_3d_radar (tensor-core fold): {rep}")
     assert rep["detected"] > 0 and rep["located"] > 0
 
 
