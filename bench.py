@@ -84,7 +84,8 @@ def measured_peak():
 
 def profile_traffic(workload, source):
     """DRAM bytes per fold launch from the committed ncu summary, if it matches the kernel source."""
-    path = os.path.join(ROOT, "profiles", f"permute_window_fold_{workload}.txt")
+    tag = "_tc" if source == "fold_tc.cu" else ""
+    path = os.path.join(ROOT, "profiles", f"permute_window_fold{tag}_{workload}.txt")
     src = os.path.join(ROOT, "paper_1610_01050_gb300", "csrc", source)
     try:
         text = open(path).read()
