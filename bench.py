@@ -349,6 +349,83 @@ def segment_mode(R, torch, plan, wl, cubes, stream, dev, ws, located, amp, count
             "note": "one 1024x256x64 segment per loop, taken round-robin from the ring of frames"}
 
 
+MIXED = ("c3_small", "c3_mid", "c3_large")
+MIXED_CAP = 1 << 17
+
+
+def mixed_batch(R, torch, ri, dev, ws, stream, n_frames=512, per_shape=2, lanes=4, chunk=64):
+    """Batched frames of uneven shapes: 512 frames drawn uniformly from the three sizes of the
+    mixed-size workload, each shape with its own plan (fold schedule picked by
+    rsft_plan_autotune on one of its frames) and every frame one recorded execute (a CUDA
+    graph) on one of 4 lanes of its plan, launched in chunks with rsft_graph_launch_batch.
+    The same sequence through rsft_execute_async on one stream is the plain comparison."""
+    rng = np.random.default_rng(1610)
+    plans, rings, graphs, outs, tuned = {}, {}, {}, [], {}
+    for name in MIXED:
+        wl = ri.WORKLOADS[name]
+        cubes, nv = [], wl.noise_var
+        for f in range(per_shape):
+            cube, _, _, nv = ri.workload_frame(name, f)
+            cubes.append(torch.from_numpy(cube).to(dev))
+        plan = R.rsft_plan_create(workload_desc(R, wl, nv, ri.frame_seed(wl, 0), max_located=MIXED_CAP))
+        us, chosen = R.rsft_plan_autotune(plan, cubes[0], candidates=4, reps=5, stream=stream)
+        tuned[name] = {"fold_us": us, "candidate": chosen}
+        plans[name], rings[name], graphs[name] = plan, cubes, []
+        for g in range(lanes):  # graph g: resident frame g % per_shape on lane g
+            o = (torch.zeros(MIXED_CAP, dtype=torch.int64, device=dev),
+                 torch.zeros(MIXED_CAP, dtype=torch.complex64, device=dev), torch.zeros(1, dtype=torch.int64, device=dev))
+            outs.append(o)
+            graphs[name].append(R.rsft_graph_create(plan, cubes[g % per_shape], o[2], located=o[0], amp=o[1], lane=g))
+    shape_of = [MIXED[i] for i in rng.integers(0, len(MIXED), n_frames)]
+    seen = {n: 0 for n in MIXED}
+    seq, plain = [], []
+    for name in shape_of:
+        k = seen[name]
+        seen[name] += 1
+        seq.append(graphs[name][k % lanes])
+        plain.append((plans[name], rings[name][k % lanes % per_shape]))
+    frame_bytes = sum(int(np.prod(ri.WORKLOADS[n].shape)) * 8 for n in shape_of)
+
+    def run_graphs(frames):
+        for i in range(0, len(frames), chunk):
+            R.rsft_graph_launch_batch(frames[i:i + chunk], stream=stream)
+
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    loc = torch.zeros(MIXED_CAP, dtype=torch.int64, device=dev)
+    amp = torch.zeros(MIXED_CAP, dtype=torch.complex64, device=dev)
+
+    def run_plain(frames):
+        for plan, x in frames:
+            R.rsft_execute_async(plan, x, count, stream=stream, located=loc, amp=amp)
+
+    run_graphs(seq[:2 * chunk])
+    run_plain(plain[:16])
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    run_graphs(seq)
+    ev[1].record(stream)
+    run_plain(plain)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(ev[0].elapsed_time(ev[1]), ws, dev)
+    ms_plain = max_over_ranks(ev[1].elapsed_time(ev[2]), ws, dev)
+    for name in MIXED:
+        for g in graphs[name]:
+            g.close()
+        plans[name].close()
+    value = whole_job_rate(ws, n_frames, ms)
+    return {"value": value, "unit": "frames/s", "frames": n_frames,
+            "shapes": {n: int(sum(1 for x in shape_of if x == n)) for n in MIXED},
+            "ms_per_frame": ms / n_frames, "hbm_gbs_cube_reads": frame_bytes / (ms / 1e3) / 1e9,
+            "plain": {"value": whole_job_rate(ws, n_frames, ms_plain), "unit": "frames/s",
+                      "note": "the same sequence, one rsft_execute_async per frame on one stream"},
+            "graph_speedup": ms_plain / ms, "autotune": tuned,
+            "note": f"shapes {', '.join('x'.join(map(str, ri.WORKLOADS[n].shape)) for n in MIXED)} (B = N/16 per "
+                    f"dim, L = 10, Pfa = 1e-5), {per_shape} resident frames per shape; one CUDA graph per frame "
+                    f"over {lanes} lanes per plan, {chunk} graphs per rsft_graph_launch_batch"}
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -497,6 +574,7 @@ def run_ours(args):
                        max(1, min(args.steps // 20, 50)))
     dense = dense_comparator(R, torch, wl, nv, cubes, targets, stream, dev, ws, max(1, min(args.steps, 200)),
                              max(3, min(args.warmup, 10)), cap, value)
+    mixed = mixed_batch(R, torch, ri, dev, ws, stream, n_frames=512 if args.steps >= 100 else 64)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -532,6 +610,7 @@ def run_ours(args):
                       "note": "one frame per rsft_execute_async, back to back on one stream",
                       "batched_speedup": value / plain_value, "lanes_tuning_frames_per_s": tune},
             "dense_fft": dense,
+            "mixed_batch": mixed,
             "segment_mode": seg,
             "refine": refine,
             "gpu_launches": int(stage[7]) * args.steps,

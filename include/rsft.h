@@ -296,6 +296,45 @@ rsft_status rsft_execute_segments_async(rsft_plan* plan, const void* const* d_se
 rsft_status rsft_execute_batch(rsft_plan* plan, const void* const* d_cubes, int64_t n_frames, int32_t lanes,
                                void* stream, uint64_t* d_located, void* d_amp, int64_t* d_counts);
 
+/* CUDA-graph form of an execute.  rsft_graph_create records, by stream capture, the
+ * launches rsft_execute_async makes for one cube and one set of outputs on execution
+ * lane `lane` (0..7, the lanes of rsft_execute_batch: each its own workspace and
+ * stream, created on first use) and instantiates them.  The pointers are fixed in the
+ * graph: every launch re-reads d_cube (device, 16-byte aligned, the plan's N complex64)
+ * and rewrites d_located (device uint64 [max_located]), d_amp (device complex64
+ * [max_located] or NULL) and d_n_located (device int64 [1]).  Graphs on one lane share
+ * its workspace, so the caller orders them (rsft_graph_launch_batch runs each lane's
+ * graphs in order on the lane's stream).  A graph keeps the plan's fold schedule and
+ * tables of the moment it was recorded: re-record after rsft_plan_autotune, and destroy
+ * every graph before its plan.  The paper has no counterpart.
+ * Errors: INVALID_ARG (NULL pointers, lane outside 0..7, misaligned cube), OOM, CUDA. */
+typedef struct rsft_graph rsft_graph;
+rsft_status rsft_graph_create(rsft_plan* plan, const void* d_cube, int32_t lane, uint64_t* d_located, void* d_amp,
+                              int64_t* d_n_located, rsft_graph** graph);
+/* One launch of a recorded execute on `stream` (cudaGraphLaunch).  Errors: INVALID_ARG, CUDA. */
+rsft_status rsft_graph_launch(rsft_graph* graph, void* stream);
+/* A batch of recorded executes, possibly of different plans (frames of different shapes):
+ * the lanes the graphs belong to start after the work queued on `stream`, each runs its
+ * graphs in the order given on its own stream, and `stream` waits for all of them.
+ * All graphs must be on one device.  Errors: INVALID_ARG (NULL graph, n < 0, mixed
+ * devices), CUDA. */
+rsft_status rsft_graph_launch_batch(rsft_graph* const* graphs, int64_t n, void* stream);
+void rsft_graph_destroy(rsft_graph* graph);
+
+/* Fold-schedule autotuner.  The plan's fold schedule (which dimensions index rows and
+ * which columns, how many residue classes a unit holds side by side, rows per step) comes
+ * from a cost model; this call times the model's `candidates` best schedules (1..16) on
+ * the caller's cube -- two warm-up and `reps` (1..1000) timed fold launches each, CUDA
+ * events on `stream` -- and keeps the fastest, rebuilding the plan's fold tables.
+ * d_cube: device, 16-byte aligned, the plan's N complex64 (only its timing matters).
+ * *us_out (may be NULL): the winner's microseconds per fold launch; *chosen (may be NULL):
+ * its rank among the candidates (0 = the model's choice).  Results of executes do not
+ * depend on the schedule beyond FP32 summation order.  Synchronises `stream`; not to be
+ * called while the plan executes on another stream.  The paper has no counterpart.
+ * Errors: INVALID_ARG, UNSUPPORTED (no candidate could run), OOM, CUDA. */
+rsft_status rsft_plan_autotune(rsft_plan* plan, const void* d_cube, void* stream, int32_t candidates, int32_t reps,
+                               double* us_out, int32_t* chosen);
+
 /* Host-buffer batch: frame f reads the host cube h_cubes[f] (pinned memory gets
  * the full copy bandwidth).  Returns when every frame's results are in host
  * memory: h_counts[f] (full count), the first min(count, max_located) entries

@@ -47,6 +47,7 @@ C_SYMBOLS = (
     "rsft_last_error", "rsft_execute_batch", "rsft_execute_host_batch", "rsft_execute_segments",
     "rsft_execute_segments_async", "rsft_bartlett_plan_create", "rsft_bartlett_plan_destroy", "rsft_bartlett_execute",
     "rsft_bartlett_execute_async", "rsft_bartlett_get", "rsft_bartlett_copy_spectrum",
+    "rsft_graph_create", "rsft_graph_launch", "rsft_graph_launch_batch", "rsft_graph_destroy", "rsft_plan_autotune",
 )
 RSFT_BARTLETT_GAMMA, RSFT_BARTLETT_GAIN, RSFT_BARTLETT_WINDOW, RSFT_BARTLETT_WORKSPACE_BYTES = 1, 2, 3, 4
 
@@ -115,6 +116,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rsft_bartlett_execute_async.argtypes = [c_void_p] * 6
     lib.rsft_bartlett_get.argtypes = [c_void_p, c_int32, c_void_p, c_size_t]
     lib.rsft_bartlett_copy_spectrum.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.rsft_graph_create.argtypes = [c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p, POINTER(c_void_p)]
+    lib.rsft_graph_launch.argtypes = [c_void_p, c_void_p]
+    lib.rsft_graph_launch_batch.argtypes = [POINTER(c_void_p), c_int64, c_void_p]
+    lib.rsft_graph_destroy.argtypes = [c_void_p]
+    lib.rsft_graph_destroy.restype = None
+    lib.rsft_plan_autotune.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_int32, POINTER(ctypes.c_double),
+                                       POINTER(c_int32)]
     lib.rsft_status_string.argtypes = [c_int32]
     lib.rsft_status_string.restype = c_char_p
     lib.rsft_last_error.argtypes = []
@@ -375,6 +383,54 @@ def rsft_status_string(status: int) -> str:
 
 def rsft_last_error() -> str:
     return load_library().rsft_last_error().decode()
+
+
+class Graph:
+    """Owning handle of an ``rsft_graph`` (one execute recorded as a CUDA graph); keeps its plan
+    and the tensors whose pointers the graph holds alive."""
+
+    def __init__(self, handle: c_void_p, plan: Plan, keep):
+        self.handle = handle
+        self.plan = plan
+        self._keep = keep
+
+    def launch(self, stream=None) -> None:
+        _check(load_library().rsft_graph_launch(self.handle, _stream(stream)))
+
+    def close(self):
+        if self.handle:
+            load_library().rsft_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rsft_graph_create(plan: Plan, cube, count, located=None, amp=None, lane: int = 0) -> Graph:
+    """Record one execute of `plan` on `cube` (results to located / amp / count) on `lane`."""
+    h = c_void_p()
+    _check(load_library().rsft_graph_create(plan.handle, _ptr(cube), int(lane), _ptr(located), _ptr(amp), _ptr(count),
+                                            ctypes.byref(h)))
+    return Graph(h, plan, (cube, count, located, amp))
+
+
+def rsft_graph_launch_batch(graphs, stream=None) -> None:
+    """Launch recorded executes (possibly of different plans), each lane's graphs in order."""
+    arr = (c_void_p * max(1, len(graphs)))(*[g.handle for g in graphs])
+    _check(load_library().rsft_graph_launch_batch(arr, len(graphs), _stream(stream)))
+
+
+def rsft_plan_autotune(plan: Plan, cube, candidates: int = 4, reps: int = 10, stream=None):
+    """Time the cost model's best `candidates` fold schedules on `cube`, keep the fastest.
+    Returns (microseconds per fold launch of the winner, its rank among the candidates)."""
+    us = ctypes.c_double(0.0)
+    chosen = c_int32(-1)
+    _check(load_library().rsft_plan_autotune(plan.handle, _ptr(cube), _stream(stream), int(candidates), int(reps),
+                                             ctypes.byref(us), ctypes.byref(chosen)))
+    return float(us.value), int(chosen.value)
 
 
 class BartlettPlan:

@@ -63,6 +63,7 @@ struct rsft_plan {
   int fold_copy_mode = -1;          // last fold launch: 0 per-row bulk copies, 3/5 tensor box rank,
                                     // 100 + rank on the tensor cores
   bool fold_tc = false;             // the fold runs on the tensor cores (fold_tc.cu)
+  int64_t partial_cap = 0;          // elements of every workspace's fold partial-sum buffer
   std::vector<int> h_sinvb;                 // [L][D] sigma^{-1} mod B_d (fold kernel parameters)
   std::vector<unsigned short> h_slots, h_xdig;
   std::vector<unsigned char> h_xres;        // residue index of each column of a 64-column chunk
@@ -134,7 +135,10 @@ float2 to_f2(cplx v) { return make_float2(static_cast<float>(v.real()), static_c
 // the 8 bytes each cube element costs: per-element row-weight setup and partial-sum traffic.
 constexpr int64_t kSms = 152;  // streaming multiprocessors the schedule is balanced for
 
-bool choose_fold_schedule(const rsft::Geometry& g, rsft::FoldSchedule& out) {
+// Scores every fold schedule the kernels support and returns the cheapest; with `all`, also
+// every candidate with its model cost (the autotuner times the best few).
+bool choose_fold_schedule(const rsft::Geometry& g, rsft::FoldSchedule& out,
+                          std::vector<std::pair<double, rsft::FoldSchedule>>* all = nullptr) {
   const int lg = std::min(g.loops, rsft::kMaxLoopGroup);
   double best = 1e300;
   bool found = false;
@@ -184,22 +188,25 @@ bool choose_fold_schedule(const rsft::Geometry& g, rsft::FoldSchedule& out) {
       const bool tensor_map = d_in >= 1 && d_in <= 2 && width <= 256;
       const double copies = (!tensor_map && width < 256) ? 1.0 : 0.0;
       const double cost = 0.5 * setup + partial + balance + idle + copies;
+      rsft::FoldSchedule c{};
+      c.d_in = d_in;
+      c.row_len = row_len;
+      c.width = static_cast<int>(width);
+      c.col_chunks = static_cast<int>(col_chunks);
+      c.classes = static_cast<int>(classes);
+      c.rows_per_class = static_cast<int>(rows_pc);
+      c.rows_per_chunk = static_cast<int>(rpc);
+      c.row_chunks = static_cast<int>(row_chunks);
+      c.xcount = static_cast<int>(xcount);
+      c.direct = (row_chunks * col_chunks == 1) ? 1 : 0;
+      c.cps = static_cast<int>(cps);
+      c.crow = static_cast<int>(crow);
+      c.groups = static_cast<int>(classes / cps);
+      if (all) all->emplace_back(cost, c);
       if (cost < best - 1e-9) {
         best = cost;
         found = true;
-        out.d_in = d_in;
-        out.row_len = row_len;
-        out.width = static_cast<int>(width);
-        out.col_chunks = static_cast<int>(col_chunks);
-        out.classes = static_cast<int>(classes);
-        out.rows_per_class = static_cast<int>(rows_pc);
-        out.rows_per_chunk = static_cast<int>(rpc);
-        out.row_chunks = static_cast<int>(row_chunks);
-        out.xcount = static_cast<int>(xcount);
-        out.direct = (row_chunks * col_chunks == 1) ? 1 : 0;
-        out.cps = static_cast<int>(cps);
-        out.crow = static_cast<int>(crow);
-        out.groups = static_cast<int>(classes / cps);
+        out = c;
       }
     }
   }
@@ -298,6 +305,22 @@ bool plan_fft_passes(const rsft::Geometry& g, std::vector<rsft::FftPass>& passes
 
 // Device workspace of one execution lane (buckets, detections, votes, row lists) and its
 // 16-byte count block (located count, error flag).
+// Partial sums a chunked fold schedule leaves for fold_reduce (0 for direct schedules).
+int64_t partial_elems(const rsft::FoldSchedule& fs, int loops) {
+  if (fs.direct) return 0;
+  return static_cast<int64_t>(std::min(loops, rsft::kMaxLoopGroup)) * fs.classes * fs.row_chunks * fs.col_chunks *
+         fs.xcount;
+}
+
+// Frees one of the plan's own device allocations (NULL is a no-op).
+void free_alloc(rsft_plan* p, const void* ptr) {
+  if (!ptr) return;
+  auto it = std::find(p->allocations.begin(), p->allocations.end(), const_cast<void*>(ptr));
+  if (it == p->allocations.end()) return;
+  cudaFree(*it);
+  p->allocations.erase(it);
+}
+
 rsft_status alloc_workspace(rsft_plan* p, rsft::Workspace& ws, int64_t** d_count) {
   const rsft::HostPlan& h = p->host;
   const int L = h.loops;
@@ -306,11 +329,10 @@ rsft_status alloc_workspace(rsft_plan* p, rsft::Workspace& ws, int64_t** d_count
   if ((st = dev_alloc(p, &ws.folded, lb * sizeof(float2))) != RSFT_OK) return st;
   if ((st = dev_alloc(p, &ws.spectrum, lb * sizeof(float2))) != RSFT_OK) return st;
   ws.partial = nullptr;
-  if (!p->fold.direct) {
-    const size_t np = static_cast<size_t>(std::min(L, rsft::kMaxLoopGroup)) * p->fold.classes *
-                      p->fold.row_chunks * p->fold.col_chunks * p->fold.xcount;
-    if ((st = dev_alloc(p, &ws.partial, np * sizeof(float2))) != RSFT_OK) return st;
-  }
+  p->partial_cap = std::max(p->partial_cap, partial_elems(p->fold, L));
+  if (p->partial_cap > 0 &&
+      (st = dev_alloc(p, &ws.partial, static_cast<size_t>(p->partial_cap) * sizeof(float2))) != RSFT_OK)
+    return st;
   ws.words_b = (h.total_b + 31) / 32;
   // rounded up to 16 bytes: the vote kernel stages the bitmaps with one bulk copy
   if ((st = dev_alloc(p, &ws.det_bits, (static_cast<size_t>(L) * ws.words_b * 4 + 15) & ~static_cast<size_t>(15))) !=
@@ -403,6 +425,116 @@ rsft_status build_fold_tables(rsft_plan* p, int group, const float4** ftable, co
     if ((st = upload(p, &f2p, fc)) != RSFT_OK) return st;
     *fcolw = f2p;
   }
+  return RSFT_OK;
+}
+
+// Everything that depends on the fold schedule p->fold: the epilogue's partial-sum slots
+// per (class, residue), the residue digits, the tensor-core choice and the fold tables
+// (segment-mode tables are rebuilt on their next use).
+rsft_status apply_fold_schedule(rsft_plan* p) {
+  const rsft::HostPlan& h = p->host;
+  const rsft::Geometry& g = p->geom;
+  const int L = h.loops, D = h.ndim;
+  rsft_status st;
+  // the previous schedule's tables (a re-tuned plan), and segment tables built from them
+  if (p->seg_ready) {
+    free_alloc(p, p->seg_tables.ftable);
+    free_alloc(p, p->seg_tables.fcolw);
+  }
+  p->seg_ready = false;
+  free_alloc(p, p->tables.ftable);
+  free_alloc(p, p->tables.fcolw);
+  free_alloc(p, p->tables.slots_by_x);
+  free_alloc(p, p->tables.x_digits);
+  p->tables.ftable = nullptr;
+  p->tables.fcolw = nullptr;
+  p->tables.slots_by_x = nullptr;
+  p->tables.x_digits = nullptr;
+  // fold epilogue tables: the partial sums left after the warp shuffle, grouped by the
+  // inner residue of their columns, and the residue digits of each inner residue
+  {
+    rsft::FoldSchedule& fs = p->fold;
+    auto residue = [&](int64_t c) {  // inner residue index of chunk column c
+      int64_t rem = c, x = 0, xstride = 1;
+      for (int d = D - 1; d >= fs.d_in; --d) {
+        const int64_t sd = rem % h.n[d];
+        rem /= h.n[d];
+        x += (sd % h.b[d]) * xstride;
+        xstride *= h.b[d];
+      }
+      return x;
+    };
+    // lane bit k moves a thread by 2^(k+1) elements: a column bit or, past the chunk width, a
+    // row bit (the class of the row for the first log2 C row bits, then its row)
+    int rmask = 0;
+    for (int k = 0; k < 5; ++k) {
+      const int pbit = k + 1;
+      bool keep = true;
+      if ((int64_t(1) << pbit) >= fs.width) {
+        keep = ((int64_t(1) << pbit) / fs.width) >= fs.cps;
+      } else {
+        int acc = 0;
+        for (int d = D - 1; d >= fs.d_in; --d) {
+          const int ln = ilog2(h.n[d]);
+          if (pbit < acc + ln) {
+            keep = (pbit - acc) >= ilog2(h.b[d]);
+            break;
+          }
+          acc += ln;
+        }
+      }
+      if (keep) rmask |= 1 << k;
+    }
+    int nbits = 0;
+    for (int k = 0; k < 5; ++k) nbits += (rmask >> k) & 1;
+    fs.red_mask = rmask;
+    fs.leaders = 32 >> nbits;
+    const int warps = rsft::kFoldConsumers / 32;
+    const int nslots = warps * fs.leaders * 2;
+    const int keys = fs.cps * fs.xcount;  // (class in step, inner residue)
+    if (nslots % keys != 0) return fail(RSFT_ERR_UNSUPPORTED, "fold epilogue: residues not balanced");
+    fs.slots_per_x = nslots / keys;
+    if (nslots > 512 || fs.xcount > 512) return fail(RSFT_ERR_UNSUPPORTED, "fold epilogue: too many residues");
+    std::vector<unsigned short> cols(static_cast<size_t>(nslots)), digits(static_cast<size_t>(fs.xcount) * 4, 0);
+    std::vector<int> fill(keys, 0);
+    for (int w = 0; w < warps; ++w)
+      for (int j = 0; j < fs.leaders; ++j) {
+        int lane = 0, bit = 0;
+        for (int b = 0; b < 5; ++b)
+          if (!((rmask >> b) & 1)) lane |= ((j >> bit++) & 1) << b;
+        for (int c = 0; c < 2; ++c) {
+          const int64_t elem = 2 * (32 * w + lane) + c;
+          const int64_t x = ((elem / fs.width) % fs.cps) * fs.xcount + residue(elem & (fs.width - 1));
+          if (fill[x] >= fs.slots_per_x) return fail(RSFT_ERR_UNSUPPORTED, "fold epilogue: residues not balanced");
+          cols[x * fs.slots_per_x + fill[x]++] = static_cast<unsigned short>((w * fs.leaders + j) * 2 + c);
+        }
+      }
+    for (int x = 0; x < fs.xcount; ++x) {
+      int64_t rem = x;
+      for (int d = D - 1; d >= fs.d_in; --d) {
+        digits[x * 4 + (d - fs.d_in)] = static_cast<unsigned short>(rem % h.b[d]);
+        rem /= h.b[d];
+      }
+    }
+    unsigned short* up = nullptr;
+    if ((st = upload(p, &up, cols)) != RSFT_OK) return st;
+    p->tables.slots_by_x = up;
+    if ((st = upload(p, &up, digits)) != RSFT_OK) return st;
+    p->tables.x_digits = up;
+    p->h_slots = cols;
+    p->h_xdig = digits;
+    p->tables.h_slots = p->h_slots.data();
+    p->tables.h_xdig = p->h_xdig.data();
+    if (rsft::fold_smem_bytes(g, fs, std::min(L, rsft::kMaxLoopGroup)) > 227 * 1024)
+      return fail(RSFT_ERR_UNSUPPORTED, "fold schedule needs more shared memory than a CTA has");
+    // the tensor-core fold (schedules of whole 64-column rows) on request: RSFT_FOLD=tc
+    const char* env = std::getenv("RSFT_FOLD");
+    p->fold_tc = rsft::fold_tc_supported(g, fs) && env && std::string(env) == "tc";
+    p->h_xres.assign(64, 0);
+    for (int c = 0; c < 64 && c < fs.width; ++c) p->h_xres[c] = static_cast<unsigned char>(residue(c));
+    p->tables.h_xres = p->h_xres.data();
+  }
+  if ((st = build_fold_tables(p, rsft::kMaxLoopGroup, &p->tables.ftable, &p->tables.fcolw)) != RSFT_OK) return st;
   return RSFT_OK;
 }
 
@@ -499,93 +631,9 @@ rsft_status build_device(rsft_plan* p) {
   float* fp = nullptr;
   if ((st = upload(p, &fp, gam)) != RSFT_OK) return st;
   p->tables.gamma = fp;
-  // fold epilogue tables: the partial sums left after the warp shuffle, grouped by the
-  // inner residue of their columns, and the residue digits of each inner residue
-  {
-    rsft::FoldSchedule& fs = p->fold;
-    auto residue = [&](int64_t c) {  // inner residue index of chunk column c
-      int64_t rem = c, x = 0, xstride = 1;
-      for (int d = D - 1; d >= fs.d_in; --d) {
-        const int64_t sd = rem % h.n[d];
-        rem /= h.n[d];
-        x += (sd % h.b[d]) * xstride;
-        xstride *= h.b[d];
-      }
-      return x;
-    };
-    // lane bit k moves a thread by 2^(k+1) elements: a column bit or, past the chunk width, a
-    // row bit (the class of the row for the first log2 C row bits, then its row)
-    int rmask = 0;
-    for (int k = 0; k < 5; ++k) {
-      const int pbit = k + 1;
-      bool keep = true;
-      if ((int64_t(1) << pbit) >= fs.width) {
-        keep = ((int64_t(1) << pbit) / fs.width) >= fs.cps;
-      } else {
-        int acc = 0;
-        for (int d = D - 1; d >= fs.d_in; --d) {
-          const int ln = ilog2(h.n[d]);
-          if (pbit < acc + ln) {
-            keep = (pbit - acc) >= ilog2(h.b[d]);
-            break;
-          }
-          acc += ln;
-        }
-      }
-      if (keep) rmask |= 1 << k;
-    }
-    int nbits = 0;
-    for (int k = 0; k < 5; ++k) nbits += (rmask >> k) & 1;
-    fs.red_mask = rmask;
-    fs.leaders = 32 >> nbits;
-    const int warps = rsft::kFoldConsumers / 32;
-    const int nslots = warps * fs.leaders * 2;
-    const int keys = fs.cps * fs.xcount;  // (class in step, inner residue)
-    if (nslots % keys != 0) return fail(RSFT_ERR_UNSUPPORTED, "fold epilogue: residues not balanced");
-    fs.slots_per_x = nslots / keys;
-    if (nslots > 512 || fs.xcount > 512) return fail(RSFT_ERR_UNSUPPORTED, "fold epilogue: too many residues");
-    std::vector<unsigned short> cols(static_cast<size_t>(nslots)), digits(static_cast<size_t>(fs.xcount) * 4, 0);
-    std::vector<int> fill(keys, 0);
-    for (int w = 0; w < warps; ++w)
-      for (int j = 0; j < fs.leaders; ++j) {
-        int lane = 0, bit = 0;
-        for (int b = 0; b < 5; ++b)
-          if (!((rmask >> b) & 1)) lane |= ((j >> bit++) & 1) << b;
-        for (int c = 0; c < 2; ++c) {
-          const int64_t elem = 2 * (32 * w + lane) + c;
-          const int64_t x = ((elem / fs.width) % fs.cps) * fs.xcount + residue(elem & (fs.width - 1));
-          if (fill[x] >= fs.slots_per_x) return fail(RSFT_ERR_UNSUPPORTED, "fold epilogue: residues not balanced");
-          cols[x * fs.slots_per_x + fill[x]++] = static_cast<unsigned short>((w * fs.leaders + j) * 2 + c);
-        }
-      }
-    for (int x = 0; x < fs.xcount; ++x) {
-      int64_t rem = x;
-      for (int d = D - 1; d >= fs.d_in; --d) {
-        digits[x * 4 + (d - fs.d_in)] = static_cast<unsigned short>(rem % h.b[d]);
-        rem /= h.b[d];
-      }
-    }
-    unsigned short* up = nullptr;
-    if ((st = upload(p, &up, cols)) != RSFT_OK) return st;
-    p->tables.slots_by_x = up;
-    if ((st = upload(p, &up, digits)) != RSFT_OK) return st;
-    p->tables.x_digits = up;
-    p->h_slots = cols;
-    p->h_xdig = digits;
-    p->h_sinvb = sib;
-    p->tables.h_slots = p->h_slots.data();
-    p->tables.h_xdig = p->h_xdig.data();
-    p->tables.h_sinvb = p->h_sinvb.data();
-    if (rsft::fold_smem_bytes(g, fs, std::min(L, rsft::kMaxLoopGroup)) > 227 * 1024)
-      return fail(RSFT_ERR_UNSUPPORTED, "fold schedule needs more shared memory than a CTA has");
-    // the tensor-core fold (schedules of whole 64-column rows) on request: RSFT_FOLD=tc
-    const char* env = std::getenv("RSFT_FOLD");
-    p->fold_tc = rsft::fold_tc_supported(g, fs) && env && std::string(env) == "tc";
-    p->h_xres.assign(64, 0);
-    for (int c = 0; c < 64 && c < fs.width; ++c) p->h_xres[c] = static_cast<unsigned char>(residue(c));
-    p->tables.h_xres = p->h_xres.data();
-  }
-  if ((st = build_fold_tables(p, rsft::kMaxLoopGroup, &p->tables.ftable, &p->tables.fcolw)) != RSFT_OK) return st;
+  p->h_sinvb = sib;
+  p->tables.h_sinvb = p->h_sinvb.data();
+  if ((st = apply_fold_schedule(p)) != RSFT_OK) return st;
   p->tables.rowmask = nullptr;
   p->tables.kb16 = nullptr;
   if (p->rows_mode && p->rows.small) {
@@ -1373,6 +1421,191 @@ rsft_status rsft_refine(rsft_plan* plan, const void* d_cube, int64_t k, float* d
     if (e != cudaSuccess) return cuda_fail(e, "rsft_refine");
   }
   return RSFT_OK;
+}
+
+rsft_status rsft_plan_autotune(rsft_plan* plan, const void* d_cube, void* stream, int32_t candidates, int32_t reps,
+                               double* us_out, int32_t* chosen) {
+  if (!plan || !d_cube) return fail(RSFT_ERR_INVALID_ARG, "NULL plan or cube");
+  if (!plan->has_device) return fail(RSFT_ERR_INVALID_ARG, "host-only plan cannot execute");
+  if (candidates < 1 || candidates > 16 || reps < 1 || reps > 1000)
+    return fail(RSFT_ERR_INVALID_ARG, "candidates must be 1..16 and reps 1..1000");
+  if (reinterpret_cast<uintptr_t>(d_cube) % 16 != 0) return fail(RSFT_ERR_INVALID_ARG, "cube must be 16-byte aligned");
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return fail(RSFT_ERR_CUDA, "cudaSetDevice failed");
+  std::vector<std::pair<double, rsft::FoldSchedule>> all;
+  rsft::FoldSchedule model{};
+  if (!choose_fold_schedule(plan->geom, model, &all)) return fail(RSFT_ERR_UNSUPPORTED, "no fold schedule");
+  std::stable_sort(all.begin(), all.end(),
+                   [](const std::pair<double, rsft::FoldSchedule>& a, const std::pair<double, rsft::FoldSchedule>& b) {
+                     return a.first < b.first;
+                   });
+  auto same = [](const rsft::FoldSchedule& a, const rsft::FoldSchedule& b) {
+    return a.d_in == b.d_in && a.width == b.width && a.cps == b.cps && a.crow == b.crow && a.col_chunks == b.col_chunks;
+  };
+  std::vector<rsft::FoldSchedule> cands;
+  for (const auto& c : all) {
+    if (static_cast<int>(cands.size()) >= candidates) break;
+    // chunked schedules need partial-sum buffers no larger than the workspaces already have
+    if (partial_elems(c.second, plan->host.loops) > plan->partial_cap) continue;
+    bool dup = false;
+    for (const auto& k : cands) dup = dup || same(k, c.second);
+    if (!dup) cands.push_back(c.second);
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_fail(e, "autotune events");
+  }
+  const rsft::FoldSchedule original = plan->fold;
+  double best_us = 1e300;
+  int best = -1;
+  rsft_status st = RSFT_OK;
+  for (size_t i = 0; i < cands.size() && st == RSFT_OK; ++i) {
+    plan->fold = cands[i];
+    if (apply_fold_schedule(plan) != RSFT_OK) continue;  // e.g. more shared memory than a CTA has
+    for (int w = 0; w < 2 && st == RSFT_OK; ++w) st = fold_cube(plan, d_cube, s);
+    if (st != RSFT_OK) break;
+    e = cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && st == RSFT_OK; ++r) st = fold_cube(plan, d_cube, s);
+    if (st != RSFT_OK) break;
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "autotune timing");
+      break;
+    }
+    const double us = 1e3 * static_cast<double>(ms) / reps;
+    if (us < best_us) {
+      best_us = us;
+      best = static_cast<int>(i);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  plan->fold = best >= 0 ? cands[best] : original;
+  const rsft_status st2 = apply_fold_schedule(plan);
+  if (st != RSFT_OK) return st;
+  if (st2 != RSFT_OK) return st2;
+  if (best < 0) return fail(RSFT_ERR_UNSUPPORTED, "no candidate fold schedule could run");
+  if (us_out) *us_out = best_us;
+  if (chosen) *chosen = best;
+  return RSFT_OK;
+}
+
+}  // extern "C"
+
+// An execute recorded as a CUDA graph on one lane of a plan.
+struct rsft_graph {
+  rsft_plan* plan = nullptr;
+  int lane = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+rsft_status rsft_graph_create(rsft_plan* plan, const void* d_cube, int32_t lane, uint64_t* d_located, void* d_amp,
+                              int64_t* d_n_located, rsft_graph** graph) {
+  if (!graph) return fail(RSFT_ERR_INVALID_ARG, "NULL graph pointer");
+  *graph = nullptr;
+  if (!plan || !d_cube || !d_n_located) return fail(RSFT_ERR_INVALID_ARG, "NULL plan, cube or count");
+  if (!plan->has_device) return fail(RSFT_ERR_INVALID_ARG, "host-only plan cannot execute");
+  if (lane < 0 || lane > 7) return fail(RSFT_ERR_INVALID_ARG, "lane must be 0..7");
+  if (plan->host.desc.max_located > 0 && !d_located) return fail(RSFT_ERR_INVALID_ARG, "d_located is NULL");
+  if (reinterpret_cast<uintptr_t>(d_cube) % 16 != 0) return fail(RSFT_ERR_INVALID_ARG, "cube must be 16-byte aligned");
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return fail(RSFT_ERR_CUDA, "cudaSetDevice failed");
+  rsft_status st = ensure_lanes(plan, lane + 1, false);
+  if (st != RSFT_OK) return st;
+  rsft_lane& ln = plan->lanes[lane];
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "graph capture stream");
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return cuda_fail(e, "cudaStreamBeginCapture");
+  }
+  bool dirty = true;  // a recorded execute always clears the vote array it starts from
+  st = run_lane(plan, ln.ws, dirty, false, d_cube, cs, d_located, nullptr, static_cast<float2*>(d_amp), nullptr,
+                d_n_located);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+  cudaStreamDestroy(cs);
+  if (st != RSFT_OK) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return st;
+  }
+  if (ec != cudaSuccess) return cuda_fail(ec, "cudaStreamEndCapture");
+  cudaGraphExec_t x = nullptr;
+  e = cudaGraphInstantiate(&x, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  rsft_graph* out = new rsft_graph;
+  out->plan = plan;
+  out->lane = lane;
+  out->graph = g;
+  out->exec = x;
+  *graph = out;
+  return RSFT_OK;
+}
+
+rsft_status rsft_graph_launch(rsft_graph* graph, void* stream) {
+  if (!graph || !graph->exec) return fail(RSFT_ERR_INVALID_ARG, "NULL graph");
+  DeviceGuard guard(graph->plan->device);
+  if (!guard.ok) return fail(RSFT_ERR_CUDA, "cudaSetDevice failed");
+  const cudaError_t e = cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? RSFT_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+rsft_status rsft_graph_launch_batch(rsft_graph* const* graphs, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && !graphs)) return fail(RSFT_ERR_INVALID_ARG, "NULL graphs or negative count");
+  if (n == 0) return RSFT_OK;
+  for (int64_t i = 0; i < n; ++i)
+    if (!graphs[i] || !graphs[i]->exec) return fail(RSFT_ERR_INVALID_ARG, "NULL graph in the batch");
+  const int dev = graphs[0]->plan->device;
+  for (int64_t i = 1; i < n; ++i)
+    if (graphs[i]->plan->device != dev) return fail(RSFT_ERR_INVALID_ARG, "graphs of one batch must share a device");
+  DeviceGuard guard(dev);
+  if (!guard.ok) return fail(RSFT_ERR_CUDA, "cudaSetDevice failed");
+  // the distinct lanes of the batch: each waits for the caller's stream, runs its graphs in
+  // order, and the caller's stream waits for all of them
+  std::vector<rsft_lane*> lanes;
+  for (int64_t i = 0; i < n; ++i) {
+    rsft_lane* ln = &graphs[i]->plan->lanes[graphs[i]->lane];
+    if (std::find(lanes.begin(), lanes.end(), ln) == lanes.end()) lanes.push_back(ln);
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t fork = graphs[0]->plan->fork;
+  cudaError_t e = cudaEventRecord(fork, s);
+  for (size_t i = 0; e == cudaSuccess && i < lanes.size(); ++i) e = cudaStreamWaitEvent(lanes[i]->stream, fork, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "graph batch fork");
+  for (int64_t i = 0; i < n; ++i) {
+    e = cudaGraphLaunch(graphs[i]->exec, graphs[i]->plan->lanes[graphs[i]->lane].stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+  }
+  for (size_t i = 0; e == cudaSuccess && i < lanes.size(); ++i) {
+    e = cudaEventRecord(lanes[i]->done, lanes[i]->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, lanes[i]->done, 0);
+  }
+  return e == cudaSuccess ? RSFT_OK : cuda_fail(e, "graph batch join");
+}
+
+void rsft_graph_destroy(rsft_graph* graph) {
+  if (!graph) return;
+  DeviceGuard guard(graph->plan->device);
+  if (graph->exec) cudaGraphExecDestroy(graph->exec);
+  if (graph->graph) cudaGraphDestroy(graph->graph);
+  cudaGetLastError();
+  delete graph;
 }
 
 const char* rsft_status_string(rsft_status s) {

@@ -20,8 +20,8 @@ FLOOR = 0.1
 BAND = 1e-5
 
 
-def gpu_run(desc, cube_np=None, cube_dev=None, want_votes=True):
-    plan = R.rsft_plan_create(desc)
+def gpu_run(desc, cube_np=None, cube_dev=None, want_votes=True, plan=None):
+    plan = plan if plan is not None else R.rsft_plan_create(desc)
     n = tuple(int(desc.n[i]) for i in range(desc.ndim))
     b = tuple(int(desc.b[i]) for i in range(desc.ndim))
     L = int(desc.loops)

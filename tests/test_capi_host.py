@@ -1,5 +1,6 @@
 """The C ABI without a GPU: library loads, exports every declared symbol, builds
 host-only plans whose tables match the oracle, and rejects bad descriptors."""
+import ctypes
 import re
 import os
 
@@ -156,3 +157,26 @@ def test_batches_need_a_device_plan():
     with pytest.raises(R.RsftError) as ei:
         R.rsft_execute_host_batch(plan, [np.zeros(64 * 64, np.complex64)], np.zeros(8, np.int64), counts)
     assert ei.value.status == R.RSFT_ERR_INVALID_ARG
+
+
+def test_graphs_and_autotune_need_a_device_plan():
+    """Graph recording and the fold autotuner check their arguments before touching a device."""
+    plan = R.rsft_plan_create(R.make_desc((64, 64), (8, 8), 4, device=-1, p_fa1=0.05, mu=1))
+    cube = np.zeros(64 * 64, np.complex64)
+    count = np.zeros(1, np.int64)
+    located = np.zeros(8, np.int64)
+    for call in (lambda: R.rsft_graph_create(plan, cube, count, located),
+                 lambda: R.rsft_plan_autotune(plan, cube)):
+        with pytest.raises(R.RsftError) as ei:
+            call()
+        assert ei.value.status == R.RSFT_ERR_INVALID_ARG
+    lib = R.load_library()
+    h = ctypes.c_void_p()
+    assert lib.rsft_graph_create(None, None, 0, None, None, None, ctypes.byref(h)) == R.RSFT_ERR_INVALID_ARG
+    assert lib.rsft_graph_create(plan.handle, R._ptr(cube), 9, R._ptr(located), None, R._ptr(count),
+                                 ctypes.byref(h)) == R.RSFT_ERR_INVALID_ARG   # lane outside 0..7
+    assert lib.rsft_graph_launch(None, None) == R.RSFT_ERR_INVALID_ARG
+    assert lib.rsft_graph_launch_batch(None, 0, None) == R.RSFT_OK           # empty batch: nothing to do
+    assert lib.rsft_graph_launch_batch(None, -1, None) == R.RSFT_ERR_INVALID_ARG
+    assert lib.rsft_plan_autotune(plan.handle, R._ptr(cube), None, 0, 10, None, None) == R.RSFT_ERR_INVALID_ARG
+    lib.rsft_graph_destroy(None)  # NULL is a no-op

@@ -1,0 +1,111 @@
+"""CUDA-graph executes and the fold autotuner.  A recorded execute runs the same kernels on
+the same arithmetic, so its results equal rsft_execute's bit for bit (on any lane, launch
+after launch); a batch of graphs of plans of different shapes gives each frame exactly its
+single-execute result; an autotuned plan (another fold schedule: only the FP32 summation
+order changes) still meets the FP64 oracle at every stage."""
+import zlib
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_1610_01050_gb300 as R
+import rsft_inputs as ri
+from tests.gpu_helpers import gpu_run, compare_full
+from tests.test_gpu_parity import make_pair
+
+pytestmark = pytest.mark.gpu
+
+CAP = 1 << 16
+SHAPES = [((128, 64, 16), (16, 8, 4), 10), ((64, 32, 64), (8, 4, 8), 8)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1610_01050_gb300 import build as B
+    B.build()
+    R.load_library()
+
+
+def _plan(n, b, loops, seed):
+    return R.rsft_plan_create(R.make_desc(n, b, loops, p_fa=1e-5, k_max=6, seed=seed, max_located=CAP))
+
+
+def _cube(n, b, seed):
+    tg = ri.draw_targets(n, 6, "offgrid", seed, (10.0, 20.0), int(np.prod(b)))
+    return torch.from_numpy(ri.tone_cube(n, tg, 1.0, seed)).cuda()
+
+
+def _outputs():
+    return (torch.zeros(CAP, dtype=torch.int64, device="cuda"), torch.zeros(CAP, dtype=torch.complex64, device="cuda"),
+            torch.zeros(1, dtype=torch.int64, device="cuda"))
+
+
+def _single(plan, x):
+    loc, amp, _ = _outputs()
+    c = R.rsft_execute(plan, x, located=loc, amp=amp)
+    return c, loc[:c].cpu().numpy(), amp[:c].cpu().numpy()
+
+
+@pytest.mark.parametrize("lane", [0, 3])
+def test_graph_equals_execute(lane):
+    n, b, loops = SHAPES[0]
+    plan = _plan(n, b, loops, 11)
+    x = _cube(n, b, 11)
+    c, loc_ref, amp_ref = _single(plan, x)
+    assert c > 0
+    loc, amp, cnt = _outputs()
+    g = R.rsft_graph_create(plan, x, cnt, located=loc, amp=amp, lane=lane)
+    for _ in range(3):  # every launch rewrites the same outputs
+        loc.zero_()
+        amp.zero_()
+        g.launch()
+        torch.cuda.synchronize()
+        k = int(cnt.item())
+        assert k == c
+        np.testing.assert_array_equal(loc[:k].cpu().numpy(), loc_ref)
+        np.testing.assert_array_equal(amp[:k].cpu().numpy(), amp_ref)
+    g.close()
+
+
+def test_graph_batch_of_mixed_shapes():
+    plans = [_plan(n, b, loops, 20 + i) for i, (n, b, loops) in enumerate(SHAPES)]
+    frames, graphs, outs, refs = [], [], [], []
+    for f in range(6):
+        i = f % 2
+        n, b, _ = SHAPES[i]
+        x = _cube(n, b, 40 + f)
+        refs.append(_single(plans[i], x))
+        o = _outputs()
+        graphs.append(R.rsft_graph_create(plans[i], x, o[2], located=o[0], amp=o[1], lane=(f // 2) % 3))
+        frames.append(x)
+        outs.append(o)
+    order = [0, 1, 2, 3, 4, 5, 1, 0, 5]  # repeats run after their earlier launch on the same lane
+    R.rsft_graph_launch_batch([graphs[f] for f in order])
+    torch.cuda.synchronize()
+    for f in range(6):
+        c, loc_ref, amp_ref = refs[f]
+        loc, amp, cnt = outs[f]
+        assert int(cnt.item()) == c
+        np.testing.assert_array_equal(loc[:c].cpu().numpy(), loc_ref)
+        np.testing.assert_array_equal(amp[:c].cpu().numpy(), amp_ref)
+    for g in graphs:
+        g.close()
+
+
+@pytest.mark.parametrize("n,b,loops", [((128, 64, 32), (16, 8, 4), 12), ((256, 128, 16), (16, 8, 1), 10)])
+def test_autotuned_plan_meets_oracle(n, b, loops):
+    seed = zlib.crc32(str(n).encode()) % 1000
+    d, op = make_pair(n, b, loops, seed=seed, p_fa=1e-5, k_max=4, noise_var=1.5, max_located=CAP)
+    tg = ri.draw_targets(n, 6, "offgrid", seed, (10.0, 20.0), int(np.prod(b)), noise_var=1.5)
+    cube = ri.tone_cube(n, tg, 1.5, seed)
+    plan = R.rsft_plan_create(d)
+    x = torch.from_numpy(cube).cuda()
+    us, chosen = R.rsft_plan_autotune(plan, x, candidates=4, reps=3)
+    assert us > 0 and 0 <= chosen < 4
+    g = gpu_run(d, cube_dev=x, plan=plan)
+    rep = compare_full(g, O.rsft(op, cube.astype(np.complex128)), op)
+    print(f"autotuned {n}: {us:.1f} us per fold, candidate {chosen}, {rep}")
+    assert rep["located"] > 0
