@@ -68,6 +68,7 @@ struct FoldArgs {
   int ring;               // stages in the ring
   int slot_bytes;         // data + the stage's row-table slice
   int colw_off, red_off, bar_off;             // shared-memory layout (bytes)
+  int lch;                                    // loops per epilogue pass (the partials buffer holds lch loops)
   int sinvb[kMaxLoopGroup * kMaxDim];        // sigma^{-1} mod B_d of the group's loops
   unsigned short slots[512];                  // [C X][slots_per_x] epilogue partial sums per (class, residue)
   unsigned short xdig[2048];                  // [X][4] inner residue digits
@@ -96,13 +97,21 @@ __host__ __device__ __forceinline__ bool colw_staged(const FoldSchedule& fs, int
   return fs.col_chunks == 1 && lg * fs.width * 8 <= 16 * 1024;
 }
 
+constexpr int kRedCap = 24 * 1024;  // epilogue partials: loops go through in passes of at most this
+
 // Shared memory: [ring x (stage data | stage row table)] [column weights] [epilogue partials] [barriers].
+// The partials hold lch loops at a time (all of them unless that would pass kRedCap).
 __host__ __device__ __forceinline__ int fold_layout(const FoldSchedule& fs, int lg, int* ring, int* slot_bytes,
-                                                    int* colw_off, int* red_off, int* bar_off) {
+                                                    int* colw_off, int* red_off, int* bar_off, int* lch) {
   const StageShape sh = stage_shape(fs, lg);
   *slot_bytes = kStageBytes + sh.table_bytes;
   const int colw = colw_staged(fs, lg) ? lg * fs.width * 8 : 0;
-  const int red = kWarps * fs.leaders * 2 * lg * 8;
+  const int red_loop = kWarps * fs.leaders * 2 * 8;
+  int lc = kRedCap / red_loop;
+  if (lc < 1) lc = 1;
+  if (lc > lg) lc = lg;
+  *lch = lc;
+  const int red = red_loop * lc;
   const int bars = (kMaxRing + 1) * 8 + kMaxRing * 4 + 16;
   int r = (kSmemBudget - colw - red - bars) / *slot_bytes;
   if (r > kMaxRing) r = kMaxRing;
@@ -123,7 +132,7 @@ __host__ __device__ __forceinline__ int fold_layout(const FoldSchedule& fs, int 
 // next unit's rows arrive during this unit's epilogue): the last warp to finish with stage i
 // (a shared-memory count per slot) issues stage i + ring into the same slot.  Each stage
 // brings its rows and their row-table slice.
-template <int LG>
+template <int LG, bool CHUNK>
 __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant__ FoldArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const Geometry& g = a.g;
@@ -295,8 +304,11 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
 
     // ---- epilogue: column weights, shuffle over lane bits that keep (class, residue), then across warps
     const float2* cw_g = a.colw + static_cast<int64_t>(cc) * LG * W;
+    const int lch = CHUNK ? a.lch : LG;  // loops per pass (one pass unless the partials would not fit)
+    for (int lc0 = 0; lc0 < LG; lc0 += lch) {
 #pragma unroll
     for (int l = 0; l < LG; ++l) {
+      if (CHUNK && (l < lc0 || l >= lc0 + lch)) continue;  // another pass's loop (warp-uniform)
       const float2 pa = k12a[l], pb = k12b[l], p3 = k3[l];
       float2 v0 = make_float2(pa.x - p3.x, pa.x + pa.y);
       float2 v1 = make_float2(pb.x - p3.y, pb.x + pb.y);
@@ -315,19 +327,21 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
       }
       if (leader) {
         const int sl = (warp * nl + lj) * 2;
-        red[sl * LG + l] = v0;
-        red[(sl + 1) * LG + l] = v1;
+        red[sl * lch + (l - lc0)] = v0;
+        red[(sl + 1) * lch + (l - lc0)] = v1;
       }
     }
     __syncthreads();
-    for (int o = tid; o < LG * keys; o += kThreads) {
-      const int l = o / keys;
-      const int key = o - l * keys;
+    const int nlc = LG - lc0 < lch ? LG - lc0 : lch;
+    for (int o = tid; o < nlc * keys; o += kThreads) {
+      const int lo = o / keys;
+      const int l = lc0 + lo;
+      const int key = o - lo * keys;
       const int x = key % X;
       const int cls = cls0 + key / X;
       float2 sum = make_float2(0.f, 0.f);
       for (int k = 0; k < per; ++k) {
-        const float2 v = red[static_cast<int>(a.slots[key * per + k]) * LG + l];
+        const float2 v = red[static_cast<int>(a.slots[key * per + k]) * lch + lo];
         sum.x += v.x;
         sum.y += v.y;
       }
@@ -358,7 +372,8 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
         a.partial[((static_cast<int64_t>(l) * fs.classes + cls) * chunks + ch) * X + x] = sum;
       }
     }
-    __syncthreads();  // the partials are read before the next unit writes them
+    __syncthreads();  // the partials are read before the next pass or unit writes them
+    }
   }
 }
 
@@ -412,7 +427,7 @@ __global__ void fold_reduce_kernel(const ReduceArgs a) {
   }
 }
 
-template <int LG>
+template <int LG, bool CHUNK>
 cudaError_t launch_fold_lg(const FoldArgs& args, int smem, cudaStream_t stream) {
   static int cached_smem[64] = {0};
   static int cached_grid[64] = {0};
@@ -420,10 +435,10 @@ cudaError_t launch_fold_lg(const FoldArgs& args, int smem, cudaStream_t stream) 
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 64 || cached_smem[dev] != smem) {
-    e = cudaFuncSetAttribute(fold_kernel<LG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(fold_kernel<LG, CHUNK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fold_kernel<LG>, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fold_kernel<LG, CHUNK>, kThreads, smem);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -435,7 +450,7 @@ cudaError_t launch_fold_lg(const FoldArgs& args, int smem, cudaStream_t stream) 
   const int units = args.fs.groups * args.fs.row_chunks * args.fs.col_chunks;
   const int resident = dev < 64 ? cached_grid[dev] : 2 * 152;
   const int grid = units < resident ? units : resident;
-  fold_kernel<LG><<<grid, kThreads, smem, stream>>>(args);
+  fold_kernel<LG, CHUNK><<<grid, kThreads, smem, stream>>>(args);
   return cudaGetLastError();
 }
 
@@ -444,7 +459,8 @@ cudaError_t launch_fold_lg(const FoldArgs& args, int smem, cudaStream_t stream) 
 int fold_smem_bytes(const Geometry& g, const FoldSchedule& fs, int lg) {
   (void)g;
   int a, b, c, d, e;
-  return fold_layout(fs, lg, &a, &b, &c, &d, &e);
+  int f;
+  return fold_layout(fs, lg, &a, &b, &c, &d, &e, &f);
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -534,24 +550,27 @@ cudaError_t launch_fold(const Geometry& g, const FoldSchedule& fs, const DeviceT
   const int nslots = fs.slots_per_x * fs.cps * fs.xcount;  // one list per (class in step, residue)
   for (int i = 0; i < nslots && i < 512; ++i) args.slots[i] = t.h_slots[i];
   for (int i = 0; i < fs.xcount * 4 && i < 2048; ++i) args.xdig[i] = t.h_xdig[i];
-  const int smem = fold_layout(fs, lg, &args.ring, &args.slot_bytes, &args.colw_off, &args.red_off, &args.bar_off);
+  const int smem = fold_layout(fs, lg, &args.ring, &args.slot_bytes, &args.colw_off, &args.red_off, &args.bar_off,
+                               &args.lch);
+  // the epilogue partials of at most 6 loops always fit: multi-pass kernels only above that
+  const bool chunk = args.lch < lg;
   switch (lg) {
-    case 1: return launch_fold_lg<1>(args, smem, stream);
-    case 2: return launch_fold_lg<2>(args, smem, stream);
-    case 3: return launch_fold_lg<3>(args, smem, stream);
-    case 4: return launch_fold_lg<4>(args, smem, stream);
-    case 5: return launch_fold_lg<5>(args, smem, stream);
-    case 6: return launch_fold_lg<6>(args, smem, stream);
-    case 7: return launch_fold_lg<7>(args, smem, stream);
-    case 8: return launch_fold_lg<8>(args, smem, stream);
-    case 9: return launch_fold_lg<9>(args, smem, stream);
-    case 10: return launch_fold_lg<10>(args, smem, stream);
-    case 11: return launch_fold_lg<11>(args, smem, stream);
-    case 12: return launch_fold_lg<12>(args, smem, stream);
-    case 13: return launch_fold_lg<13>(args, smem, stream);
-    case 14: return launch_fold_lg<14>(args, smem, stream);
-    case 15: return launch_fold_lg<15>(args, smem, stream);
-    case 16: return launch_fold_lg<16>(args, smem, stream);
+    case 1: return launch_fold_lg<1, false>(args, smem, stream);
+    case 2: return launch_fold_lg<2, false>(args, smem, stream);
+    case 3: return launch_fold_lg<3, false>(args, smem, stream);
+    case 4: return launch_fold_lg<4, false>(args, smem, stream);
+    case 5: return launch_fold_lg<5, false>(args, smem, stream);
+    case 6: return launch_fold_lg<6, false>(args, smem, stream);
+    case 7: return chunk ? launch_fold_lg<7, true>(args, smem, stream) : launch_fold_lg<7, false>(args, smem, stream);
+    case 8: return chunk ? launch_fold_lg<8, true>(args, smem, stream) : launch_fold_lg<8, false>(args, smem, stream);
+    case 9: return chunk ? launch_fold_lg<9, true>(args, smem, stream) : launch_fold_lg<9, false>(args, smem, stream);
+    case 10: return chunk ? launch_fold_lg<10, true>(args, smem, stream) : launch_fold_lg<10, false>(args, smem, stream);
+    case 11: return chunk ? launch_fold_lg<11, true>(args, smem, stream) : launch_fold_lg<11, false>(args, smem, stream);
+    case 12: return chunk ? launch_fold_lg<12, true>(args, smem, stream) : launch_fold_lg<12, false>(args, smem, stream);
+    case 13: return chunk ? launch_fold_lg<13, true>(args, smem, stream) : launch_fold_lg<13, false>(args, smem, stream);
+    case 14: return chunk ? launch_fold_lg<14, true>(args, smem, stream) : launch_fold_lg<14, false>(args, smem, stream);
+    case 15: return chunk ? launch_fold_lg<15, true>(args, smem, stream) : launch_fold_lg<15, false>(args, smem, stream);
+    case 16: return chunk ? launch_fold_lg<16, true>(args, smem, stream) : launch_fold_lg<16, false>(args, smem, stream);
     default: return cudaErrorInvalidValue;
   }
 }
