@@ -165,6 +165,14 @@ def batched_frames(R, bplan, ring, nframes, lanes, bcounts, bloc, bamp, stream):
         done += m
 
 
+def graph_frames(R, graphs, nframes, stream):
+    """nframes frames as recorded executes (frame f: graph f mod len(graphs), one per lane),
+    BATCH_CHUNK per rsft_graph_launch_batch."""
+    seq = [graphs[f % len(graphs)] for f in range(nframes)]
+    for i in range(0, nframes, BATCH_CHUNK):
+        R.rsft_graph_launch_batch(seq[i:i + BATCH_CHUNK], stream=stream)
+
+
 def oracle_plan(wl, nv, seed):
     import oracle as O
     return O.make_plan(wl.shape, wl.buckets, wl.loops, seed=seed, atten_db=wl.atten_db,
@@ -497,6 +505,23 @@ def run_ours(args):
     best_lanes = max(tune, key=tune.get)
     if ws > 1:
         best_lanes = int(max_over_ranks(best_lanes, ws, dev))
+    # the same frames as recorded executes (CUDA graphs), one per lane over 4 lanes
+    glanes = 4
+    gout = [(torch.zeros(BATCH_CAP, dtype=torch.int64, device=dev), torch.zeros(BATCH_CAP, dtype=torch.complex64, device=dev),
+             torch.zeros(1, dtype=torch.int64, device=dev)) for _ in range(glanes)]
+    graphs = [R.rsft_graph_create(bplan, cubes[k % F], gout[k][2], located=gout[k][0], amp=gout[k][1], lane=k)
+              for k in range(glanes)]
+    graph_frames(R, graphs, BATCH_CHUNK, stream)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    graph_frames(R, graphs, 2 * BATCH_CHUNK, stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    tune["graphs"] = 2 * BATCH_CHUNK / (t0.elapsed_time(t1) / 1e3)
+    use_graphs = tune["graphs"] > tune[best_lanes]
+    if ws > 1:
+        use_graphs = bool(max_over_ranks(float(use_graphs), ws, dev))
     for k in range(args.warmup):
         R.rsft_execute_async(plan, cubes[k % F], count, stream=stream, located=located, amp=amp)
     torch.cuda.synchronize()
@@ -523,7 +548,10 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     ev0.record(stream)
-    batched_frames(R, bplan, ring, args.steps, best_lanes, bcounts, bloc, bamp, stream)
+    if use_graphs:
+        graph_frames(R, graphs, args.steps, stream)
+    else:
+        batched_frames(R, bplan, ring, args.steps, best_lanes, bcounts, bloc, bamp, stream)
     ev1.record(stream)
     torch.cuda.synchronize()
     sampler.mark(False)
@@ -568,6 +596,8 @@ def run_ours(args):
     t_e2e = max_over_ranks(time.perf_counter() - t0, ws, dev)
     e2e_val = whole_job_rate(ws, e2e_steps, t_e2e * 1e3)
 
+    for g_ in graphs:
+        g_.close()
     bplan.close()
     refine = refinement(R, torch, plan, wl, cubes, targets, stream, cap)
     seg = segment_mode(R, torch, plan, wl, cubes, stream, dev, ws, located, amp, count,
@@ -592,8 +622,11 @@ def run_ours(args):
                 "frames_per_rank_ring": F,
                 "l2": f"inputs larger than L2: ring of {F} frames, {F * int(np.prod(wl.shape)) * 8 / 1e6:.0f} MB",
                 "parallelism": f"frames sharded over {ws} GPU(s), no collective on the data path",
-                "form": f"batched: frames spread over {best_lanes} concurrent lanes (lane count tuned over 1-4), "
-                        f"{BATCH_CHUNK} frames per call",
+                "form": (f"batched: each frame one recorded execute (CUDA graph) on one of {glanes} lanes, "
+                         f"{BATCH_CHUNK} graphs per rsft_graph_launch_batch (faster than rsft_execute_batch over "
+                         f"{best_lanes} lanes in the tuning)" if use_graphs else
+                         f"batched: frames spread over {best_lanes} concurrent lanes (lane count tuned over 1-4), "
+                         f"{BATCH_CHUNK} frames per call"),
                 "mu": int(R.rsft_plan_get(plan, R.RSFT_GET_MU)[0]),
                 "pfa1": float(R.rsft_plan_get(plan, R.RSFT_GET_PFA1)[0]),
             },
