@@ -109,3 +109,46 @@ def test_autotuned_plan_meets_oracle(n, b, loops):
     rep = compare_full(g, O.rsft(op, cube.astype(np.complex128)), op)
     print(f"autotuned {n}: {us:.1f} us per fold, candidate {chosen}, {rep}")
     assert rep["located"] > 0
+
+
+def test_graph_in_scatter_vote_mode():
+    """The atomic-scatter vote path (vote array cleared inside the recorded execute) replays exactly."""
+    n, b, loops = SHAPES[1]
+    plan = R.rsft_plan_create(R.make_desc(n, b, loops, p_fa=1e-5, k_max=6, seed=5, max_located=CAP,
+                                          vote_mode=R.RSFT_VOTES_SCATTER))
+    x = _cube(n, b, 5)
+    c, loc_ref, amp_ref = _single(plan, x)
+    loc, amp, cnt = _outputs()
+    g = R.rsft_graph_create(plan, x, cnt, located=loc, amp=amp, lane=1)
+    for _ in range(2):
+        g.launch()
+        torch.cuda.synchronize()
+        assert int(cnt.item()) == c
+        np.testing.assert_array_equal(loc[:c].cpu().numpy(), loc_ref)
+        np.testing.assert_array_equal(amp[:c].cpu().numpy(), amp_ref)
+    g.close()
+
+
+def test_autotune_then_segments_and_multipass_epilogue():
+    """After autotuning, segment mode rebuilds its one-loop tables from the new schedule; a
+    geometry whose fold epilogue runs in passes (512-column chunks, 64 residues, 16 loops)
+    tunes and still meets the oracle."""
+    n, b, loops = (256, 2048), (8, 64), 16
+    seed = 77
+    d, op = make_pair(n, b, loops, seed=seed, p_fa=1e-5, k_max=4, noise_var=1.5, max_located=CAP)
+    tg = ri.draw_targets(n, 6, "offgrid", seed, (10.0, 20.0), int(np.prod(b)), noise_var=1.5)
+    cube = ri.tone_cube(n, tg, 1.5, seed)
+    plan = R.rsft_plan_create(d)
+    x = torch.from_numpy(cube).cuda()
+    us, chosen = R.rsft_plan_autotune(plan, x, candidates=3, reps=2)
+    assert us > 0
+    g = gpu_run(d, cube_dev=x, plan=plan)
+    compare_full(g, O.rsft(op, cube.astype(np.complex128)), op)
+    # segment mode on the tuned plan: every loop folds the same cube -> the plain result
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    loc, amp, _ = _outputs()
+    R.rsft_execute_segments_async(plan, [x] * loops, count, located=loc, amp=amp)
+    torch.cuda.synchronize()
+    c = int(count.item())
+    assert c == g["count"]
+    np.testing.assert_array_equal(loc[:c].cpu().numpy().astype(np.int64), g["located"])
