@@ -434,6 +434,36 @@ def mixed_batch(R, torch, ri, dev, ws, stream, n_frames=512, per_shape=2, lanes=
                     f"over {lanes} lanes per plan, {chunk} graphs per rsft_graph_launch_batch"}
 
 
+def per_pass_roofline(R, torch, wl, nv, seed, cubes, stream, peak, steps, lpp=4):
+    """The fold with `lpp` loops per pass over the cube (ceil(L / lpp) passes, each reading the
+    cube): the HBM-bound form of the same step, against the one fused compute-bound pass."""
+    plan = R.rsft_plan_create(workload_desc(R, wl, nv, seed))
+    R.rsft_plan_set_loops_per_pass(plan, lpp)
+    dev = cubes[0].device
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    loc = torch.zeros(1 << 20, dtype=torch.int64, device=dev)
+    amp = torch.zeros(1 << 20, dtype=torch.complex64, device=dev)
+    for k in range(3):
+        R.rsft_execute_async(plan, cubes[k % len(cubes)], count, stream=stream, located=loc, amp=amp)
+    torch.cuda.synchronize()
+    R.rsft_plan_timing(plan, True)
+    for k in range(steps):
+        R.rsft_execute_async(plan, cubes[k % len(cubes)], count, stream=stream, located=loc, amp=amp)
+    torch.cuda.synchronize()
+    st = R.rsft_plan_get(plan, R.RSFT_GET_STAGE_MS)
+    n = max(1.0, st[6])
+    fold_s = st[0] / n / 1e3
+    fold_bytes = int(R.rsft_plan_get(plan, R.RSFT_GET_FOLD_BYTES)[0])
+    passes = -(-wl.loops // lpp)
+    plan.close()
+    achieved = fold_bytes / fold_s / 1e9
+    return {"bound": "hbm", "loops_per_pass": lpp, "passes": passes, "fold_us": fold_s * 1e6,
+            "us_per_pass": fold_s * 1e6 / passes, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "algorithmic_bytes_per_execute": fold_bytes,
+            "note": "same workload and kernel, the cube read once per pass of lpp loops (CUDA events over "
+                    f"{steps} executes); frames/s is lower than the fused pass, HBM use per byte higher"}
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -605,6 +635,7 @@ def run_ours(args):
     dense = dense_comparator(R, torch, wl, nv, cubes, targets, stream, dev, ws, max(1, min(args.steps, 200)),
                              max(3, min(args.warmup, 10)), cap, value)
     mixed = mixed_batch(R, torch, ri, dev, ws, stream, n_frames=512 if args.steps >= 100 else 64)
+    per_pass = per_pass_roofline(R, torch, wl, nv, seed, cubes, stream, peak, max(10, min(args.steps, 400)))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -637,6 +668,7 @@ def run_ours(args):
                          if tensor_fold else "fold_kernel: SIMT FP32") + ")", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_kind} (copy bandwidth)",
                          "traffic": traffic, "algorithmic_bytes_per_launch": fold_bytes},
+            "roofline_per_pass": per_pass,
             "e2e": {"value": e2e_val, "unit": "frames/s", "h2d_bytes_per_step": int(np.prod(wl.shape)) * 8,
                     "d2h_bytes_per_step": int(d2h / e2e_steps)},
             "plain": {"value": plain_value, "unit": "frames/s", "ms_per_frame": ms_plain / args.steps,

@@ -335,6 +335,16 @@ void rsft_graph_destroy(rsft_graph* graph);
 rsft_status rsft_plan_autotune(rsft_plan* plan, const void* d_cube, void* stream, int32_t candidates, int32_t reps,
                                double* us_out, int32_t* chosen);
 
+/* Loops folded per pass over the cube (1..16; a new plan folds up to 16 loops per pass, so
+ * the radar and mixed-size cubes are read once per execute).  Fewer loops per pass read the
+ * cube ceil(L / loops_per_pass) times with less arithmetic per byte in each pass: the
+ * trade-off between one fused, compute-bound pass and several HBM-bound ones (results are
+ * the same up to FP32 summation order).  Rebuilds the plan's fold tables after waiting for
+ * the device; graphs recorded before must be recorded again.  The paper has no counterpart
+ * (Algorithm 1 folds each loop on its own).  Errors: INVALID_ARG (NULL or host-only plan,
+ * value outside 1..16), UNSUPPORTED, OOM, CUDA. */
+rsft_status rsft_plan_set_loops_per_pass(rsft_plan* plan, int32_t loops_per_pass);
+
 /* Host-buffer batch: frame f reads the host cube h_cubes[f] (pinned memory gets
  * the full copy bandwidth).  Returns when every frame's results are in host
  * memory: h_counts[f] (full count), the first min(count, max_located) entries

@@ -48,6 +48,7 @@ C_SYMBOLS = (
     "rsft_execute_segments_async", "rsft_bartlett_plan_create", "rsft_bartlett_plan_destroy", "rsft_bartlett_execute",
     "rsft_bartlett_execute_async", "rsft_bartlett_get", "rsft_bartlett_copy_spectrum",
     "rsft_graph_create", "rsft_graph_launch", "rsft_graph_launch_batch", "rsft_graph_destroy", "rsft_plan_autotune",
+    "rsft_plan_set_loops_per_pass",
 )
 RSFT_BARTLETT_GAMMA, RSFT_BARTLETT_GAIN, RSFT_BARTLETT_WINDOW, RSFT_BARTLETT_WORKSPACE_BYTES = 1, 2, 3, 4
 
@@ -123,6 +124,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rsft_graph_destroy.restype = None
     lib.rsft_plan_autotune.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_int32, POINTER(ctypes.c_double),
                                        POINTER(c_int32)]
+    lib.rsft_plan_set_loops_per_pass.argtypes = [c_void_p, c_int32]
     lib.rsft_status_string.argtypes = [c_int32]
     lib.rsft_status_string.restype = c_char_p
     lib.rsft_last_error.argtypes = []
@@ -431,6 +433,11 @@ def rsft_plan_autotune(plan: Plan, cube, candidates: int = 4, reps: int = 10, st
     _check(load_library().rsft_plan_autotune(plan.handle, _ptr(cube), _stream(stream), int(candidates), int(reps),
                                              ctypes.byref(us), ctypes.byref(chosen)))
     return float(us.value), int(chosen.value)
+
+
+def rsft_plan_set_loops_per_pass(plan: Plan, loops_per_pass: int) -> None:
+    """Fold `loops_per_pass` loops per pass over the cube (1..16)."""
+    _check(load_library().rsft_plan_set_loops_per_pass(plan.handle, int(loops_per_pass)))
 
 
 class BartlettPlan:

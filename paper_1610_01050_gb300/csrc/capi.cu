@@ -64,6 +64,7 @@ struct rsft_plan {
                                     // 100 + rank on the tensor cores
   bool fold_tc = false;             // the fold runs on the tensor cores (fold_tc.cu)
   int64_t partial_cap = 0;          // elements of every workspace's fold partial-sum buffer
+  int loop_group = rsft::kMaxLoopGroup;  // loops folded per pass over the cube
   std::vector<int> h_sinvb;                 // [L][D] sigma^{-1} mod B_d (fold kernel parameters)
   std::vector<unsigned short> h_slots, h_xdig;
   std::vector<unsigned char> h_xres;        // residue index of each column of a 64-column chunk
@@ -138,8 +139,9 @@ constexpr int64_t kSms = 152;  // streaming multiprocessors the schedule is bala
 // Scores every fold schedule the kernels support and returns the cheapest; with `all`, also
 // every candidate with its model cost (the autotuner times the best few).
 bool choose_fold_schedule(const rsft::Geometry& g, rsft::FoldSchedule& out,
-                          std::vector<std::pair<double, rsft::FoldSchedule>>* all = nullptr) {
-  const int lg = std::min(g.loops, rsft::kMaxLoopGroup);
+                          std::vector<std::pair<double, rsft::FoldSchedule>>* all = nullptr,
+                          int group = rsft::kMaxLoopGroup) {
+  const int lg = std::min(g.loops, group);
   double best = 1e300;
   bool found = false;
   for (int d_in = 0; d_in < g.ndim; ++d_in) {
@@ -525,7 +527,7 @@ rsft_status apply_fold_schedule(rsft_plan* p) {
     p->h_xdig = digits;
     p->tables.h_slots = p->h_slots.data();
     p->tables.h_xdig = p->h_xdig.data();
-    if (rsft::fold_smem_bytes(g, fs, std::min(L, rsft::kMaxLoopGroup)) > 227 * 1024)
+    if (rsft::fold_smem_bytes(g, fs, std::min(L, p->loop_group)) > 227 * 1024)
       return fail(RSFT_ERR_UNSUPPORTED, "fold schedule needs more shared memory than a CTA has");
     // the tensor-core fold (schedules of whole 64-column rows) on request: RSFT_FOLD=tc
     const char* env = std::getenv("RSFT_FOLD");
@@ -534,7 +536,7 @@ rsft_status apply_fold_schedule(rsft_plan* p) {
     for (int c = 0; c < 64 && c < fs.width; ++c) p->h_xres[c] = static_cast<unsigned char>(residue(c));
     p->tables.h_xres = p->h_xres.data();
   }
-  if ((st = build_fold_tables(p, rsft::kMaxLoopGroup, &p->tables.ftable, &p->tables.fcolw)) != RSFT_OK) return st;
+  if ((st = build_fold_tables(p, p->loop_group, &p->tables.ftable, &p->tables.fcolw)) != RSFT_OK) return st;
   return RSFT_OK;
 }
 
@@ -738,7 +740,7 @@ void drain_timing(rsft_plan* p) {
 }
 
 int launches_per_execute(const rsft_plan* p) {
-  const int groups = (p->geom.loops + rsft::kMaxLoopGroup - 1) / rsft::kMaxLoopGroup;
+  const int groups = (p->geom.loops + p->loop_group - 1) / p->loop_group;
   return groups * (p->fold.direct ? 1 : 2) + static_cast<int>(p->passes.size()) + (p->rows_mode ? 3 : 4) + 1;
 }
 
@@ -805,7 +807,7 @@ rsft_status run_lane(rsft_plan* p, rsft::Workspace& ws, bool& votes_dirty, bool 
   mark(0);
   // segment mode: loop l folds its own segment (one loop per launch); otherwise every loop
   // group folds the same cube in one pass
-  const int group = d_segments ? 1 : rsft::kMaxLoopGroup;
+  const int group = d_segments ? 1 : p->loop_group;
   const rsft::DeviceTables& ft = d_segments ? p->seg_tables : p->tables;
   for (int l0 = 0; l0 < g.loops; l0 += group) {
     const int lg = std::min(group, g.loops - l0);
@@ -1276,7 +1278,7 @@ rsft_status rsft_plan_get(const rsft_plan* plan, int32_t what, void* out, size_t
       return RSFT_OK;
     case RSFT_GET_FOLD_BYTES: {
       if (!need(8)) break;
-      const int groups = (L + rsft::kMaxLoopGroup - 1) / rsft::kMaxLoopGroup;
+      const int groups = (L + plan->loop_group - 1) / plan->loop_group;
       *static_cast<int64_t*>(out) = groups * h.total_n * 8 + static_cast<int64_t>(L) * h.total_b * 8;
       return RSFT_OK;
     }
@@ -1365,8 +1367,8 @@ rsft_status fold_cube(rsft_plan* p, const void* d_cube, cudaStream_t stream) {
   if (reinterpret_cast<uintptr_t>(d_cube) % 16 != 0) return fail(RSFT_ERR_INVALID_ARG, "cube must be 16-byte aligned");
   const rsft::Geometry& g = p->geom;
   rsft::Workspace& ws = p->ws;
-  for (int l0 = 0; l0 < g.loops; l0 += rsft::kMaxLoopGroup) {
-    const int lg = std::min(rsft::kMaxLoopGroup, g.loops - l0);
+  for (int l0 = 0; l0 < g.loops; l0 += p->loop_group) {
+    const int lg = std::min(p->loop_group, g.loops - l0);
     cudaError_t e = fold_group(p, p->tables, p->fold_tc, d_cube, l0, lg, ws, stream);
     if (e != cudaSuccess) return cuda_fail(e, "permute_window_fold");
   }
@@ -1423,6 +1425,25 @@ rsft_status rsft_refine(rsft_plan* plan, const void* d_cube, int64_t k, float* d
   return RSFT_OK;
 }
 
+rsft_status rsft_plan_set_loops_per_pass(rsft_plan* plan, int32_t loops_per_pass) {
+  if (!plan) return fail(RSFT_ERR_INVALID_ARG, "NULL plan");
+  if (!plan->has_device) return fail(RSFT_ERR_INVALID_ARG, "host-only plan cannot execute");
+  if (loops_per_pass < 1 || loops_per_pass > rsft::kMaxLoopGroup)
+    return fail(RSFT_ERR_INVALID_ARG, "loops per pass must be 1..16");
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return fail(RSFT_ERR_CUDA, "cudaSetDevice failed");
+  cudaError_t e = cudaDeviceSynchronize();  // the old tables may still be read by queued work
+  if (e != cudaSuccess) return cuda_fail(e, "rsft_plan_set_loops_per_pass");
+  const int previous = plan->loop_group;
+  plan->loop_group = loops_per_pass;
+  const rsft_status st = apply_fold_schedule(plan);
+  if (st != RSFT_OK) {
+    plan->loop_group = previous;
+    apply_fold_schedule(plan);
+  }
+  return st;
+}
+
 rsft_status rsft_plan_autotune(rsft_plan* plan, const void* d_cube, void* stream, int32_t candidates, int32_t reps,
                                double* us_out, int32_t* chosen) {
   if (!plan || !d_cube) return fail(RSFT_ERR_INVALID_ARG, "NULL plan or cube");
@@ -1434,7 +1455,8 @@ rsft_status rsft_plan_autotune(rsft_plan* plan, const void* d_cube, void* stream
   if (!guard.ok) return fail(RSFT_ERR_CUDA, "cudaSetDevice failed");
   std::vector<std::pair<double, rsft::FoldSchedule>> all;
   rsft::FoldSchedule model{};
-  if (!choose_fold_schedule(plan->geom, model, &all)) return fail(RSFT_ERR_UNSUPPORTED, "no fold schedule");
+  if (!choose_fold_schedule(plan->geom, model, &all, plan->loop_group))
+    return fail(RSFT_ERR_UNSUPPORTED, "no fold schedule");
   std::stable_sort(all.begin(), all.end(),
                    [](const std::pair<double, rsft::FoldSchedule>& a, const std::pair<double, rsft::FoldSchedule>& b) {
                      return a.first < b.first;

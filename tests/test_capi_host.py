@@ -180,3 +180,10 @@ def test_graphs_and_autotune_need_a_device_plan():
     assert lib.rsft_graph_launch_batch(None, -1, None) == R.RSFT_ERR_INVALID_ARG
     assert lib.rsft_plan_autotune(plan.handle, R._ptr(cube), None, 0, 10, None, None) == R.RSFT_ERR_INVALID_ARG
     lib.rsft_graph_destroy(None)  # NULL is a no-op
+
+
+def test_loops_per_pass_checks_arguments():
+    lib = R.load_library()
+    assert lib.rsft_plan_set_loops_per_pass(None, 4) == R.RSFT_ERR_INVALID_ARG
+    plan = R.rsft_plan_create(R.make_desc((64, 64), (8, 8), 4, device=-1, p_fa1=0.05, mu=1))
+    assert lib.rsft_plan_set_loops_per_pass(plan.handle, 4) == R.RSFT_ERR_INVALID_ARG  # host-only plan

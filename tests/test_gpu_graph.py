@@ -152,3 +152,22 @@ def test_autotune_then_segments_and_multipass_epilogue():
     c = int(count.item())
     assert c == g["count"]
     np.testing.assert_array_equal(loc[:c].cpu().numpy().astype(np.int64), g["located"])
+
+
+@pytest.mark.parametrize("lpp", [1, 4, 5])
+def test_loops_per_pass_meet_oracle(lpp):
+    """Folding the loops in passes of 1, 4 or 5 (the last pass ragged) gives the oracle's
+    results at every stage, like the default single pass."""
+    n, b, loops = (128, 64, 32), (16, 8, 4), 12
+    seed = 31 + lpp
+    d, op = make_pair(n, b, loops, seed=seed, p_fa=1e-5, k_max=4, noise_var=1.5, max_located=CAP)
+    tg = ri.draw_targets(n, 6, "offgrid", seed, (10.0, 20.0), int(np.prod(b)), noise_var=1.5)
+    cube = ri.tone_cube(n, tg, 1.5, seed)
+    plan = R.rsft_plan_create(d)
+    R.rsft_plan_set_loops_per_pass(plan, lpp)
+    fold_bytes = int(R.rsft_plan_get(plan, R.RSFT_GET_FOLD_BYTES)[0])
+    assert fold_bytes == -(-loops // lpp) * int(np.prod(n)) * 8 + loops * int(np.prod(b)) * 8
+    x = torch.from_numpy(cube).cuda()
+    g = gpu_run(d, cube_dev=x, plan=plan)
+    rep = compare_full(g, O.rsft(op, cube.astype(np.complex128)), op)
+    assert rep["located"] > 0
