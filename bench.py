@@ -204,6 +204,12 @@ def cpu_baseline(wl, cube, nv, seed, min_s=10.0, max_frames=3):
     return {"value": 1.0 / per_frame, "unit": "frames/s", "cores": cores, "kind": "oracle", "sample": sample}
 
 
+def workload_name(wl):
+    """The config's workload string, the same for both arms."""
+    return (f"{wl.name}: {'x'.join(map(str, wl.shape))} complex64, B={'x'.join(map(str, wl.buckets))}, "
+            f"L={wl.loops}, {wl.atten_db:g} dB Chebyshev, Pfa={wl.p_fa:g}, K={wl.k_range[0]}-{wl.k_range[1]} {wl.kind}")
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -229,7 +235,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
         "steps": steps, "warmup": warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "shape": list(wl.shape), "buckets": list(wl.buckets), "loops": wl.loops},
+        "config": {"workload": workload_name(wl), "shape": list(wl.shape), "buckets": list(wl.buckets),
+                   "loops": wl.loops},
         "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -647,9 +654,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {
-                "workload": f"{wl.name}: {'x'.join(map(str, wl.shape))} complex64, B={'x'.join(map(str, wl.buckets))}, "
-                            f"L={wl.loops}, {wl.atten_db:g} dB Chebyshev, Pfa={wl.p_fa:g}, "
-                            f"K={wl.k_range[0]}-{wl.k_range[1]} {wl.kind}",
+                "workload": workload_name(wl),
                 "frames_per_rank_ring": F,
                 "l2": f"inputs larger than L2: ring of {F} frames, {F * int(np.prod(wl.shape)) * 8 / 1e6:.0f} MB",
                 "parallelism": f"frames sharded over {ws} GPU(s), no collective on the data path",
