@@ -366,7 +366,7 @@ rsft_status alloc_workspace(rsft_plan* p, rsft::Workspace& ws, int64_t** d_count
 }
 
 // Fold tables in FP64, rounded once: per row the product of the row dimensions' weights
-// a_{l,d}(s_d) as (c, d - c, c + d, c + d) of w = c + jd, and per column the product of the
+// a_{l,d}(s_d) as (d - c, c + d, c, c) of w = c + jd, and per column the product of the
 // rest; loops grouped by `group` (one fold launch per group).
 rsft_status build_fold_tables(rsft_plan* p, int group, const float4** ftable, const float2** fcolw) {
   const rsft::HostPlan& h = p->host;
@@ -401,8 +401,8 @@ rsft_status build_fold_tables(rsft_plan* p, int group, const float4** ftable, co
             cplx wv(1.0, 0.0);
             for (int d = 0; d < fs.d_in; ++d) wv *= weight(l0 + l, d, sdig[d]);
             ft[tbase + static_cast<size_t>(e) * lg + l] =
-                make_float4(static_cast<float>(wv.real()), static_cast<float>(wv.imag() - wv.real()),
-                            static_cast<float>(wv.real() + wv.imag()), static_cast<float>(wv.real() + wv.imag()));
+                make_float4(static_cast<float>(wv.imag() - wv.real()), static_cast<float>(wv.real() + wv.imag()),
+                            static_cast<float>(wv.real()), static_cast<float>(wv.real()));
           }
         }
       }

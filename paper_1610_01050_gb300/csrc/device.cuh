@@ -85,7 +85,7 @@ struct DeviceTables {
   const float2* ginv[kMaxDim];   // [M_d]: 1 / G_d(-v) (dimension 0 also holds 1 / sum w)
   const unsigned short* slots_by_x; // [X][slots_per_x]: epilogue partial sums of each residue
   const float4* ftable;          // fold row table [loop group][class group][row chunk][row][class][lg]:
-                                 // (c, d-c, c+d, c+d)
+                                 // (d-c, c+d, c, c)
   const float2* fcolw;           // fold column weights [loop group][col chunk][lg][W]
   const int* h_sinvb;            // host copies of small tables passed as kernel parameters
   const unsigned short* h_slots;

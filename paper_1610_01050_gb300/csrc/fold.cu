@@ -18,8 +18,10 @@
 //     acc_l(c) = sum_rows a_l^{row}(row) r(row, c),   contribution a_l^{col}(c) acc_l(c).
 // A complex multiply-add w x r (w = c + jd, r = a + jb) is done with three real
 // multiply-adds, K1 += c (a + b), K2 += (d - c) a, K3 += (c + d) b, and
-// Re = K1 - K3, Im = K1 + K2 at the end; the row table holds (c, d - c, c + d, c + d) so
-// that (K1, K2) and the K3 of both columns advance with paired FP32 multiply-adds.
+// Re = K1 - K3, Im = K1 + K2 at the end; the row table holds (d - c, c + d, c, c) so that
+// (K2, K3) of a column advance with one paired FP32 multiply-add on (a, b) as loaded, and the
+// K1 of both columns with one more on the pair (a + b) of the two columns: no register moves
+// to form operand pairs.
 //
 // Persistent CTAs (as many as fit, two per SM) walk the units.  TMA brings each
 // stage of a shared-memory ring -- one tensor-map box holding a few rows of the C
@@ -62,7 +64,7 @@ struct FoldArgs {
   float2* folded;
   float2* partial;
   int* err;
-  const float4* table;    // this loop group's row table: [group][row chunk][row][class][lg] (c, d - c, c + d, c + d)
+  const float4* table;    // this loop group's row table: [group][row chunk][row][class][lg] (d - c, c + d, c, c)
   const float2* colw;     // this loop group's column weights: [col chunk][lg][W]
   int smem_colw;          // one column chunk: its weights staged in shared memory once
   int ring;               // stages in the ring
@@ -269,21 +271,20 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
       if (ok && !mbar_try_wait(full + slot, parity) && !mbar_wait(full + slot, parity, abort_flag, a.err)) ok = false;
       if (ok && active) {
         const float4* src = reinterpret_cast<const float4*>(smem + slot * a.slot_bytes) + tid;
-        // row-table entries (c, d - c, c + d, c + d): pairs for the paired multiply-adds
+        // row-table entries (d - c, c + d, c, c): pairs for the paired multiply-adds
         const float4* tr = reinterpret_cast<const float4*>(smem + slot * a.slot_bytes + kStageBytes) + ro * LG;
 #pragma unroll
         for (int step = 0; step < kStepsPerStage; ++step) {
           if (step < spst) {
             const float4 v = src[step * (RS * W / 2)];
-            const float2 d0 = make_float2(v.x + v.y, v.x);
-            const float2 d1 = make_float2(v.z + v.w, v.z);
-            const float2 bb = make_float2(v.y, v.w);
+            const float2 x0 = make_float2(v.x, v.y), x1 = make_float2(v.z, v.w);  // (a, b) of the columns
+            const float2 ss = make_float2(v.x + v.y, v.z + v.w);                  // (a + b) of both
 #pragma unroll
             for (int l = 0; l < LG; ++l) {
               const float4 w = tr[step * RS * LG + l];
-              k12a[l] = __ffma2_rn(make_float2(w.x, w.y), d0, k12a[l]);
-              k12b[l] = __ffma2_rn(make_float2(w.x, w.y), d1, k12b[l]);
-              k3[l] = __ffma2_rn(make_float2(w.z, w.w), bb, k3[l]);
+              k12a[l] = __ffma2_rn(make_float2(w.x, w.y), x0, k12a[l]);  // (K2, K3), column cp
+              k12b[l] = __ffma2_rn(make_float2(w.x, w.y), x1, k12b[l]);  // (K2, K3), column cp + 1
+              k3[l] = __ffma2_rn(make_float2(w.z, w.w), ss, k3[l]);      // K1 of both columns
             }
           }
         }
@@ -309,9 +310,9 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
 #pragma unroll
     for (int l = 0; l < LG; ++l) {
       if (CHUNK && (l < lc0 || l >= lc0 + lch)) continue;  // another pass's loop (warp-uniform)
-      const float2 pa = k12a[l], pb = k12b[l], p3 = k3[l];
-      float2 v0 = make_float2(pa.x - p3.x, pa.x + pa.y);
-      float2 v1 = make_float2(pb.x - p3.y, pb.x + pb.y);
+      const float2 pa = k12a[l], pb = k12b[l], p1 = k3[l];
+      float2 v0 = make_float2(p1.x - pa.y, p1.x + pa.x);  // (K1 - K3, K1 + K2)
+      float2 v1 = make_float2(p1.y - pb.y, p1.y + pb.x);
       const float2 w0 = smem_colw ? colw[l * W + cp] : __ldg(cw_g + l * W + cp);
       const float2 w1 = smem_colw ? colw[l * W + cp + 1] : __ldg(cw_g + l * W + cp + 1);
       v0 = (ok && active) ? cmul(w0, v0) : make_float2(0.f, 0.f);
