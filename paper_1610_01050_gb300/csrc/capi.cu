@@ -65,6 +65,7 @@ struct rsft_plan {
   bool fold_tc = false;             // the fold runs on the tensor cores (fold_tc.cu)
   int64_t partial_cap = 0;          // elements of every workspace's fold partial-sum buffer
   int loop_group = rsft::kMaxLoopGroup;  // loops folded per pass over the cube
+  int sms = 152;                    // streaming multiprocessors of the plan's device (schedule balance)
   std::vector<int> h_sinvb;                 // [L][D] sigma^{-1} mod B_d (fold kernel parameters)
   std::vector<unsigned short> h_slots, h_xdig;
   std::vector<unsigned char> h_xres;        // residue index of each column of a 64-column chunk
@@ -134,11 +135,9 @@ float2 to_f2(cplx v) { return make_float2(static_cast<float>(v.real()), static_c
 
 // Choose how the fold splits rows and columns (see fold.cu).  Costs are relative to
 // the 8 bytes each cube element costs: per-element row-weight setup and partial-sum traffic.
-constexpr int64_t kSms = 152;  // streaming multiprocessors the schedule is balanced for
-
 // Scores every fold schedule the kernels support and returns the cheapest; with `all`, also
 // every candidate with its model cost (the autotuner times the best few).
-bool choose_fold_schedule(const rsft::Geometry& g, rsft::FoldSchedule& out,
+bool choose_fold_schedule(const rsft::Geometry& g, int sms, rsft::FoldSchedule& out,
                           std::vector<std::pair<double, rsft::FoldSchedule>>* all = nullptr,
                           int group = rsft::kMaxLoopGroup) {
   const int lg = std::min(g.loops, group);
@@ -182,7 +181,7 @@ bool choose_fold_schedule(const rsft::Geometry& g, rsft::FoldSchedule& out,
       // persistent CTAs (two per SM) take units round robin and each runs at about a fixed
       // rate: the busiest CTA's units against an even share, plus a per-unit cost (epilogue,
       // ring refill) worth about 3072 elements of the row loop
-      const double slots = 2.0 * kSms;
+      const double slots = 2.0 * sms;
       const double per_cta = std::ceil(static_cast<double>(units) / slots);
       const double balance = std::min(4.0, per_cta / (static_cast<double>(units) / slots) - 1.0) +
                              3072.0 / static_cast<double>(cps * rpc * width);
@@ -563,7 +562,13 @@ rsft_status build_device(rsft_plan* p) {
       g.b_shift[d] += g.log_b[e];
     }
   }
-  if (!choose_fold_schedule(g, p->fold))
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess || sms < 1) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  p->sms = sms;
+  if (!choose_fold_schedule(g, sms, p->fold))
     return fail(RSFT_ERR_UNSUPPORTED, "no fold schedule for this bucket grid (inner B_d too large)");
   p->rows = rsft::VoteRowSchedule{};
   p->rows_mode = h.desc.vote_mode == RSFT_VOTES_ROWS && choose_vote_rows(g, p->rows) &&
@@ -1455,7 +1460,7 @@ rsft_status rsft_plan_autotune(rsft_plan* plan, const void* d_cube, void* stream
   if (!guard.ok) return fail(RSFT_ERR_CUDA, "cudaSetDevice failed");
   std::vector<std::pair<double, rsft::FoldSchedule>> all;
   rsft::FoldSchedule model{};
-  if (!choose_fold_schedule(plan->geom, model, &all, plan->loop_group))
+  if (!choose_fold_schedule(plan->geom, plan->sms, model, &all, plan->loop_group))
     return fail(RSFT_ERR_UNSUPPORTED, "no fold schedule");
   std::stable_sort(all.begin(), all.end(),
                    [](const std::pair<double, rsft::FoldSchedule>& a, const std::pair<double, rsft::FoldSchedule>& b) {
