@@ -27,11 +27,16 @@
  *  - DFTs are forward (kernel e^{-j 2 pi k n / B}) and unnormalised (eq. (f)).
  *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
  *    default stream).  Calls are stream-ordered unless stated otherwise.
+ *  - Threads: a plan (its workspaces, lanes, events and the graphs recorded
+ *    on it) is used by one host thread at a time; calls that share a plan
+ *    from several threads must be serialised by the caller.  Different plans
+ *    are independent.
  *  - Errors: every call returns an rsft_status; on failure nothing is
  *    guaranteed about the outputs and rsft_last_error() holds a message.
- *    The library never traps, never spins on device flags, and never falls
- *    back to the CPU: without a usable CUDA device, calls that need one
- *    return RSFT_ERR_CUDA.
+ *    The library never traps and never falls back to the CPU: without a
+ *    usable CUDA device, calls that need one return RSFT_ERR_CUDA.  Kernels
+ *    wait only on their own CTA's barriers, each wait bounded (2 s); a wait
+ *    that gives up makes the call return RSFT_ERR_TIMEOUT.
  */
 #ifndef RSFT_H
 #define RSFT_H
