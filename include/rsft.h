@@ -36,7 +36,9 @@
  *    The library never traps and never falls back to the CPU: without a
  *    usable CUDA device, calls that need one return RSFT_ERR_CUDA.  Kernels
  *    wait only on their own CTA's barriers, each wait bounded (2 s); a wait
- *    that gives up makes the call return RSFT_ERR_TIMEOUT.
+ *    that gives up sets the plan's error flag, which the synchronous calls
+ *    (rsft_execute, rsft_execute_host and their batch forms) report as
+ *    RSFT_ERR_TIMEOUT.
  */
 #ifndef RSFT_H
 #define RSFT_H
