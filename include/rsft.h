@@ -37,7 +37,8 @@
  *    usable CUDA device, calls that need one return RSFT_ERR_CUDA.  Kernels
  *    wait only on their own CTA's barriers, each wait bounded (2 s); a wait
  *    that gives up sets the plan's error flag, which the synchronous calls
- *    (rsft_execute, rsft_execute_host and their batch forms) report as
+ *    (rsft_execute, rsft_execute_segments, rsft_execute_host,
+ *    rsft_execute_host_batch) report as
  *    RSFT_ERR_TIMEOUT.
  */
 #ifndef RSFT_H
