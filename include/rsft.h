@@ -232,9 +232,12 @@ rsft_status rsft_copy_detections(rsft_plan* plan, void* d_out, void* stream);
  *   diagonal (device float [K][D + 1]: amplitude term, then one per frequency;
  *   NULL allowed) of the tones against the buckets of the last prepare or
  *   execute.  Stream-ordered.
- * rsft_refine: prepare, then `steps` Levenberg-Marquardt updates per tone
- *   (the Gauss-Newton matrix of a tone's amplitude and D frequencies, damped by
- *   1e-3 of its diagonal; theta += lr * delta), in place on d_freq and d_amp.
+ * rsft_refine: prepare, then `steps` Levenberg-Marquardt iterations, in place
+ *   on d_freq and d_amp.  Each tone solves (H + lambda diag H) delta = -g with
+ *   its own Gauss-Newton matrix H of (a_re, a_im, f_0 .. f_{D-1}) and moves by
+ *   lr * delta; the trial is kept when the loss E drops (lambda / 10) and
+ *   undone otherwise (lambda * 10), lambda starting at 1e-3.  The tones end at
+ *   the kept point of lowest E (steps + 1 evaluations of E).
  * Errors: INVALID_ARG (NULL, k < 1, steps < 0, lr <= 0, misaligned cube),
  * UNSUPPORTED (K > 2^20), OOM, CUDA.
  */

@@ -465,27 +465,37 @@ rsft_status apply_fold_schedule(rsft_plan* p) {
       }
       return x;
     };
-    // lane bit k moves a thread by 2^(k+1) elements: a column bit or, past the chunk width, a
-    // row bit (the class of the row for the first log2 C row bits, then its row)
-    int rmask = 0;
-    for (int k = 0; k < 5; ++k) {
-      const int pbit = k + 1;
-      bool keep = true;
-      if ((int64_t(1) << pbit) >= fs.width) {
-        keep = ((int64_t(1) << pbit) / fs.width) >= fs.cps;
-      } else {
-        int acc = 0;
-        for (int d = D - 1; d >= fs.d_in; --d) {
-          const int ln = ilog2(h.n[d]);
-          if (pbit < acc + ln) {
-            keep = (pbit - acc) >= ilog2(h.b[d]);
-            break;
-          }
-          acc += ln;
-        }
+    // element bit e of a row step: a column bit or, past the chunk width, a row bit (the class
+    // of the row for the first log2 C row bits, then its row); does flipping it keep the
+    // thread's (class, inner residue)?
+    auto keeps = [&](int e) {
+      if ((int64_t(1) << e) >= fs.width) return ((int64_t(1) << e) / fs.width) >= fs.cps;
+      int acc = 0;
+      for (int d = D - 1; d >= fs.d_in; --d) {
+        const int ln = ilog2(h.n[d]);
+        if (e < acc + ln) return (e - acc) >= ilog2(h.b[d]);
+        acc += ln;
       }
-      if (keep) rmask |= 1 << k;
+      return true;
+    };
+    // thread -> column pair: thread bits 0-2 stay on pair bits 0-2 (a quarter warp reads 128
+    // contiguous bytes, free of bank conflicts); when a chunk row has more than 32 pairs,
+    // thread bits 3-4 take the lowest pair bits that keep the residue, so the warp shuffle
+    // sums them instead of the epilogue's shared-memory partials
+    int perm[8] = {0, 1, 2, 3, 4, 5, 6, 7};
+    const int pair_bits = ilog2(fs.width / 2);
+    if (pair_bits > 5) {
+      std::vector<int> first, rest;
+      for (int pb = 3; pb < pair_bits; ++pb) (keeps(pb + 1) && first.size() < 2 ? first : rest).push_back(pb);
+      first.insert(first.end(), rest.begin(), rest.end());
+      for (int b = 3; b < pair_bits; ++b) perm[b] = first[b - 3];
     }
+    fs.lane_perm = 0;
+    for (int b = 0; b < 8; ++b) fs.lane_perm |= static_cast<unsigned>(perm[b]) << (4 * b);
+    // lane bit k moves a thread's pair index by 2^perm[k], its elements by twice that
+    int rmask = 0;
+    for (int k = 0; k < 5; ++k)
+      if (keeps(perm[k] + 1)) rmask |= 1 << k;
     int nbits = 0;
     for (int k = 0; k < 5; ++k) nbits += (rmask >> k) & 1;
     fs.red_mask = rmask;
@@ -504,7 +514,7 @@ rsft_status apply_fold_schedule(rsft_plan* p) {
         for (int b = 0; b < 5; ++b)
           if (!((rmask >> b) & 1)) lane |= ((j >> bit++) & 1) << b;
         for (int c = 0; c < 2; ++c) {
-          const int64_t elem = 2 * (32 * w + lane) + c;
+          const int64_t elem = 2 * static_cast<int64_t>(rsft::fold_pair_of(32 * w + lane, fs.lane_perm)) + c;
           const int64_t x = ((elem / fs.width) % fs.cps) * fs.xcount + residue(elem & (fs.width - 1));
           if (fill[x] >= fs.slots_per_x) return fail(RSFT_ERR_UNSUPPORTED, "fold epilogue: residues not balanced");
           cols[x * fs.slots_per_x + fill[x]++] = static_cast<unsigned short>((w * fs.leaders + j) * 2 + c);
@@ -1363,6 +1373,11 @@ rsft_status ensure_refine(rsft_plan* p, int64_t k) {
   const int vals = 3 + 5 * rsft::kMaxDim + rsft::kMaxDim * (rsft::kMaxDim - 1);
   if ((st = dev_alloc(p, &w.contr, static_cast<size_t>(h.loops) * kk * vals * sizeof(float))) != RSFT_OK)
     return st;
+  if ((st = dev_alloc(p, &w.lm_gh, static_cast<size_t>(2) * kk * rsft::kLmTone * sizeof(double))) != RSFT_OK)
+    return st;
+  if ((st = dev_alloc(p, &w.lm_freq, static_cast<size_t>(kk) * rsft::kMaxDim * sizeof(float))) != RSFT_OK) return st;
+  if ((st = dev_alloc(p, &w.lm_amp, static_cast<size_t>(kk) * sizeof(float2))) != RSFT_OK) return st;
+  if (!w.lm_state && (st = dev_alloc(p, &w.lm_state, 8 * sizeof(double))) != RSFT_OK) return st;
   w.k_cap = kk;
   return RSFT_OK;
 }
@@ -1402,9 +1417,8 @@ rsft_status rsft_refine_eval(rsft_plan* plan, int64_t k, const float* d_freq, co
   rsft_status st = ensure_refine(plan, k);
   if (st != RSFT_OK) return st;
   cudaError_t e = rsft::launch_refine_eval(plan->refine_geom, plan->tables, plan->refine, plan->ws.folded,
-                                           static_cast<int>(k), const_cast<float*>(d_freq),
-                                           static_cast<float2*>(const_cast<void*>(d_amp)), d_loss, d_grad_freq,
-                                           static_cast<float2*>(d_grad_amp), d_hdiag, 0.f,
+                                           static_cast<int>(k), d_freq, static_cast<const float2*>(d_amp), d_loss,
+                                           d_grad_freq, static_cast<float2*>(d_grad_amp), d_hdiag, nullptr,
                                            static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? RSFT_OK : cuda_fail(e, "rsft_refine_eval");
 }
@@ -1421,10 +1435,12 @@ rsft_status rsft_refine(rsft_plan* plan, const void* d_cube, int64_t k, float* d
   rsft_status st = ensure_refine(plan, k);
   if (st == RSFT_OK) st = fold_cube(plan, d_cube, s);
   if (st != RSFT_OK) return st;
-  for (int it = 0; it < steps; ++it) {
-    cudaError_t e = rsft::launch_refine_eval(plan->refine_geom, plan->tables, plan->refine, plan->ws.folded,
-                                             static_cast<int>(k), d_freq, static_cast<float2*>(d_amp), nullptr,
-                                             nullptr, nullptr, nullptr, lr, s);
+  // steps + 1 evaluations: the starting point, then one trial per step; the tones end at the
+  // accepted point of lowest loss
+  for (int it = 0; steps > 0 && it <= steps; ++it) {
+    cudaError_t e = rsft::launch_refine_step(plan->refine_geom, plan->tables, plan->refine, plan->ws.folded,
+                                             static_cast<int>(k), d_freq, static_cast<float2*>(d_amp), it, lr,
+                                             it == steps, s);
     if (e != cudaSuccess) return cuda_fail(e, "rsft_refine");
   }
   return RSFT_OK;

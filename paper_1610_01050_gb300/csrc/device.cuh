@@ -46,7 +46,17 @@ struct FoldSchedule {
   int red_mask;           // lane bits whose flip keeps a thread's (class, column residue) (shuffle-summed)
   int leaders;            // lanes per warp left after the shuffle sum: 32 >> popcount(red_mask)
   int slots_per_x;        // epilogue partial sums per (class, residue): 2 * warps * leaders / (C X)
+  unsigned lane_perm;     // thread -> column pair: nibble b is the pair-index bit that thread bit b sets
 };
+
+// Column pair (float4 index into a row step) of fold thread tid: the thread's bits placed as
+// lane_perm says (the identity 0x76543210 is the pair tid itself).
+__host__ __device__ __forceinline__ int fold_pair_of(int tid, unsigned lane_perm) {
+  int q = 0;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) q |= ((tid >> b) & 1) << ((lane_perm >> (4 * b)) & 15u);
+  return q;
+}
 
 // One FFT pass over the bucket arrays: transforms dimensions [da, db) in shared memory.
 struct FftPass {
@@ -133,15 +143,26 @@ struct RefineWork {
   double* partial = nullptr;
   int parts = 0;            // residual blocks (loss partial sums)
   float* contr = nullptr;   // [L][K][3 + 5 kMaxDim + kMaxDim (kMaxDim - 1)] contractions
+  double* lm_gh = nullptr;  // [2][K][kLmTone] g and Gauss-Newton matrix per tone: last trial, accepted point
+  float* lm_freq = nullptr; // [K][D] frequencies of the accepted point
+  float2* lm_amp = nullptr; // [K] amplitudes of the accepted point
+  double* lm_state = nullptr;  // [2][E, lambda] (one half per iteration), [4] E of the last trial
   int64_t k_cap = 0;
 };
+constexpr int kLmTone = (kMaxDim + 2) + (kMaxDim + 2) * (kMaxDim + 2);
 
 // Launchers (return cudaSuccess or the launch error).
-// Loss, gradient and Gauss-Newton diagonal of K tones against the folded buckets; with lr > 0
-// the tones are also updated in place by a damped diagonal Gauss-Newton step.
+// Loss, gradient and Gauss-Newton diagonal of K tones against the folded buckets (each may be
+// null); with gh set, each tone's gradient and Gauss-Newton matrix are stored there too.
 cudaError_t launch_refine_eval(const RefineGeom& rg, const DeviceTables& t, const RefineWork& w,
-                               const float2* folded, int K, float* freq, float2* amp, double* loss,
-                               float* grad_freq, float2* grad_amp, float* hdiag, float lr, cudaStream_t stream);
+                               const float2* folded, int K, const float* freq, const float2* amp, double* loss,
+                               float* grad_freq, float2* grad_amp, float* hdiag, double* gh, cudaStream_t stream);
+// One Levenberg-Marquardt iteration (iter = 0, 1, ...): evaluate the tones' current parameters,
+// accept or reject them against the accepted point's loss (adapting the damping), and move the
+// tones to the next trial -- or, with final_call, back to the accepted point.
+cudaError_t launch_refine_step(const RefineGeom& rg, const DeviceTables& t, const RefineWork& w,
+                               const float2* folded, int K, float* freq, float2* amp, int iter, float lr,
+                               bool final_call, cudaStream_t stream);
 // Exclusive scan of n u32 counts into offsets[0..n] (offsets[n] = total), total also to *total.
 cudaError_t launch_count_scan(const uint32_t* counts, int64_t n, uint64_t* offsets, int64_t* total,
                               cudaStream_t stream);

@@ -30,8 +30,11 @@
 // finish with a slot refills it, so the next unit's rows arrive during an epilogue.
 // The epilogue applies the column weights, sums threads of equal (class, residue)
 // with warp shuffles over the lane bits that keep both, then across warps in a fixed
-// order (deterministic results).  Every barrier wait is bounded in time; a wait that
-// gives up sets the plan's error flag and the CTA skips its remaining work.
+// order (deterministic results).  Which column pair a thread holds is a permutation of
+// its index's bits chosen with the schedule: in chunk rows wider than a warp, lane bits
+// 3-4 sit on column bits that keep the residue, so the shuffles do most of that sum.
+// Every barrier wait is bounded in time; a wait that gives up sets the plan's error flag
+// and the CTA skips its remaining work.
 #include <cuda.h>
 
 #include "device.cuh"
@@ -45,6 +48,7 @@ __host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 
 constexpr int kThreads = kFoldConsumers;   // 256 threads, two columns each
+static_assert(kThreads == 256, "fold_pair_of places 8 thread bits");
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxRing = 8;                // shared-memory stages
 constexpr int kStepsPerStage = 8;          // row steps (2 * threads elements each) per stage
@@ -228,8 +232,10 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
   }
 
   // this thread: columns cp, cp + 1 of row slot ro = (class c = ro % C, row ro / C) of each step
-  const int cp = (2 * tid) & (W - 1);
-  const int ro = (2 * tid) >> a.log_width;
+  // (pair pq of the step: the thread's bits as the schedule places them)
+  const int pq = fold_pair_of(tid, fs.lane_perm);
+  const int cp = (2 * pq) & (W - 1);
+  const int ro = (2 * pq) >> a.log_width;
   const bool active = ro < RS;
   bool ok = true;
   if (smem_colw) ok = mbar_wait(cbar, 0u, abort_flag, a.err);
@@ -270,7 +276,7 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
     for (int k = 0; k < nst; ++k, ++i) {
       if (ok && !mbar_try_wait(full + slot, parity) && !mbar_wait(full + slot, parity, abort_flag, a.err)) ok = false;
       if (ok && active) {
-        const float4* src = reinterpret_cast<const float4*>(smem + slot * a.slot_bytes) + tid;
+        const float4* src = reinterpret_cast<const float4*>(smem + slot * a.slot_bytes) + pq;
         // row-table entries (d - c, c + d, c, c): pairs for the paired multiply-adds
         const float4* tr = reinterpret_cast<const float4*>(smem + slot * a.slot_bytes + kStageBytes) + ro * LG;
 #pragma unroll

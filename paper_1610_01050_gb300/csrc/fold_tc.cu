@@ -577,6 +577,7 @@ cudaError_t launch_tc_lg(const TcArgs& args, int smem, cudaStream_t stream) {
 
 bool fold_tc_supported(const Geometry& g, const FoldSchedule& fs) {
   if (fs.width != kTcW || fs.col_chunks != 1 || !fs.direct || fs.row_chunks != 1) return false;
+  if (fs.lane_perm != 0x76543210u) return false;  // the epilogue tables assume thread = column pair
   if (fs.d_in < 1 || fs.d_in > 2 || fs.rows_per_chunk % kTcRows != 0 || fs.classes % kTcClasses != 0) return false;
   if (g.b[fs.d_in - 1] < kTcClasses) return false;  // the box's two classes are consecutive x_{d_in - 1}
   if (fs.xcount > kTcW || kTcW % fs.xcount != 0) return false;

@@ -224,11 +224,11 @@ __global__ void __launch_bounds__(kRefineThreads) contract_kernel(RefineGeom rg,
 
 // Per tone: sums over loops (fixed order) into the gradient and the Gauss-Newton matrix of the
 // real parameters (a_re, a_im, f_0 .. f_{D-1}); thread 0 of block 0 also sums the loss
-// partials.  With lr > 0 the tone then takes a Levenberg-Marquardt step: solve
-// (H + lambda diag H) delta = -g in FP64 and add lr * delta (frequencies wrapped into [0, 1)).
+// partials.  With gh set, each tone's g and H go there ([K][P + P^2], P = D + 2) for the
+// Levenberg-Marquardt iteration.
 __global__ void finish_kernel(RefineGeom rg, const float* __restrict__ out, int K, const double* __restrict__ partial,
-                              int nparts, float* freq, float2* amp, double* loss, float* grad_freq, float2* grad_amp,
-                              float* hdiag, float lr) {
+                              int nparts, const float2* __restrict__ amp, double* loss, float* grad_freq,
+                              float2* grad_amp, float* hdiag, double* gh) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k == 0 && loss) {
     double s = 0.0;
@@ -273,56 +273,101 @@ __global__ void finish_kernel(RefineGeom rg, const float* __restrict__ out, int 
     if (hdiag) hdiag[k * (D + 1) + 1 + d] = static_cast<float>(H[2 + d][2 + d]);
   }
   if (hdiag) hdiag[k * (D + 1)] = static_cast<float>(H[0][0]);
-  if (lr > 0.f) {
-    // Levenberg-Marquardt: (H + 1e-3 diag H + tiny) delta = -g, Gaussian elimination with pivoting
-    double M[kMaxDim + 2][kMaxDim + 3];
-    for (int i = 0; i < P; ++i) {
-      for (int j = 0; j < P; ++j) M[i][j] = H[i][j];
-      M[i][i] += 1e-3 * H[i][i] + 1e-30;
-      M[i][P] = -g[i];
+  if (gh) {
+    double* o = gh + static_cast<int64_t>(k) * kLmTone;
+    for (int i = 0; i < P; ++i) o[i] = g[i];
+    for (int i = 0; i < P; ++i)
+      for (int j = 0; j < P; ++j) o[P + i * P + j] = H[i][j];
+  }
+}
+
+constexpr double kLambda0 = 1e-3, kLambdaMin = 1e-7, kLambdaMax = 1e7;
+
+// One Levenberg-Marquardt iteration over all tones, with Marquardt's adaptive damping.  The
+// tones' current parameters (the trial just evaluated) are accepted when their loss is below
+// the accepted point's (always on the first call, iter = 0), and lambda shrinks tenfold;
+// otherwise the tones return to the accepted point and lambda grows tenfold.  Each tone then
+// solves (H + lambda diag H) delta = -g at the accepted point (FP64, Gaussian elimination with
+// pivoting) and moves to accepted + lr delta, the next trial (frequencies wrapped into
+// [0, 1)); on the final call it stays at the accepted point instead.  Every thread derives the
+// decision and lambda from the same values; thread 0 writes them to the other half of the
+// double-buffered state ([2][E, lambda]; state[4] = the trial's loss) for the next call.
+__global__ void lm_kernel(RefineGeom rg, int K, float* freq, float2* amp, double* gh, float* acc_freq,
+                          float2* acc_amp, double* state, int iter, float lr, int final_call) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const double* prev = state + 2 * (iter & 1);
+  const double e_trial = state[4];
+  const bool accept = iter == 0 || e_trial < prev[0];  // a NaN loss is never below
+  const double lambda = iter == 0 ? kLambda0
+                        : accept  ? fmax(prev[1] * 0.1, kLambdaMin)
+                                  : fmin(prev[1] * 10.0, kLambdaMax);
+  if (k == 0) {
+    double* next = state + 2 * ((iter + 1) & 1);
+    next[0] = accept ? e_trial : prev[0];
+    next[1] = lambda;
+  }
+  if (k >= K) return;
+  const int D = rg.ndim, P = D + 2;
+  const double* trial = gh + static_cast<int64_t>(k) * kLmTone;
+  double* acc = gh + (static_cast<int64_t>(K) + k) * kLmTone;
+  if (accept) {
+    for (int i = 0; i < P + P * P; ++i) acc[i] = trial[i];
+    for (int d = 0; d < D; ++d) acc_freq[k * D + d] = freq[k * D + d];
+    acc_amp[k] = amp[k];
+  }
+  const float2 a0 = acc_amp[k];
+  if (final_call) {
+    amp[k] = a0;
+    for (int d = 0; d < D; ++d) freq[k * D + d] = acc_freq[k * D + d];
+    return;
+  }
+  double M[kMaxDim + 2][kMaxDim + 3];
+  for (int i = 0; i < P; ++i) {
+    for (int j = 0; j < P; ++j) M[i][j] = acc[P + i * P + j];
+    M[i][i] += lambda * acc[P + i * P + i] + 1e-30;
+    M[i][P] = -acc[i];
+  }
+  bool ok = true;
+  for (int c = 0; c < P && ok; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < P; ++r)
+      if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
+    if (!(fabs(M[piv][c]) > 0.0)) {
+      ok = false;
+      break;
     }
-    bool ok = true;
-    for (int c = 0; c < P && ok; ++c) {
-      int piv = c;
-      for (int r = c + 1; r < P; ++r)
-        if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
-      if (!(fabs(M[piv][c]) > 0.0)) {
-        ok = false;
-        break;
+    if (piv != c)
+      for (int j = c; j <= P; ++j) {
+        const double tmp = M[c][j];
+        M[c][j] = M[piv][j];
+        M[piv][j] = tmp;
       }
-      if (piv != c)
-        for (int j = c; j <= P; ++j) {
-          const double tmp = M[c][j];
-          M[c][j] = M[piv][j];
-          M[piv][j] = tmp;
-        }
-      for (int r = c + 1; r < P; ++r) {
-        const double f = M[r][c] / M[c][c];
-        for (int j = c; j <= P; ++j) M[r][j] -= f * M[c][j];
-      }
+    for (int r = c + 1; r < P; ++r) {
+      const double f = M[r][c] / M[c][c];
+      for (int j = c; j <= P; ++j) M[r][j] -= f * M[c][j];
     }
-    if (ok) {
-      double delta[kMaxDim + 2];
-      for (int i = P - 1; i >= 0; --i) {
-        double t = M[i][P];
-        for (int j = i + 1; j < P; ++j) t -= M[i][j] * delta[j];
-        delta[i] = t / M[i][i];
-      }
-      amp[k] = make_float2(static_cast<float>(ar + lr * delta[0]), static_cast<float>(ai + lr * delta[1]));
-      for (int d = 0; d < D; ++d) {
-        double f = freq[k * D + d] + lr * delta[2 + d];
-        f -= floor(f);
-        freq[k * D + d] = static_cast<float>(f);
-      }
+  }
+  double delta[kMaxDim + 2];
+  for (int i = 0; i < P; ++i) delta[i] = 0.0;
+  if (ok)
+    for (int i = P - 1; i >= 0; --i) {
+      double t = M[i][P];
+      for (int j = i + 1; j < P; ++j) t -= M[i][j] * delta[j];
+      delta[i] = t / M[i][i];
     }
+  amp[k] = make_float2(static_cast<float>(a0.x + lr * delta[0]), static_cast<float>(a0.y + lr * delta[1]));
+  for (int d = 0; d < D; ++d) {
+    double f = acc_freq[k * D + d] + lr * delta[2 + d];
+    f -= floor(f);
+    freq[k * D + d] = static_cast<float>(f);
   }
 }
 
 }  // namespace
 
 cudaError_t launch_refine_eval(const RefineGeom& rg, const DeviceTables& t, const RefineWork& w,
-                               const float2* folded, int K, float* freq, float2* amp, double* loss,
-                               float* grad_freq, float2* grad_amp, float* hdiag, float lr, cudaStream_t stream) {
+                               const float2* folded, int K, const float* freq, const float2* amp, double* loss,
+                               float* grad_freq, float2* grad_amp, float* hdiag, double* gh, cudaStream_t stream) {
   const int64_t warps = static_cast<int64_t>(rg.loops) * K * rg.sumb;
   int blocks = static_cast<int>(std::min<int64_t>((warps + 7) / 8, 152 * 16));
   tone_response_kernel<<<std::max(blocks, 1), 256, 0, stream>>>(rg, t, freq, K, w.gres, w.gder);
@@ -332,8 +377,19 @@ cudaError_t launch_refine_eval(const RefineGeom& rg, const DeviceTables& t, cons
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   contract_kernel<<<rg.loops * K, kRefineThreads, 0, stream>>>(rg, w.resid, w.gres, w.gder, K, w.contr);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  finish_kernel<<<(K + 127) / 128, 128, 0, stream>>>(rg, w.contr, K, w.partial, w.parts, freq, amp, loss, grad_freq,
-                                                     grad_amp, hdiag, lr);
+  finish_kernel<<<(K + 127) / 128, 128, 0, stream>>>(rg, w.contr, K, w.partial, w.parts, amp, loss, grad_freq,
+                                                     grad_amp, hdiag, gh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine_step(const RefineGeom& rg, const DeviceTables& t, const RefineWork& w,
+                               const float2* folded, int K, float* freq, float2* amp, int iter, float lr,
+                               bool final_call, cudaStream_t stream) {
+  cudaError_t e = launch_refine_eval(rg, t, w, folded, K, freq, amp, w.lm_state + 4, nullptr, nullptr, nullptr,
+                                     w.lm_gh, stream);
+  if (e != cudaSuccess) return e;
+  lm_kernel<<<(K + 127) / 128, 128, 0, stream>>>(rg, K, freq, amp, w.lm_gh, w.lm_freq, w.lm_amp, w.lm_state, iter,
+                                                 lr, final_call ? 1 : 0);
   return cudaGetLastError();
 }
 

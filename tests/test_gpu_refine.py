@@ -124,3 +124,35 @@ def test_refinement_reduces_off_grid_frequency_error():
     rmse0, rmse1 = math.sqrt(np.mean(err0 ** 2)), math.sqrt(np.mean(err1 ** 2))
     assert rmse1 < 0.1 * rmse0, (rmse0, rmse1)
     assert np.max(np.abs(a.cpu().numpy() - true_a) / np.abs(true_a)) < 0.05
+
+
+def test_refinement_keeps_only_steps_that_lower_the_loss():
+    """Two tones 1.5 bins apart with a third model tone on the same pair: the per-tone steps are
+    coupled, so single trials can raise the loss; the iteration keeps only trials that lower it,
+    ends at the best kept point, and zero steps leave the tones as given."""
+    n, b, loops = (64, 64), (8, 8), 6
+    true_f = np.array([[20.3, 30.6], [21.8, 30.9]]) / 64.0
+    true_a = np.array([1.5 + 0.5j, -1.0 + 1.2j])
+    rng = np.random.default_rng(8)
+    cube = O.tone_field(n, true_f, true_a) + 0.05 * (rng.standard_normal(n) + 1j * rng.standard_normal(n))
+    plan = R.rsft_plan_create(R.make_desc(n, b, loops, seed=8, atten_db=50.0, p_fa1=0.05, mu=1))
+    x = torch.from_numpy(cube.astype(np.complex64)).cuda()
+    f0 = (np.array([[20.0, 31.0], [22.0, 31.0], [21.0, 30.0]]) / 64.0).astype(np.float32)
+    a0 = np.array([1.0, 1.0j, 0.5], dtype=np.complex64)
+    R.rsft_refine_prepare(plan, x)
+    e_start = _eval(plan, f0, a0)[0]
+    f = torch.from_numpy(f0).cuda()
+    a = torch.from_numpy(a0).cuda()
+    R.rsft_refine(plan, x, 3, f, a, 0, 1.0)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(f.cpu().numpy(), f0)
+    np.testing.assert_array_equal(a.cpu().numpy(), a0)
+    losses = [e_start]
+    for steps in (1, 3, 10, 30):
+        f = torch.from_numpy(f0).cuda()
+        a = torch.from_numpy(a0).cuda()
+        R.rsft_refine(plan, x, 3, f, a, steps, 1.0)
+        torch.cuda.synchronize()
+        losses.append(_eval(plan, f.cpu().numpy(), a.cpu().numpy())[0])
+    assert all(l1 <= l0 for l0, l1 in zip(losses, losses[1:])), losses
+    assert losses[-1] < 0.5 * losses[0], losses
