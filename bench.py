@@ -364,6 +364,50 @@ def segment_mode(R, torch, plan, wl, cubes, stream, dev, ws, located, amp, count
             "note": "one 1024x256x64 segment per loop, taken round-robin from the ring of frames"}
 
 
+SRUR_BUCKETS = (64, 16, 8)
+SRUR_BURSTS = 8
+
+
+def srur_frames(R, torch, ri, dev, ws, stream, frames):
+    """SRUR radar frames (§VI): 8 bursts of the Table III system (2048 range samples x 64
+    elements x 32 repetition intervals, complex64, 268 MB per frame) with the Table IV targets
+    at their "mixed" SNRs and Swerling-I amplitudes redrawn per burst, one burst per loop
+    (segment mode), B = 64x16x8, 60 dB Chebyshev, P_fa = 1e-6; Pd of the four targets."""
+    sy = ri.SrurSystem()
+    cubes, freqs, _ = ri.srur_bursts(sy, ri.TABLE_IV["mixed"], SRUR_BURSTS, seed=4001)
+    segs = [torch.from_numpy(c).to(dev) for c in cubes]
+    del cubes
+    cap = 1 << 18
+    plan = R.rsft_plan_create(R.make_desc(sy.shape, SRUR_BUCKETS, SRUR_BURSTS, atten_db=60.0, p_fa=1e-6, k_max=4,
+                                          noise_var=1.0, seed=4001, max_located=cap))
+    loc = torch.zeros(cap, dtype=torch.int64, device=dev)
+    amp = torch.zeros(cap, dtype=torch.complex64, device=dev)
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    c = min(R.rsft_execute_segments(plan, segs, stream=stream, located=loc, amp=amp, allow_capacity=True), cap)
+    n = np.asarray(sy.shape)
+    idx = np.stack(np.unravel_index(loc[:c].cpu().numpy(), sy.shape), axis=1)
+    hits = 0
+    for f in freqs:
+        d = np.abs(idx - np.rint(f * n).astype(np.int64) % n)
+        hits += int(np.any(np.all(np.minimum(d, n - d) <= 1, axis=1)))
+    for _ in range(3):
+        R.rsft_execute_segments_async(plan, segs, count, stream=stream, located=loc, amp=amp)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(frames):
+        R.rsft_execute_segments_async(plan, segs, count, stream=stream, located=loc, amp=amp)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), ws, dev)
+    plan.close()
+    return {"value": whole_job_rate(ws, frames, ms), "unit": "frames/s", "frames": frames,
+            "ms_per_frame": ms / frames, "bursts_per_frame": SRUR_BURSTS,
+            "hbm_gbs": SRUR_BURSTS * int(np.prod(sy.shape)) * 8 * frames / (ms / 1e3) / 1e9,
+            "pd": hits / len(freqs), "located": int(c),
+            "note": "Table III system, Table IV targets (mixed SNRs), one burst per loop, B = 64x16x8"}
+
+
 MIXED = ("c3_small", "c3_mid", "c3_large")
 MIXED_CAP = 1 << 17
 
@@ -642,6 +686,7 @@ def run_ours(args):
     dense = dense_comparator(R, torch, wl, nv, cubes, targets, stream, dev, ws, max(1, min(args.steps, 200)),
                              max(3, min(args.warmup, 10)), cap, value)
     mixed = mixed_batch(R, torch, ri, dev, ws, stream, n_frames=512 if args.steps >= 100 else 64)
+    srur = srur_frames(R, torch, ri, dev, ws, stream, max(1, min(args.steps // 20, 50)))
     per_pass = per_pass_roofline(R, torch, wl, nv, seed, cubes, stream, peak, max(10, min(args.steps, 400)))
 
     cpu = None
@@ -682,6 +727,7 @@ def run_ours(args):
             "dense_fft": dense,
             "mixed_batch": mixed,
             "segment_mode": seg,
+            "srur": srur,
             "refine": refine,
             "gpu_launches": int(stage[7]) * args.steps,
             "clocks": clocks,

@@ -26,7 +26,8 @@ import numpy as np
 
 __all__ = [
     "Targets", "Workload", "WORKLOADS", "draw_targets", "tone_cube",
-    "workload_frame", "frame_seed",
+    "workload_frame", "frame_seed", "segment_cubes",
+    "SrurSystem", "SrurTarget", "TABLE_IV", "srur_frequencies", "srur_bursts", "srur_amplitudes",
 ]
 
 _CHUNK = 1 << 20  # elements per noise chunk (fixed: part of the cube definition)
@@ -239,4 +240,94 @@ def segment_cubes(shape: Sequence[int], targets: Targets, noise_var: float, seed
         amps = (rng.standard_normal(len(sb2)) + 1j * rng.standard_normal(len(sb2))) * np.sqrt(sb2 / 2.0)
         tg = Targets(targets.freqs, amps, targets.snr_db)
         out.append(tone_cube(shape, tg, noise_var, seed * 1000 + 17 * s + 1))
+    return out
+
+
+# ---------------------------------------------------------------- SRUR radar cubes (§VI)
+
+@dataclasses.dataclass(frozen=True)
+class SrurSystem:
+    """The short-range ubiquitous radar of §VI-B (Table III): an LFMCW waveform de-chirped
+    in analogue and IQ-sampled on every element of a half-wavelength uniform linear array."""
+    range_bins: int = 2048      # R: fast-time samples per repetition interval
+    elements: int = 64          # N: receiving elements
+    ris: int = 32               # M: repetition intervals per burst
+    wavelength: float = 0.03    # lambda (m)
+    c: float = 3.0e8            # propagation speed (m/s)
+    bandwidth: float = 150.0e6  # B_w (Hz)
+    t_p: float = 5.0e-5         # T_p: repetition interval (s)
+    r_max: float = 1.5e3        # maximum range (m)
+    chirp_rate: float = 3.0e12  # rho (Hz/s)
+    f_s: float = 41.0e6         # IQ sampling frequency (Hz)
+
+    @property
+    def shape(self) -> tuple:
+        """Cube layout (range sample, element, repetition interval): the R x N x M data cube."""
+        return (self.range_bins, self.elements, self.ris)
+
+
+@dataclasses.dataclass(frozen=True)
+class SrurTarget:
+    """One point target: range (m), closing velocity (m/s), direction of arrival from the
+    array normal (degrees) and per-sample SNR (dB, the paper's SNR_i of §IV-A)."""
+    range_m: float
+    velocity: float
+    doa_deg: float
+    snr_db: float
+
+
+# Table IV: four targets; targets 3 and 4 differ only by 4 degrees of DOA.  "equal": every
+# target at -10 dB; "mixed": 0, -10, -20, -20 dB.
+TABLE_IV = {
+    "equal": (SrurTarget(1000.0, 100.0, 30.0, -10.0), SrurTarget(500.0, 50.0, 0.0, -10.0),
+              SrurTarget(350.0, 240.0, -16.0, -10.0), SrurTarget(350.0, 240.0, -20.0, -10.0)),
+    "mixed": (SrurTarget(1000.0, 100.0, 30.0, 0.0), SrurTarget(500.0, 50.0, 0.0, -10.0),
+              SrurTarget(350.0, 240.0, -16.0, -20.0), SrurTarget(350.0, 240.0, -20.0, -20.0)),
+}
+
+
+def srur_frequencies(system: SrurSystem, targets: Sequence[SrurTarget]) -> np.ndarray:
+    """K x 3 frequencies in cycles per sample along (range sample, element, RI), in [0, 1).
+
+    Eq. (s_u): the de-chirp leaves the beat frequency f_r = 2 rho r / c in fast time (sampled
+    at f_s) and the Doppler frequency f_d = 2 v / lambda, whose phase advances by f_d T_p per
+    repetition interval; half-wavelength element spacing advances the phase by pi sin(theta)
+    per element, sin(theta) / 2 cycles."""
+    f = np.zeros((len(targets), 3))
+    for k, t in enumerate(targets):
+        f_r = 2.0 * system.chirp_rate * t.range_m / system.c
+        f_d = 2.0 * t.velocity / system.wavelength
+        f[k] = (f_r / system.f_s, 0.5 * math.sin(math.radians(t.doa_deg)), f_d * system.t_p)
+    return f - np.floor(f)
+
+
+def srur_bursts(system: SrurSystem, targets: Sequence[SrurTarget], bursts: int, seed: int,
+                amplitudes: np.ndarray | None = None, noise_var: float = 1.0):
+    """T bursts of the de-chirped array signal of eq. (r_i), as complex64 IQ cubes of
+    ``system.shape``:
+
+        r[tau, i, v] = sum_k a_k(s) exp(j 2 pi (f_r tau / f_s + i sin(theta_k) / 2 + f_d v T_p)) + n,
+
+    n ~ CN(0, noise_var).  Swerling-I amplitudes (§VI-A): a_k(s) ~ CN(0, noise_var 10^(SNR_k/10)),
+    static within burst s and independent between bursts, unless ``amplitudes`` ([T][K]) fixes
+    them.  Returns (cubes, freqs [K][3], amplitudes [T][K]); each burst is one data segment of
+    the segment mode (one loop per burst).  Seeds: (seed, burst) keyed."""
+    freqs = srur_frequencies(system, targets)
+    snr = np.asarray([t.snr_db for t in targets], dtype=np.float64)
+    # a noise-free cube (noise_var = 0) keeps the amplitudes of unit noise
+    amps = (srur_amplitudes(targets, bursts, seed, noise_var if noise_var > 0 else 1.0) if amplitudes is None
+            else np.asarray(amplitudes, dtype=np.complex128))
+    cubes = [tone_cube(system.shape, Targets(freqs, amps[s], snr), noise_var, seed * 1000 + 31 * s + 3)
+             for s in range(bursts)]
+    return cubes, freqs, amps
+
+
+def srur_amplitudes(targets: Sequence[SrurTarget], bursts: int, seed: int, noise_var: float = 1.0) -> np.ndarray:
+    """[T][K] Swerling-I amplitudes: a_k(s) ~ CN(0, noise_var 10^(SNR_k / 10)), one draw per
+    burst (keyed by (seed, burst))."""
+    s2 = noise_var * 10.0 ** (np.asarray([t.snr_db for t in targets], dtype=np.float64) / 10.0)
+    out = np.empty((bursts, len(s2)), dtype=np.complex128)
+    for s in range(bursts):
+        rng = _rng(seed, 11, s)
+        out[s] = (rng.standard_normal(len(s2)) + 1j * rng.standard_normal(len(s2))) * np.sqrt(s2 / 2.0)
     return out
