@@ -1359,6 +1359,15 @@ rsft_status ensure_refine(rsft_plan* p, int64_t k) {
   }
   rsft::RefineWork& w = p->refine;
   if (w.k_cap >= k && w.gres) return RSFT_OK;
+  if (w.gres) {
+    // more tones than before: the smaller per-tone buffers may still be read by queued work
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "rsft_refine (growing the tone buffers)");
+    for (const void* q : {static_cast<const void*>(w.gres), static_cast<const void*>(w.gder),
+                          static_cast<const void*>(w.contr), static_cast<const void*>(w.lm_gh),
+                          static_cast<const void*>(w.lm_freq), static_cast<const void*>(w.lm_amp)})
+      free_alloc(p, q);
+  }
   const int64_t kk = std::max<int64_t>(k, 16);
   rsft_status st;
   const size_t resp = static_cast<size_t>(h.loops) * kk * rg.sumb * sizeof(float2);

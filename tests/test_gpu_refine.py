@@ -156,3 +156,21 @@ def test_refinement_keeps_only_steps_that_lower_the_loss():
         losses.append(_eval(plan, f.cpu().numpy(), a.cpu().numpy())[0])
     assert all(l1 <= l0 for l0, l1 in zip(losses, losses[1:])), losses
     assert losses[-1] < 0.5 * losses[0], losses
+
+
+def test_growing_the_tone_count_on_one_plan():
+    """Evaluations with 2, then 40, then 2 tones on one plan equal those of fresh plans (the
+    per-tone buffers are regrown in between)."""
+    n, b, loops, tf, ta = CASES[2][1:]
+    plan, x, _, f0, a0, _ = _setup(n, b, loops, np.asarray(tf), np.asarray(ta), 0.05, 6, 0.2 / np.asarray(n))
+    rng = np.random.default_rng(2)
+    f40 = rng.uniform(0, 1, (40, 2)).astype(np.float32)
+    a40 = (rng.standard_normal(40) + 1j * rng.standard_normal(40)).astype(np.complex64)
+    first = _eval(plan, f0, a0)
+    many = _eval(plan, f40, a40)
+    again = _eval(plan, f0, a0)
+    for r0, r1 in zip(first, again):
+        np.testing.assert_array_equal(np.asarray(r0), np.asarray(r1))
+    fresh, _, _, _, _, _ = _setup(n, b, loops, np.asarray(tf), np.asarray(ta), 0.05, 6, 0.2 / np.asarray(n))
+    for r0, r1 in zip(many, _eval(fresh, f40, a40)):
+        np.testing.assert_array_equal(np.asarray(r0), np.asarray(r1))
