@@ -21,7 +21,7 @@ LIB = os.path.join(OUT, "librsft.so")
 
 CU_SOURCES = ["capi.cu", "fold.cu", "fold_tc.cu", "spectrum.cu", "votes.cu", "bartlett.cu", "refine.cu"]
 CPP_SOURCES = ["plan_host.cpp"]
-HEADERS = ["device.cuh", "tma.cuh", "plan_host.h"]
+HEADERS = ["device.cuh", "tma.cuh", "plan_host.h", "fold_schedule.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "device.cuh"
+#include "fold_schedule.h"
 #include "plan_host.h"
 #include "rsft.h"
 
@@ -132,87 +133,6 @@ rsft_status upload(rsft_plan* p, T** dst, const std::vector<T>& src) {
 }
 
 float2 to_f2(cplx v) { return make_float2(static_cast<float>(v.real()), static_cast<float>(v.imag())); }
-
-// Choose how the fold splits rows and columns (see fold.cu).  Costs are relative to
-// the 8 bytes each cube element costs: per-element row-weight setup and partial-sum traffic.
-// Scores every fold schedule the kernels support and returns the cheapest; with `all`, also
-// every candidate with its model cost (the autotuner times the best few).
-bool choose_fold_schedule(const rsft::Geometry& g, int sms, rsft::FoldSchedule& out,
-                          std::vector<std::pair<double, rsft::FoldSchedule>>* all = nullptr,
-                          int group = rsft::kMaxLoopGroup) {
-  const int lg = std::min(g.loops, group);
-  double best = 1e300;
-  bool found = false;
-  for (int d_in = 0; d_in < g.ndim; ++d_in) {
-    int64_t row_len = 1, rows_pc = 1, classes = 1, xcount = 1, after = 1;
-    for (int e = d_in; e < g.ndim; ++e) {
-      row_len *= g.n[e];
-      xcount *= g.b[e];
-    }
-    for (int e = d_in + 1; e < g.ndim; ++e) after *= g.n[e];
-    for (int e = 0; e < d_in; ++e) {
-      rows_pc *= g.m[e];
-      classes *= g.b[e];
-    }
-    const int64_t width = std::min<int64_t>(row_len, 2 * rsft::kFoldConsumers);
-    if (width < row_len) {
-      // a chunk must hold whole residue periods: W = w_p * prod_{e > d_in} N_e, B_{d_in} | w_p
-      if (width % after != 0) continue;
-      if ((width / after) % g.b[d_in] != 0) continue;
-    }
-    if (xcount > width || xcount > 65535) continue;
-    if (classes > (int64_t(1) << 30)) continue;
-    // C classes side by side in a step: consecutive residues of the innermost row dimension
-    int64_t cmax = 1;
-    if (d_in >= 1)
-      while (cmax * 2 * width <= 2 * rsft::kFoldConsumers && cmax * 2 <= g.b[d_in - 1] && cmax * 2 <= classes) cmax *= 2;
-    for (int64_t cps = 1; cps <= cmax; cps *= 2) {
-      const int64_t rpc = rows_pc;  // whole classes per unit (direct output unless columns are chunked)
-      const int64_t crow = std::min<int64_t>(2 * rsft::kFoldConsumers / (width * cps), rpc);
-      const int64_t row_chunks = 1;
-      const int64_t col_chunks = row_len / width;
-      const int64_t units = classes / cps * row_chunks * col_chunks;
-      if (units > 0x7fffffff || rpc > (int64_t(1) << 30)) continue;
-      const double setup = static_cast<double>(lg) / static_cast<double>(width * cps * crow / 2);
-      const double partial = (row_chunks * col_chunks > 1)
-                                 ? 2.0 * lg * static_cast<double>(xcount) / static_cast<double>(rpc * width)
-                                 : 0.0;
-      const double idle = 1.0 - static_cast<double>(width * cps * crow) / (2 * rsft::kFoldConsumers);
-      // persistent CTAs (two per SM) take units round robin and each runs at about a fixed
-      // rate: the busiest CTA's units against an even share, plus a per-unit cost (epilogue,
-      // ring refill) worth about 3072 elements of the row loop
-      const double slots = 2.0 * sms;
-      const double per_cta = std::ceil(static_cast<double>(units) / slots);
-      const double balance = std::min(4.0, per_cta / (static_cast<double>(units) / slots) - 1.0) +
-                             3072.0 / static_cast<double>(cps * rpc * width);
-      // rows without a tensor map go as one bulk copy each: small ones are request-rate bound
-      const bool tensor_map = d_in >= 1 && d_in <= 2 && width <= 256;
-      const double copies = (!tensor_map && width < 256) ? 1.0 : 0.0;
-      const double cost = 0.5 * setup + partial + balance + idle + copies;
-      rsft::FoldSchedule c{};
-      c.d_in = d_in;
-      c.row_len = row_len;
-      c.width = static_cast<int>(width);
-      c.col_chunks = static_cast<int>(col_chunks);
-      c.classes = static_cast<int>(classes);
-      c.rows_per_class = static_cast<int>(rows_pc);
-      c.rows_per_chunk = static_cast<int>(rpc);
-      c.row_chunks = static_cast<int>(row_chunks);
-      c.xcount = static_cast<int>(xcount);
-      c.direct = (row_chunks * col_chunks == 1) ? 1 : 0;
-      c.cps = static_cast<int>(cps);
-      c.crow = static_cast<int>(crow);
-      c.groups = static_cast<int>(classes / cps);
-      if (all) all->emplace_back(cost, c);
-      if (cost < best - 1e-9) {
-        best = cost;
-        found = true;
-        out = c;
-      }
-    }
-  }
-  return found;
-}
 
 // Rows of the vote count: the fewest trailing dimensions whose product of N_d reaches a
 // useful row length, bounded by the per-warp shared-memory counters (16 KiB).
@@ -455,78 +375,9 @@ rsft_status apply_fold_schedule(rsft_plan* p) {
   // inner residue of their columns, and the residue digits of each inner residue
   {
     rsft::FoldSchedule& fs = p->fold;
-    auto residue = [&](int64_t c) {  // inner residue index of chunk column c
-      int64_t rem = c, x = 0, xstride = 1;
-      for (int d = D - 1; d >= fs.d_in; --d) {
-        const int64_t sd = rem % h.n[d];
-        rem /= h.n[d];
-        x += (sd % h.b[d]) * xstride;
-        xstride *= h.b[d];
-      }
-      return x;
-    };
-    // element bit e of a row step: a column bit or, past the chunk width, a row bit (the class
-    // of the row for the first log2 C row bits, then its row); does flipping it keep the
-    // thread's (class, inner residue)?
-    auto keeps = [&](int e) {
-      if ((int64_t(1) << e) >= fs.width) return ((int64_t(1) << e) / fs.width) >= fs.cps;
-      int acc = 0;
-      for (int d = D - 1; d >= fs.d_in; --d) {
-        const int ln = ilog2(h.n[d]);
-        if (e < acc + ln) return (e - acc) >= ilog2(h.b[d]);
-        acc += ln;
-      }
-      return true;
-    };
-    // thread -> column pair: thread bits 0-2 stay on pair bits 0-2 (a quarter warp reads 128
-    // contiguous bytes, free of bank conflicts); when a chunk row has more than 32 pairs,
-    // thread bits 3-4 take the lowest pair bits that keep the residue, so the warp shuffle
-    // sums them instead of the epilogue's shared-memory partials
-    int perm[8] = {0, 1, 2, 3, 4, 5, 6, 7};
-    const int pair_bits = ilog2(fs.width / 2);
-    if (pair_bits > 5) {
-      std::vector<int> first, rest;
-      for (int pb = 3; pb < pair_bits; ++pb) (keeps(pb + 1) && first.size() < 2 ? first : rest).push_back(pb);
-      first.insert(first.end(), rest.begin(), rest.end());
-      for (int b = 3; b < pair_bits; ++b) perm[b] = first[b - 3];
-    }
-    fs.lane_perm = 0;
-    for (int b = 0; b < 8; ++b) fs.lane_perm |= static_cast<unsigned>(perm[b]) << (4 * b);
-    // lane bit k moves a thread's pair index by 2^perm[k], its elements by twice that
-    int rmask = 0;
-    for (int k = 0; k < 5; ++k)
-      if (keeps(perm[k] + 1)) rmask |= 1 << k;
-    int nbits = 0;
-    for (int k = 0; k < 5; ++k) nbits += (rmask >> k) & 1;
-    fs.red_mask = rmask;
-    fs.leaders = 32 >> nbits;
-    const int warps = rsft::kFoldConsumers / 32;
-    const int nslots = warps * fs.leaders * 2;
-    const int keys = fs.cps * fs.xcount;  // (class in step, inner residue)
-    if (nslots % keys != 0) return fail(RSFT_ERR_UNSUPPORTED, "fold epilogue: residues not balanced");
-    fs.slots_per_x = nslots / keys;
-    if (nslots > 512 || fs.xcount > 512) return fail(RSFT_ERR_UNSUPPORTED, "fold epilogue: too many residues");
-    std::vector<unsigned short> cols(static_cast<size_t>(nslots)), digits(static_cast<size_t>(fs.xcount) * 4, 0);
-    std::vector<int> fill(keys, 0);
-    for (int w = 0; w < warps; ++w)
-      for (int j = 0; j < fs.leaders; ++j) {
-        int lane = 0, bit = 0;
-        for (int b = 0; b < 5; ++b)
-          if (!((rmask >> b) & 1)) lane |= ((j >> bit++) & 1) << b;
-        for (int c = 0; c < 2; ++c) {
-          const int64_t elem = 2 * static_cast<int64_t>(rsft::fold_pair_of(32 * w + lane, fs.lane_perm)) + c;
-          const int64_t x = ((elem / fs.width) % fs.cps) * fs.xcount + residue(elem & (fs.width - 1));
-          if (fill[x] >= fs.slots_per_x) return fail(RSFT_ERR_UNSUPPORTED, "fold epilogue: residues not balanced");
-          cols[x * fs.slots_per_x + fill[x]++] = static_cast<unsigned short>((w * fs.leaders + j) * 2 + c);
-        }
-      }
-    for (int x = 0; x < fs.xcount; ++x) {
-      int64_t rem = x;
-      for (int d = D - 1; d >= fs.d_in; --d) {
-        digits[x * 4 + (d - fs.d_in)] = static_cast<unsigned short>(rem % h.b[d]);
-        rem /= h.b[d];
-      }
-    }
+    std::vector<unsigned short> cols, digits;
+    if (const char* why = rsft::fold_epilogue_tables(h.n, h.b, D, fs, cols, digits))
+      return fail(RSFT_ERR_UNSUPPORTED, why);
     unsigned short* up = nullptr;
     if ((st = upload(p, &up, cols)) != RSFT_OK) return st;
     p->tables.slots_by_x = up;
@@ -542,7 +393,8 @@ rsft_status apply_fold_schedule(rsft_plan* p) {
     const char* env = std::getenv("RSFT_FOLD");
     p->fold_tc = rsft::fold_tc_supported(g, fs) && env && std::string(env) == "tc";
     p->h_xres.assign(64, 0);
-    for (int c = 0; c < 64 && c < fs.width; ++c) p->h_xres[c] = static_cast<unsigned char>(residue(c));
+    for (int c = 0; c < 64 && c < fs.width; ++c)
+      p->h_xres[c] = static_cast<unsigned char>(rsft::fold_residue(h.n, h.b, D, fs, c));
     p->tables.h_xres = p->h_xres.data();
   }
   if ((st = build_fold_tables(p, p->loop_group, &p->tables.ftable, &p->tables.fcolw)) != RSFT_OK) return st;
@@ -578,7 +430,7 @@ rsft_status build_device(rsft_plan* p) {
     sms = 152;
   }
   p->sms = sms;
-  if (!choose_fold_schedule(g, sms, p->fold))
+  if (!rsft::choose_fold_schedule(g, sms, p->fold))
     return fail(RSFT_ERR_UNSUPPORTED, "no fold schedule for this bucket grid (inner B_d too large)");
   p->rows = rsft::VoteRowSchedule{};
   p->rows_mode = h.desc.vote_mode == RSFT_VOTES_ROWS && choose_vote_rows(g, p->rows) &&
@@ -1485,7 +1337,7 @@ rsft_status rsft_plan_autotune(rsft_plan* plan, const void* d_cube, void* stream
   if (!guard.ok) return fail(RSFT_ERR_CUDA, "cudaSetDevice failed");
   std::vector<std::pair<double, rsft::FoldSchedule>> all;
   rsft::FoldSchedule model{};
-  if (!choose_fold_schedule(plan->geom, plan->sms, model, &all, plan->loop_group))
+  if (!rsft::choose_fold_schedule(plan->geom, plan->sms, model, &all, plan->loop_group))
     return fail(RSFT_ERR_UNSUPPORTED, "no fold schedule");
   std::stable_sort(all.begin(), all.end(),
                    [](const std::pair<double, rsft::FoldSchedule>& a, const std::pair<double, rsft::FoldSchedule>& b) {
