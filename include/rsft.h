@@ -419,6 +419,18 @@ rsft_status rsft_bartlett_get(const rsft_bartlett_plan* plan, int32_t what, void
 /* Copies the last execute's spectrum (N complex64, row-major) to d_out. */
 rsft_status rsft_bartlett_copy_spectrum(const rsft_bartlett_plan* plan, void* d_out, void* stream);
 
+/*
+ * Check of the bounded device waits (the paper has no counterpart).  Every wait of the
+ * library's kernels on a barrier gives up after a time limit, sets an error flag and lets
+ * its kernel return (see Errors above).  This call runs one CTA that waits, through the same
+ * device routine as the fold, on a barrier that nothing ever completes, with a limit of
+ * limit_ms milliseconds (1..1000).  It returns RSFT_ERR_TIMEOUT when the wait gave up and
+ * reported it -- the expected result -- and leaves the device context usable.
+ * Synchronous on `stream` (current device).  Errors: INVALID_ARG (limit out of range), OOM,
+ * CUDA; RSFT_OK would mean the wait did not report giving up.
+ */
+rsft_status rsft_check_wait_timeout(int32_t limit_ms, void* stream);
+
 /* Static description of a status code (never NULL). */
 const char* rsft_status_string(rsft_status status);
 

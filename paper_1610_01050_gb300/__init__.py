@@ -48,7 +48,7 @@ C_SYMBOLS = (
     "rsft_execute_segments_async", "rsft_bartlett_plan_create", "rsft_bartlett_plan_destroy", "rsft_bartlett_execute",
     "rsft_bartlett_execute_async", "rsft_bartlett_get", "rsft_bartlett_copy_spectrum",
     "rsft_graph_create", "rsft_graph_launch", "rsft_graph_launch_batch", "rsft_graph_destroy", "rsft_plan_autotune",
-    "rsft_plan_set_loops_per_pass",
+    "rsft_plan_set_loops_per_pass", "rsft_check_wait_timeout",
 )
 RSFT_BARTLETT_GAMMA, RSFT_BARTLETT_GAIN, RSFT_BARTLETT_WINDOW, RSFT_BARTLETT_WORKSPACE_BYTES = 1, 2, 3, 4
 
@@ -125,6 +125,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rsft_plan_autotune.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_int32, POINTER(ctypes.c_double),
                                        POINTER(c_int32)]
     lib.rsft_plan_set_loops_per_pass.argtypes = [c_void_p, c_int32]
+    lib.rsft_check_wait_timeout.argtypes = [c_int32, c_void_p]
+    lib.rsft_check_wait_timeout.restype = c_int32
     lib.rsft_status_string.argtypes = [c_int32]
     lib.rsft_status_string.restype = c_char_p
     lib.rsft_last_error.argtypes = []
@@ -377,6 +379,11 @@ def rsft_stage2_static(votes, n, mu, located, count, located_votes=None, capacit
     cap = int(located.numel()) if capacity is None else int(capacity)
     _check(load_library().rsft_stage2_static(_ptr(votes), int(n), int(mu), _ptr(located), _ptr(located_votes),
                                              cap, _ptr(count), _stream(stream)))
+
+
+def rsft_check_wait_timeout(limit_ms: int = 20, stream=None) -> int:
+    """Run the bounded-wait check; returns the status (RSFT_ERR_TIMEOUT is the expected one)."""
+    return int(load_library().rsft_check_wait_timeout(int(limit_ms), _stream(stream)))
 
 
 def rsft_status_string(status: int) -> str:

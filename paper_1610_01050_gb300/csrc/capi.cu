@@ -1512,6 +1512,26 @@ void rsft_graph_destroy(rsft_graph* graph) {
   delete graph;
 }
 
+rsft_status rsft_check_wait_timeout(int32_t limit_ms, void* stream) {
+  if (limit_ms < 1 || limit_ms > 1000) return fail(RSFT_ERR_INVALID_ARG, "limit_ms must be 1..1000");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* d_err = nullptr;
+  cudaError_t e = cudaMalloc(&d_err, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? RSFT_ERR_OOM : RSFT_ERR_CUDA, "cudaMalloc failed");
+  }
+  int h_err = 0;
+  e = cudaMemsetAsync(d_err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = rsft::launch_wait_selftest(d_err, static_cast<uint64_t>(limit_ms) * 1000000ull, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_err);
+  if (e != cudaSuccess) return cuda_fail(e, "rsft_check_wait_timeout");
+  if (h_err != 1) return RSFT_OK;
+  return fail(RSFT_ERR_TIMEOUT, "the bounded wait gave up, as intended");
+}
+
 const char* rsft_status_string(rsft_status s) {
   switch (s) {
     case RSFT_OK: return "ok";

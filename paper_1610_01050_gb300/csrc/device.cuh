@@ -195,6 +195,9 @@ cudaError_t vote_rows_small_residency(const Geometry& g, const VoteRowSchedule& 
                                       int* warps_per_sm);
 
 int fold_smem_bytes(const Geometry& g, const FoldSchedule& fs, int lg);
+// One CTA waits on a barrier that never completes, through the fold's bounded wait with the
+// given limit; *err is set to 1 when the wait gives up.
+cudaError_t launch_wait_selftest(int* err, uint64_t limit_ns, cudaStream_t stream);
 
 // Tensor-core fold (fold_tc.cu): schedules with 64-column chunks, two or more classes side
 // by side, whole classes, rows in stages of 16.

@@ -461,7 +461,27 @@ cudaError_t launch_fold_lg(const FoldArgs& args, int smem, cudaStream_t stream) 
   return cudaGetLastError();
 }
 
+// One CTA waits, through the fold's bounded barrier wait, on a barrier that nothing
+// arrives on: the wait gives up after limit_ns and reports it the way the fold does (the CTA's
+// abort flag, then *err = 1).  No copy is in flight and no tensor memory is held.
+__global__ void wait_selftest_kernel(int* err, uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    mbar_init_fence();
+  }
+  __syncthreads();
+  mbar_wait(&bar, 0u, &abort_flag, err, limit_ns);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(int* err, uint64_t limit_ns, cudaStream_t stream) {
+  wait_selftest_kernel<<<1, 32, 0, stream>>>(err, limit_ns);
+  return cudaGetLastError();
+}
 
 int fold_smem_bytes(const Geometry& g, const FoldSchedule& fs, int lg) {
   (void)g;

@@ -187,3 +187,8 @@ def test_loops_per_pass_checks_arguments():
     assert lib.rsft_plan_set_loops_per_pass(None, 4) == R.RSFT_ERR_INVALID_ARG
     plan = R.rsft_plan_create(R.make_desc((64, 64), (8, 8), 4, device=-1, p_fa1=0.05, mu=1))
     assert lib.rsft_plan_set_loops_per_pass(plan.handle, 4) == R.RSFT_ERR_INVALID_ARG  # host-only plan
+
+
+def test_wait_check_rejects_limits_out_of_range():
+    assert R.rsft_check_wait_timeout(0) == R.RSFT_ERR_INVALID_ARG
+    assert R.rsft_check_wait_timeout(1001) == R.RSFT_ERR_INVALID_ARG
