@@ -159,6 +159,41 @@ def _ptr(x):
     raise TypeError(f"cannot take a pointer of {type(x)}")
 
 
+def _dptr(x, what):
+    """Device pointer of a CUDA tensor (None -> NULL; an int is taken as a device address).
+    Host memory is refused here: the kernels would read it as device memory."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return c_void_p(x)
+    if hasattr(x, "is_cuda") and x.is_cuda:
+        return c_void_p(x.data_ptr())
+    kind = "a CPU tensor" if hasattr(x, "is_cuda") else type(x).__name__
+    raise TypeError(f"{what} must be a CUDA tensor (device memory), not {kind}")
+
+
+def _hptr(x, what):
+    """Host pointer of a numpy array or CPU tensor (None -> NULL; an int is taken as a host address)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return c_void_p(x)
+    if isinstance(x, np.ndarray):
+        return c_void_p(x.ctypes.data)
+    if hasattr(x, "is_cuda") and not x.is_cuda:
+        return c_void_p(x.data_ptr())
+    kind = "a CUDA tensor" if hasattr(x, "is_cuda") else type(x).__name__
+    raise TypeError(f"{what} must be host memory (a numpy array or CPU tensor), not {kind}")
+
+
+def _dptr_array(xs, what):
+    return (c_void_p * max(1, len(xs)))(*[_dptr(x, what).value for x in xs])
+
+
+def _hptr_array(xs, what):
+    return (c_void_p * max(1, len(xs)))(*[_hptr(x, what).value for x in xs])
+
+
 def _stream(stream):
     if stream is None:
         try:
@@ -259,8 +294,9 @@ def rsft_execute(plan: Plan, cube, stream=None, located=None, located_votes=None
                  votes_out=None, allow_capacity=False) -> int:
     """Run the hot path on a device cube; returns the number of located frequencies."""
     n = c_int64(0)
-    st = load_library().rsft_execute(plan.handle, _ptr(cube), _stream(stream), _ptr(located),
-                                     _ptr(located_votes), _ptr(amp), _ptr(votes_out), ctypes.byref(n))
+    st = load_library().rsft_execute(plan.handle, _dptr(cube, "cube"), _stream(stream), _dptr(located, "located"),
+                                     _dptr(located_votes, "located_votes"), _dptr(amp, "amp"),
+                                     _dptr(votes_out, "votes_out"), ctypes.byref(n))
     _check(st, allow=(RSFT_ERR_CAPACITY,) if allow_capacity else ())
     return int(n.value)
 
@@ -268,14 +304,17 @@ def rsft_execute(plan: Plan, cube, stream=None, located=None, located_votes=None
 def rsft_execute_async(plan: Plan, cube, count, stream=None, located=None, located_votes=None, amp=None,
                        votes_out=None) -> None:
     """Stream-ordered run; the located count lands in the device int64 tensor ``count``."""
-    _check(load_library().rsft_execute_async(plan.handle, _ptr(cube), _stream(stream), _ptr(located),
-                                             _ptr(located_votes), _ptr(amp), _ptr(votes_out), _ptr(count)))
+    _check(load_library().rsft_execute_async(plan.handle, _dptr(cube, "cube"), _stream(stream),
+                                             _dptr(located, "located"), _dptr(located_votes, "located_votes"),
+                                             _dptr(amp, "amp"), _dptr(votes_out, "votes_out"),
+                                             _dptr(count, "count")))
 
 
 def rsft_execute_host(plan: Plan, h_cube, located, amp=None, stream=None, allow_capacity=False) -> int:
     """End-to-end run on host buffers (numpy or CPU torch; pinned memory recommended)."""
     n = c_int64(0)
-    st = load_library().rsft_execute_host(plan.handle, _ptr(h_cube), _stream(stream), _ptr(located), _ptr(amp),
+    st = load_library().rsft_execute_host(plan.handle, _hptr(h_cube, "h_cube"), _stream(stream),
+                                          _hptr(located, "located"), _hptr(amp, "amp"),
                                           ctypes.byref(n))
     _check(st, allow=(RSFT_ERR_CAPACITY,) if allow_capacity else ())
     return int(n.value)
@@ -300,30 +339,34 @@ def rsft_execute_segments(plan: Plan, segments, stream=None, located=None, locat
                           votes_out=None, allow_capacity=False) -> int:
     """Segment mode: loop l folds segments[l] (one device cube per loop); returns the count."""
     n = c_int64(0)
-    st = load_library().rsft_execute_segments(plan.handle, _ptr_array(segments), _stream(stream), _ptr(located),
-                                              _ptr(located_votes), _ptr(amp), _ptr(votes_out), ctypes.byref(n))
+    st = load_library().rsft_execute_segments(plan.handle, _dptr_array(segments, "segments"), _stream(stream),
+                                              _dptr(located, "located"), _dptr(located_votes, "located_votes"),
+                                              _dptr(amp, "amp"), _dptr(votes_out, "votes_out"), ctypes.byref(n))
     _check(st, allow=(RSFT_ERR_CAPACITY,) if allow_capacity else ())
     return int(n.value)
 
 
 def rsft_execute_segments_async(plan: Plan, segments, count, stream=None, located=None, located_votes=None,
                                 amp=None, votes_out=None) -> None:
-    _check(load_library().rsft_execute_segments_async(plan.handle, _ptr_array(segments), _stream(stream),
-                                                      _ptr(located), _ptr(located_votes), _ptr(amp),
-                                                      _ptr(votes_out), _ptr(count)))
+    _check(load_library().rsft_execute_segments_async(plan.handle, _dptr_array(segments, "segments"),
+                                                      _stream(stream), _dptr(located, "located"),
+                                                      _dptr(located_votes, "located_votes"), _dptr(amp, "amp"),
+                                                      _dptr(votes_out, "votes_out"), _dptr(count, "count")))
 
 
 def rsft_execute_batch(plan: Plan, cubes, counts, lanes: int = 2, located=None, amp=None, stream=None) -> None:
     """Stream-ordered batch of device cubes over `lanes` lanes; frame f's count lands in
     counts[f], its located list in located[f * max_located:], its amplitudes likewise."""
-    _check(load_library().rsft_execute_batch(plan.handle, _ptr_array(cubes), len(cubes), lanes, _stream(stream),
-                                             _ptr(located), _ptr(amp), _ptr(counts)))
+    _check(load_library().rsft_execute_batch(plan.handle, _dptr_array(cubes, "cubes"), len(cubes), lanes,
+                                             _stream(stream), _dptr(located, "located"), _dptr(amp, "amp"),
+                                             _dptr(counts, "counts")))
 
 
 def rsft_execute_host_batch(plan: Plan, h_cubes, located, counts, amp=None, stream=None, allow_capacity=False) -> None:
     """Host cubes in, host results out (counts[f], located[f * max_located:], amp likewise)."""
-    st = load_library().rsft_execute_host_batch(plan.handle, _ptr_array(h_cubes), len(h_cubes), _stream(stream),
-                                                _ptr(located), _ptr(amp), _ptr(counts))
+    st = load_library().rsft_execute_host_batch(plan.handle, _hptr_array(h_cubes, "h_cubes"), len(h_cubes),
+                                                _stream(stream), _hptr(located, "located"), _hptr(amp, "amp"),
+                                                _hptr(counts, "counts"))
     _check(st, allow=(RSFT_ERR_CAPACITY,) if allow_capacity else ())
 
 
@@ -345,23 +388,24 @@ def rsft_plan_timing(plan: Plan, enable: bool) -> None:
 
 
 def rsft_copy_buckets(plan: Plan, which: int, out, stream=None) -> None:
-    _check(load_library().rsft_copy_buckets(plan.handle, int(which), _ptr(out), _stream(stream)))
+    _check(load_library().rsft_copy_buckets(plan.handle, int(which), _dptr(out, "out"), _stream(stream)))
 
 
 def rsft_copy_detections(plan: Plan, out, stream=None) -> None:
-    _check(load_library().rsft_copy_detections(plan.handle, _ptr(out), _stream(stream)))
+    _check(load_library().rsft_copy_detections(plan.handle, _dptr(out, "out"), _stream(stream)))
 
 
 def rsft_refine(plan: Plan, cube, k, freq, amp, steps, lr, stream=None) -> None:
     """Fold the cube, then `steps` Levenberg-Marquardt updates of the K tones in place
     (freq: device float32 [K, D] cycles/sample, amp: device complex64 [K])."""
-    _check(load_library().rsft_refine(plan.handle, _ptr(cube), int(k), _ptr(freq), _ptr(amp), int(steps),
+    _check(load_library().rsft_refine(plan.handle, _dptr(cube, "cube"), int(k), _dptr(freq, "freq"),
+                                      _dptr(amp, "amp"), int(steps),
                                       ctypes.c_float(lr), _stream(stream)))
 
 
 def rsft_refine_prepare(plan: Plan, cube, stream=None) -> None:
     """Fold the cube into the plan's buckets (the data side of the refinement loss)."""
-    _check(load_library().rsft_refine_prepare(plan.handle, _ptr(cube), _stream(stream)))
+    _check(load_library().rsft_refine_prepare(plan.handle, _dptr(cube, "cube"), _stream(stream)))
 
 
 def rsft_refine_eval(plan: Plan, freq, amp, loss=None, grad_freq=None, grad_amp=None, hdiag=None,
@@ -369,16 +413,18 @@ def rsft_refine_eval(plan: Plan, freq, amp, loss=None, grad_freq=None, grad_amp=
     """Loss (device float64 [1]), gradients (float32 [K, D], complex64 [K] holding (dE/da_re,
     dE/da_im)) and Gauss-Newton diagonal (float32 [K, D + 1]) of the tones."""
     k = int(amp.shape[0])
-    _check(load_library().rsft_refine_eval(plan.handle, k, _ptr(freq), _ptr(amp), _ptr(loss), _ptr(grad_freq),
-                                           _ptr(grad_amp), _ptr(hdiag), _stream(stream)))
+    _check(load_library().rsft_refine_eval(plan.handle, k, _dptr(freq, "freq"), _dptr(amp, "amp"),
+                                           _dptr(loss, "loss"), _dptr(grad_freq, "grad_freq"),
+                                           _dptr(grad_amp, "grad_amp"), _dptr(hdiag, "hdiag"), _stream(stream)))
 
 
 def rsft_stage2_static(votes, n, mu, located, count, located_votes=None, capacity=None, stream=None) -> None:
     """Second-stage compaction into caller buffers, with library-owned fixed scratch
     (no device allocation); ``votes`` is cleared.  See include/rsft.h."""
     cap = int(located.numel()) if capacity is None else int(capacity)
-    _check(load_library().rsft_stage2_static(_ptr(votes), int(n), int(mu), _ptr(located), _ptr(located_votes),
-                                             cap, _ptr(count), _stream(stream)))
+    _check(load_library().rsft_stage2_static(_dptr(votes, "votes"), int(n), int(mu), _dptr(located, "located"),
+                                             _dptr(located_votes, "located_votes"), cap, _dptr(count, "count"),
+                                             _stream(stream)))
 
 
 def rsft_check_wait_timeout(limit_ms: int = 20, stream=None) -> int:
@@ -421,7 +467,8 @@ class Graph:
 def rsft_graph_create(plan: Plan, cube, count, located=None, amp=None, lane: int = 0) -> Graph:
     """Record one execute of `plan` on `cube` (results to located / amp / count) on `lane`."""
     h = c_void_p()
-    _check(load_library().rsft_graph_create(plan.handle, _ptr(cube), int(lane), _ptr(located), _ptr(amp), _ptr(count),
+    _check(load_library().rsft_graph_create(plan.handle, _dptr(cube, "cube"), int(lane), _dptr(located, "located"),
+                                            _dptr(amp, "amp"), _dptr(count, "count"),
                                             ctypes.byref(h)))
     return Graph(h, plan, (cube, count, located, amp))
 
@@ -437,7 +484,8 @@ def rsft_plan_autotune(plan: Plan, cube, candidates: int = 4, reps: int = 10, st
     Returns (microseconds per fold launch of the winner, its rank among the candidates)."""
     us = ctypes.c_double(0.0)
     chosen = c_int32(-1)
-    _check(load_library().rsft_plan_autotune(plan.handle, _ptr(cube), _stream(stream), int(candidates), int(reps),
+    _check(load_library().rsft_plan_autotune(plan.handle, _dptr(cube, "cube"), _stream(stream), int(candidates),
+                                             int(reps),
                                              ctypes.byref(us), ctypes.byref(chosen)))
     return float(us.value), int(chosen.value)
 
@@ -483,15 +531,17 @@ def rsft_bartlett_plan_destroy(plan: BartlettPlan) -> None:
 def rsft_bartlett_execute(plan: BartlettPlan, cube, located=None, amp=None, stream=None, allow_capacity=False) -> int:
     """Dense detection of a device cube; returns the number of detected bins."""
     n = c_int64(0)
-    st = load_library().rsft_bartlett_execute(plan.handle, _ptr(cube), _stream(stream), _ptr(located), _ptr(amp),
+    st = load_library().rsft_bartlett_execute(plan.handle, _dptr(cube, "cube"), _stream(stream),
+                                              _dptr(located, "located"), _dptr(amp, "amp"),
                                               ctypes.byref(n))
     _check(st, allow=(RSFT_ERR_CAPACITY,) if allow_capacity else ())
     return int(n.value)
 
 
 def rsft_bartlett_execute_async(plan: BartlettPlan, cube, count, located=None, amp=None, stream=None) -> None:
-    _check(load_library().rsft_bartlett_execute_async(plan.handle, _ptr(cube), _stream(stream), _ptr(located),
-                                                      _ptr(amp), _ptr(count)))
+    _check(load_library().rsft_bartlett_execute_async(plan.handle, _dptr(cube, "cube"), _stream(stream),
+                                                      _dptr(located, "located"), _dptr(amp, "amp"),
+                                                      _dptr(count, "count")))
 
 
 def rsft_bartlett_get(plan: BartlettPlan, what: int):
@@ -506,4 +556,4 @@ def rsft_bartlett_get(plan: BartlettPlan, what: int):
 
 
 def rsft_bartlett_copy_spectrum(plan: BartlettPlan, out, stream=None) -> None:
-    _check(load_library().rsft_bartlett_copy_spectrum(plan.handle, _ptr(out), _stream(stream)))
+    _check(load_library().rsft_bartlett_copy_spectrum(plan.handle, _dptr(out, "out"), _stream(stream)))

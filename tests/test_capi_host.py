@@ -124,7 +124,7 @@ def test_host_plan_cannot_execute(lib):
     p = R.rsft_plan_create(R.make_desc((32, 64), (4, 8), 3, p_fa1=0.01, mu=1, device=-1))
     cube = np.zeros((32, 64), dtype=np.complex64)
     with pytest.raises(R.RsftError) as ei:
-        R.rsft_execute(p, cube)
+        R.rsft_execute(p, cube.ctypes.data)   # an address: the plan refuses before any device access
     assert ei.value.status == R.RSFT_ERR_INVALID_ARG
 
 
@@ -165,8 +165,8 @@ def test_graphs_and_autotune_need_a_device_plan():
     cube = np.zeros(64 * 64, np.complex64)
     count = np.zeros(1, np.int64)
     located = np.zeros(8, np.int64)
-    for call in (lambda: R.rsft_graph_create(plan, cube, count, located),
-                 lambda: R.rsft_plan_autotune(plan, cube)):
+    for call in (lambda: R.rsft_graph_create(plan, cube.ctypes.data, count.ctypes.data, located.ctypes.data),
+                 lambda: R.rsft_plan_autotune(plan, cube.ctypes.data)):
         with pytest.raises(R.RsftError) as ei:
             call()
         assert ei.value.status == R.RSFT_ERR_INVALID_ARG
@@ -192,3 +192,40 @@ def test_loops_per_pass_checks_arguments():
 def test_wait_check_rejects_limits_out_of_range():
     assert R.rsft_check_wait_timeout(0) == R.RSFT_ERR_INVALID_ARG
     assert R.rsft_check_wait_timeout(1001) == R.RSFT_ERR_INVALID_ARG
+
+
+class _FakeTensor:
+    """Stands for a torch tensor on the given side (only the attributes the binding reads)."""
+
+    def __init__(self, cuda):
+        self.is_cuda = cuda
+        self.shape = (4,)
+
+    def data_ptr(self):
+        return 1 << 40
+
+
+def test_binding_refuses_memory_of_the_wrong_side():
+    """Device arguments must be CUDA tensors (or raw addresses) and host arguments host memory:
+    the binding raises TypeError before the library sees a pointer of the wrong kind."""
+    import torch
+    plan = R.rsft_plan_create(R.make_desc((64, 64), (8, 8), 4, device=-1, p_fa1=0.05, mu=1))
+    host_np, host_t, dev = np.zeros(64 * 64, np.complex64), torch.zeros(64 * 64, dtype=torch.complex64), _FakeTensor(True)
+    for bad in (host_np, host_t, _FakeTensor(False)):
+        for call in (lambda: R.rsft_execute(plan, bad),
+                     lambda: R.rsft_execute_async(plan, bad, None),
+                     lambda: R.rsft_execute_segments(plan, [bad]),
+                     lambda: R.rsft_execute_batch(plan, [bad], None),
+                     lambda: R.rsft_copy_buckets(plan, R.RSFT_BUCKETS_FOLDED, bad),
+                     lambda: R.rsft_copy_detections(plan, bad),
+                     lambda: R.rsft_refine_prepare(plan, bad),
+                     lambda: R.rsft_refine_eval(plan, bad, host_t[:4]),
+                     lambda: R.rsft_stage2_static(bad, 16384, 1, None, None, capacity=8),
+                     lambda: R.rsft_graph_create(plan, bad, None),
+                     lambda: R.rsft_plan_autotune(plan, bad)):
+            with pytest.raises(TypeError, match="CUDA tensor"):
+                call()
+    with pytest.raises(TypeError, match="host memory"):
+        R.rsft_execute_host(plan, dev, np.zeros(8, np.uint64))
+    with pytest.raises(TypeError, match="host memory"):
+        R.rsft_execute_host_batch(plan, [host_np], dev, np.zeros(1, np.int64))
