@@ -28,9 +28,11 @@
  *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
  *    default stream).  Calls are stream-ordered unless stated otherwise.
  *  - Threads: a plan (its workspaces, lanes, events and the graphs recorded
- *    on it) is used by one host thread at a time; calls that share a plan
- *    from several threads must be serialised by the caller.  Different plans
- *    are independent.
+ *    on it) is used by one host thread at a time.  The kernels' launch
+ *    attributes (dynamic shared-memory limits, cached occupancies) are
+ *    process-wide and set without a lock, so calls from several host threads
+ *    must be serialised by the caller, whether or not they share a plan;
+ *    plans do not otherwise share state.
  *  - Errors: every call returns an rsft_status; on failure nothing is
  *    guaranteed about the outputs and rsft_last_error() holds a message.
  *    The library never traps and never falls back to the CPU: without a
