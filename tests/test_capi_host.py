@@ -38,6 +38,7 @@ CASES = [
     dict(n=(1024, 256, 64), b=(64, 32, 8), loops=12, atten=80.0, flat="cheb", support=None, k=32, pfa=1e-6),
     dict(n=(64, 32, 16, 8), b=(8, 4, 2, 2), loops=16, atten=60.0, flat="ideal", support=None, k=2, pfa=1e-5),
     dict(n=(4096,), b=(64,), loops=5, atten=45.0, flat="cheb", support=(512,), k=3, pfa=1e-6),
+    dict(n=(64, 64), b=(8, 8), loops=255, atten=60.0, flat="cheb", support=None, k=2, pfa=1e-6),  # largest L
 ]
 
 

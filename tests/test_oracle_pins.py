@@ -230,7 +230,8 @@ def _exact_case(n, b, loops, k, seed):
 
 
 @pytest.mark.parametrize("n,b,loops,k", [((64, 32), (8, 8), 6, 4), ((32, 16, 8), (4, 4, 2), 5, 3),
-                                         ((256,), (16,), 7, 3)])
+                                         ((256,), (16,), 7, 3),
+                                         ((32, 16), (4, 4), 255, 2)])   # the largest L: 255 votes, mu = 254
 def test_exact_recovery_noise_free(n, b, loops, k):
     x, tg = _exact_case(n, b, loops, k, 17)
     tiny = 1e-6 * np.min(np.abs(tg.amps)) ** 2
