@@ -717,7 +717,10 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "kernel": "permute_window_fold (" + ("fold_tc_kernel: tcgen05 3xTF32"
                          if tensor_fold else "fold_kernel: SIMT FP32") + ")", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_kind} (copy bandwidth)",
-                         "traffic": traffic, "algorithmic_bytes_per_launch": fold_bytes},
+                         "traffic": traffic, "algorithmic_bytes_per_launch": fold_bytes,
+                         "dram_gbs": traffic / fold_s / 1e9 if traffic else None,
+                         "dram_note": "ncu DRAM bytes of one launch (traffic) over the same launch time: the "
+                                      "sector-level rate, beside the useful-byte rate (achieved)"},
             "roofline_per_pass": per_pass,
             "e2e": {"value": e2e_val, "unit": "frames/s", "h2d_bytes_per_step": int(np.prod(wl.shape)) * 8,
                     "d2h_bytes_per_step": int(d2h / e2e_steps)},
