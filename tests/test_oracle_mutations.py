@@ -14,6 +14,7 @@ import oracle.pipeline as orsft
 import oracle.windows as owin
 import oracle.design as odes
 import tests.test_oracle_pins as pins
+import tests.test_oracle_refine as rpins
 
 
 def _perm_inverse(y, sigma_row):
@@ -61,6 +62,27 @@ def _mapping_off_by_one(plan, l, i):
 
 _ORIG_FLAT = owin.flat_window
 _ORIG_EST = orsft.estimate_amplitudes
+_ORIG_GRAD = O.refine_grad
+_ORIG_FIELD = O.tone_field
+
+
+def _grad_no_j(plan, cube, freqs, amps):          # dE/da_im taken along the real direction
+    gf, gre, _ = _ORIG_GRAD(plan, cube, freqs, amps)
+    return gf, gre, gre
+
+
+def _grad_freq_sign(plan, cube, freqs, amps):     # exp(-j 2 pi f t) differentiated as exp(+j ...)
+    gf, gre, gim = _ORIG_GRAD(plan, cube, freqs, amps)
+    return -gf, gre, gim
+
+
+def _grad_dims_swapped(plan, cube, freqs, amps):  # frequency gradient of the wrong dimension
+    gf, gre, gim = _ORIG_GRAD(plan, cube, freqs, amps)
+    return gf[:, ::-1], gre, gim
+
+
+def _field_conj(shape, freqs, amps):              # tones synthesised with the conjugate phase
+    return _ORIG_FIELD(shape, -np.asarray(freqs), amps)
 
 CASES = [
     ("permute with sigma^-1", [(orsft, "permute", _perm_inverse), (O, "permute", _perm_inverse)],
@@ -78,6 +100,14 @@ CASES = [
      lambda: pins.test_exact_recovery_noise_free((64, 32), (8, 8), 6, 4)),
     ("mapping off by one", [(orsft, "mapping", _mapping_off_by_one), (O, "mapping", _mapping_off_by_one)],
      lambda: pins.test_reversibility_and_distinctiveness_exhaustive(16)),
+    ("refinement: amplitude gradient without j", [(O, "refine_grad", _grad_no_j)],
+     lambda: rpins.test_gradient_matches_central_differences()),
+    ("refinement: frequency gradient with the wrong sign", [(O, "refine_grad", _grad_freq_sign)],
+     lambda: rpins.test_gradient_matches_central_differences()),
+    ("refinement: frequency gradient of the other dimension", [(O, "refine_grad", _grad_dims_swapped)],
+     lambda: rpins.test_gradient_matches_central_differences()),
+    ("refinement: tones with the conjugate phase", [(O, "tone_field", _field_conj)],
+     lambda: rpins.test_tone_field_is_the_sum_of_exponentials()),
 ]
 
 
