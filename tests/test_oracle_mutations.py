@@ -4,6 +4,7 @@ Each case swaps one oracle function for a subtly wrong version (a transposed
 operand, a dropped term, a wrong sign or index) and runs the pin that must
 catch it.  This shows the pins are sharp enough to notice such slips.
 """
+import importlib
 import math
 
 import numpy as np
@@ -15,6 +16,7 @@ import oracle.windows as owin
 import oracle.design as odes
 import tests.test_oracle_pins as pins
 import tests.test_oracle_refine as rpins
+import tests.test_oracle_bartlett as bpins
 
 
 def _perm_inverse(y, sigma_row):
@@ -64,6 +66,9 @@ _ORIG_FLAT = owin.flat_window
 _ORIG_EST = orsft.estimate_amplitudes
 _ORIG_GRAD = O.refine_grad
 _ORIG_FIELD = O.tone_field
+_ORIG_BARTLETT = O.bartlett
+# the package re-exports the function bartlett under the module's own name: reach the module itself
+obart = importlib.import_module("oracle.bartlett")
 
 
 def _grad_no_j(plan, cube, freqs, amps):          # dE/da_im taken along the real direction
@@ -83,6 +88,20 @@ def _grad_dims_swapped(plan, cube, freqs, amps):  # frequency gradient of the wr
 
 def _field_conj(shape, freqs, amps):              # tones synthesised with the conjugate phase
     return _ORIG_FIELD(shape, -np.asarray(freqs), amps)
+
+
+def _gamma_no_square(ws, noise_var, p_fa):        # ||w||_1 in place of ||w||_2^2
+    energy = 1.0
+    for w in ws:
+        energy *= float(np.sum(np.abs(w)))
+    return -noise_var * energy * math.log(p_fa)
+
+
+def _dense_gain_squared(*args, **kwargs):         # amplitudes over (sum w)^2 instead of sum w
+    out = _ORIG_BARTLETT(*args, **kwargs)
+    gain = math.prod(float(np.sum(w)) for w in out["windows"])
+    out["amplitudes"] = out["amplitudes"] / gain
+    return out
 
 CASES = [
     ("permute with sigma^-1", [(orsft, "permute", _perm_inverse), (O, "permute", _perm_inverse)],
@@ -108,6 +127,10 @@ CASES = [
      lambda: rpins.test_gradient_matches_central_differences()),
     ("refinement: tones with the conjugate phase", [(O, "tone_field", _field_conj)],
      lambda: rpins.test_tone_field_is_the_sum_of_exponentials()),
+    ("dense detector: threshold without the square", [(obart, "bartlett_gamma", _gamma_no_square)],
+     lambda: bpins.test_noise_only_power_is_exponential_and_pfa_holds()),
+    ("dense detector: amplitude over the squared gain", [(O, "bartlett", _dense_gain_squared)],
+     lambda: bpins.test_exact_recovery_of_on_grid_tones()),
 ]
 
 
