@@ -680,14 +680,26 @@ def run_ours(args):
     for g_ in graphs:
         g_.close()
     bplan.close()
-    refine = refinement(R, torch, plan, wl, cubes, targets, stream, cap)
-    seg = segment_mode(R, torch, plan, wl, cubes, stream, dev, ws, located, amp, count,
-                       max(1, min(args.steps // 20, 50)))
-    dense = dense_comparator(R, torch, wl, nv, cubes, targets, stream, dev, ws, max(1, min(args.steps, 200)),
-                             max(3, min(args.warmup, 10)), cap, value)
-    mixed = mixed_batch(R, torch, ri, dev, ws, stream, n_frames=512 if args.steps >= 100 else 64)
-    srur = srur_frames(R, torch, ri, dev, ws, stream, max(1, min(args.steps // 20, 50)))
-    per_pass = per_pass_roofline(R, torch, wl, nv, seed, cubes, stream, peak, max(10, min(args.steps, 400)))
+    def side(fn):
+        """A secondary measurement: on one GPU a failure is recorded in its own field and the
+        line still prints; with several ranks it propagates (a rank that skipped a collective
+        would leave the others waiting)."""
+        if ws > 1:
+            return fn()
+        try:
+            return fn()
+        except Exception as e:  # recorded, not hidden: the field carries the error
+            return {"error": f"{type(e).__name__}: {e}"[:400]}
+
+    refine = side(lambda: refinement(R, torch, plan, wl, cubes, targets, stream, cap))
+    seg = side(lambda: segment_mode(R, torch, plan, wl, cubes, stream, dev, ws, located, amp, count,
+                                    max(1, min(args.steps // 20, 50))))
+    dense = side(lambda: dense_comparator(R, torch, wl, nv, cubes, targets, stream, dev, ws,
+                                          max(1, min(args.steps, 200)), max(3, min(args.warmup, 10)), cap, value))
+    mixed = side(lambda: mixed_batch(R, torch, ri, dev, ws, stream, n_frames=512 if args.steps >= 100 else 64))
+    srur = side(lambda: srur_frames(R, torch, ri, dev, ws, stream, max(1, min(args.steps // 20, 50))))
+    per_pass = side(lambda: per_pass_roofline(R, torch, wl, nv, seed, cubes, stream, peak,
+                                              max(10, min(args.steps, 400))))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
