@@ -13,6 +13,12 @@ the CUDA library; both sides only read the same seeded cubes from
 ``refine.py`` is the bucket-domain refinement loss of off-grid tones and its gradient
 (beyond the paper), pinned by central finite differences.
 
+The first stage has two modes: known noise (the paper's model, sigma_n^2 given) and an
+estimate mode in which each loop's noise floor is the lower median of its bucket powers
+divided by ln 2 (eq. (exp): the median of an exponential is its mean times ln 2).  The
+second-stage design has the paper's Normal vote approximation (Claims 2-3) and an exact
+binomial vote law (``design.optimal_thresholds_binomial``).
+
 ``bartlett.py`` is the dense comparison system of Appendix A (Algorithm 2, one
 segment): window, full N-D DFT, exact NP threshold on the bin power.
 
@@ -28,11 +34,12 @@ from .windows import (chebyshev_window, flat_window, flat_gain, window_6db_bins,
                       chebyshev_poly)
 from .pipeline import (OraclePlan, make_plan, rsft, fold_loop, bucket_spectrum,
                        fold_bucket_direct, reverse_map, mapping, estimate_amplitudes,
-                       permute, alias)
+                       permute, alias, noise_floor_gamma, spectrum_at)
 from .refine import tone_field, refine_loss, refine_grad
 from .bartlett import bartlett, bartlett_window, bartlett_gamma, bartlett_pd_swerling1
 from .design import (beta_sigma, alpha_sigma, mean_alpha, mean_beta, q_func,
-                     solve_pd_bar, solve_pfa1, optimal_thresholds,
+                     solve_pd_bar, solve_pfa1, optimal_thresholds, optimal_thresholds_binomial,
+                     binomial_vote_tail, solve_pd_bar_binomial, solve_pfa1_binomial,
                      complexity_rsft, complexity_bartlett, first_stage_gamma)
 
 __all__ = [
@@ -40,9 +47,10 @@ __all__ = [
     "chebyshev_window", "flat_window", "flat_gain", "window_6db_bins", "chebyshev_poly",
     "OraclePlan", "make_plan", "rsft", "fold_loop", "bucket_spectrum",
     "fold_bucket_direct", "reverse_map", "mapping", "estimate_amplitudes",
-    "permute", "alias",
+    "permute", "alias", "noise_floor_gamma", "spectrum_at",
     "beta_sigma", "alpha_sigma", "mean_alpha", "mean_beta", "q_func",
-    "solve_pd_bar", "solve_pfa1", "optimal_thresholds", "complexity_rsft",
+    "solve_pd_bar", "solve_pfa1", "optimal_thresholds", "optimal_thresholds_binomial",
+    "binomial_vote_tail", "solve_pd_bar_binomial", "solve_pfa1_binomial", "complexity_rsft",
     "complexity_bartlett", "first_stage_gamma",
     "bartlett", "bartlett_window", "bartlett_gamma", "bartlett_pd_swerling1",
     "tone_field", "refine_loss", "refine_grad",

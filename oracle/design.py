@@ -12,6 +12,16 @@ solves P_d and P_fa for (Pd-bar, Pfa1-bar), and keeps the mu with the smallest
 SNR_min = (beta-bar / alpha-bar) (ln Pfa1-bar / ln Pd-bar - 1), which follows
 from eq. (bpd).
 
+Binomial design (a reading beyond the paper, kept as an option; the paper's Normal form is
+the default): sigma_l is drawn independently per loop (Def. 1), so the per-loop votes of one
+cell are independent Bernoulli trials.  A true cell votes with probability Pd-bar, so its
+count is Binomial(L, Pd-bar) exactly (the law Claim 2 approximates).  An off-target cell, in
+each loop independently, shares its bucket with a target's main lobe with probability
+rho = K eta_m / B (Claim 3's F / L) and then votes with probability min(1, eta_p Pd-bar), and
+otherwise votes with probability Pfa1-bar; its count is Binomial(L, q), q = rho min(1,
+eta_p Pd-bar) + (1 - rho) Pfa1-bar.  Claim 3's Normal approximation of the same count is thin
+in the upper tail when q is small, which is where P_fa lives.
+
 Operation counts: eq. (RSFT_complexity) with B log2 B for the FFT term, and the
 Bartlett count of Table I.
 """
@@ -20,7 +30,7 @@ from __future__ import annotations
 import math
 
 import numpy as np
-from scipy.stats import norm
+from scipy.stats import binom, norm
 
 
 def beta_sigma(wbars, ws, sigma_row) -> float:
@@ -142,6 +152,63 @@ def optimal_thresholds(loops: int, b: int, k: int, eta_m: float, p_d: float,
     return {"mu": best[0], "pd_bar": best[1], "pfa1": best[2], "snr": best[3],
             "snr_db": 10 * math.log10(best[3]) if best[3] > 0 else float("-inf"),
             "f_count": f_count, "table": rows}
+
+
+def binomial_vote_tail(loops: int, p: float, mu: int) -> float:
+    """P(V > mu) for V ~ Binomial(L, p): the vote count of a cell whose per-loop vote
+    probability is p, the loops being independent."""
+    return float(binom.sf(mu, loops, p))
+
+
+def solve_pd_bar_binomial(mu: int, loops: int, p_d: float):
+    """Pd-bar with P(Binomial(L, Pd-bar) > mu) = P_d (the exact law behind Claim 2); None if none."""
+    def fun(p):
+        return binomial_vote_tail(loops, p, mu) - p_d
+    lo, hi = 1e-15, 1 - 1e-15
+    if (fun(lo) > 0) == (fun(hi) > 0):
+        return None
+    return _bisect(fun, lo, hi)
+
+
+def solve_pfa1_binomial(mu: int, loops: int, p_fa: float, rho: float, eta_p, pd_bar: float):
+    """Pfa1-bar with P(Binomial(L, q) > mu) = P_fa, q = rho hit + (1 - rho) Pfa1-bar (the exact
+    law behind Claim 3); None when even Pfa1-bar = 0 gives a tail above P_fa."""
+    ep = (1.0 / pd_bar) if eta_p == "upper" else float(eta_p)
+    hit = min(1.0, ep * pd_bar)
+    base = rho * hit
+
+    def fun(q):
+        return binomial_vote_tail(loops, base + (1.0 - rho) * q, mu) - p_fa
+    lo, hi = 1e-300, 1 - 1e-12
+    if fun(0.0) >= 0 or (fun(lo) > 0) == (fun(hi) > 0):
+        return None
+    return _bisect(fun, lo, hi, iters=400)
+
+
+def optimal_thresholds_binomial(loops: int, b: int, k: int, eta_m: float, p_d: float,
+                                p_fa: float, eta_p=1.0, alpha_bar: float = 1.0,
+                                beta_bar: float = 1.0) -> dict:
+    """Eq. (opt) with the binomial vote laws in place of Claims 2-3's Normal forms: enumerate
+    mu in [L], solve both laws for (Pd-bar, Pfa1-bar), keep the smallest SNR_min."""
+    rho = k * eta_m / b
+    if rho >= 1.0:
+        raise ValueError("infeasible design: K eta_m >= B (Remark 2)")
+    rows = []
+    for mu in range(loops):
+        pd = solve_pd_bar_binomial(mu, loops, p_d)
+        if pd is None:
+            continue
+        q = solve_pfa1_binomial(mu, loops, p_fa, rho, eta_p, pd)
+        if q is None or q >= pd:
+            continue
+        snr = (beta_bar / alpha_bar) * (math.log(q) / math.log(pd) - 1.0)
+        rows.append((mu, pd, q, snr))
+    if not rows:
+        raise ValueError("no feasible second-stage threshold")
+    best = min(rows, key=lambda r: r[3])
+    return {"mu": best[0], "pd_bar": best[1], "pfa1": best[2], "snr": best[3],
+            "snr_db": 10 * math.log10(best[3]) if best[3] > 0 else float("-inf"),
+            "rho": rho, "f_count": loops * rho, "table": rows}
 
 
 def first_stage_gamma(noise_var: float, beta: float, pfa1: float) -> float:

@@ -28,7 +28,7 @@ import numpy as np
 
 from .perm import draw_sigmas, inverse_mod
 from .windows import pre_window, flat_window, flat_gain, window_6db_bins
-from .design import beta_sigma, optimal_thresholds, first_stage_gamma
+from .design import beta_sigma, optimal_thresholds, optimal_thresholds_binomial, first_stage_gamma
 
 
 @dataclasses.dataclass
@@ -44,7 +44,7 @@ class OraclePlan:
     gain: list               # G_d(u) = DFT(w-bar_d)[u] / N_d
     wsum: float              # prod_d sum_t w_d(t): DC gain of the pre-window
     beta: np.ndarray         # [L] beta(sigma_l)
-    gamma: np.ndarray        # [L] first-stage thresholds
+    gamma: np.ndarray        # [L] first-stage thresholds (known noise); NaN in estimate mode
     mu: int
     pfa1: float
     noise_var: float
@@ -55,13 +55,25 @@ class OraclePlan:
     def ndim(self) -> int:
         return len(self.n)
 
+    @property
+    def estimate_noise(self) -> bool:
+        """Estimate mode: the noise floor of each loop is taken from its own bucket powers."""
+        return not self.noise_var > 0
+
 
 def make_plan(n, b, loops: int, seed: int = 0, window: str = "cheb",
               atten_db: float = 60.0, flat: str = "cheb", flat_support=None,
               noise_var: float = 1.0, p_fa: float = 1e-6, p_d: float = 0.9,
               k_max: int = 8, eta_p=1.0, pfa1: float | None = None,
-              mu: int | None = None, sigma=None, beta_mode: str = "exact") -> OraclePlan:
-    """Build the oracle's plan: sigma draws, windows, and both thresholds."""
+              mu: int | None = None, sigma=None, beta_mode: str = "exact",
+              design_mode: str = "normal") -> OraclePlan:
+    """Build the oracle's plan: sigma draws, windows, and both thresholds.
+
+    ``noise_var <= 0`` selects the estimate mode of the first stage (the noise floor is
+    estimated per loop from the bucket powers, ``noise_floor_gamma``); the thresholds are then
+    formed at run time and ``gamma`` holds NaN.  ``design_mode`` picks the second-stage vote
+    model of the threshold design: "normal" (Claims 2-3, the paper) or "binomial" (the exact
+    binomial vote law, ``design.optimal_thresholds_binomial``)."""
     n = tuple(int(x) for x in n)
     b = tuple(int(x) for x in b)
     d = len(n)
@@ -83,10 +95,17 @@ def make_plan(n, b, loops: int, seed: int = 0, window: str = "cheb",
     eta_m = float(np.prod([window_6db_bins(x) for x in w]))
     design = None
     if pfa1 is None or mu is None:
-        design = optimal_thresholds(loops, int(np.prod(b)), k_max, eta_m, p_d, p_fa, eta_p)
+        if design_mode == "binomial":
+            design = optimal_thresholds_binomial(loops, int(np.prod(b)), k_max, eta_m, p_d, p_fa, eta_p)
+        elif design_mode == "normal":
+            design = optimal_thresholds(loops, int(np.prod(b)), k_max, eta_m, p_d, p_fa, eta_p)
+        else:
+            raise ValueError("design_mode must be 'normal' or 'binomial'")
         pfa1 = design["pfa1"] if pfa1 is None else pfa1
         mu = design["mu"] if mu is None else mu
-    if beta_mode == "mean":
+    if not noise_var > 0:
+        gamma = np.full(loops, np.nan)       # estimate mode: formed per loop from the data
+    elif beta_mode == "mean":
         from .design import mean_beta
         bb = mean_beta(wbar, w)
         gamma = np.full(loops, first_stage_gamma(noise_var, bb, pfa1))
@@ -148,6 +167,62 @@ def fold_bucket_direct(plan: OraclePlan, r: np.ndarray, l: int, j) -> complex:
     return complex(np.sum(_outer(wb) * _outer(wp) * vals))
 
 
+def noise_floor_gamma(power: np.ndarray, pfa1: float) -> float:
+    """First-stage threshold of one loop from its own bucket powers (estimate mode).
+
+    Under H0 a bucket's power is exponential with mean sigma_n^2 beta (eq. (exp)), whose median
+    is the mean times ln 2; so the lower median of the loop's B powers (rank floor((B - 1) / 2)
+    in ascending order) divided by ln 2 estimates the mean, and the threshold is that estimate
+    in place of sigma_n^2 beta in gamma = -sigma_n^2 beta ln Pfa1 (eq. (tpd))."""
+    flat = np.sort(np.asarray(power, dtype=np.float64).reshape(-1))
+    m_hat = flat[(flat.size - 1) // 2] / math.log(2.0)
+    return -m_hat * math.log(pfa1)
+
+
+def spectrum_at(plan: OraclePlan, r: np.ndarray, pairs, rows_per_chunk: int = 0) -> np.ndarray:
+    """f-hat_l[k] for a list of (l, k) pairs, without forming any other bucket.
+
+    Eq. (l) followed by the bucket DFT (eq. (f)) is one sum over the cube:
+        f-hat_l[k] = sum_t w-bar(t) w(sigma_l t) r(sigma_l t) e^{-j 2 pi sum_d t_d k_d / B_d},
+    and with s = sigma_l t (t = sigma_l^{-1} s mod N, a bijection, Def. 1) every factor but r
+    splits over the dimensions:
+        f-hat_l[k] = sum_s r(s) prod_d v_d(s_d),
+        v_d(s_d) = w-bar_d(t_d) w_d(s_d) e^{-j 2 pi t_d k_d / B_d},  t_d = sigma_{l,d}^{-1} s_d mod N_d.
+    The cube is contracted with the pairs' vectors one dimension at a time, last dimension first,
+    in slabs of the first dimension (FP64; the cube is read once for all pairs)."""
+    r = np.asarray(r)
+    if tuple(r.shape) != plan.n:
+        raise ValueError("cube shape does not match the plan")
+    pairs = [(int(l), tuple(int(x) for x in k)) for l, k in pairs]
+    P = len(pairs)
+    D = plan.ndim
+    vecs = []
+    for dd in range(D):
+        n, bd = plan.n[dd], plan.b[dd]
+        s = np.arange(n)
+        v = np.empty((n, P), dtype=np.complex128)
+        for p, (l, k) in enumerate(pairs):
+            t = (int(plan.sigma_inv[l, dd]) * s) % n
+            v[:, p] = plan.wbar[dd][t] * plan.w[dd][s] * np.exp(-2j * np.pi * ((t * k[dd]) % bd) / bd)
+        vecs.append(v)
+    out = np.zeros(P, dtype=np.complex128)
+    inner = int(np.prod(plan.n[1:])) if D > 1 else 1
+    step = rows_per_chunk or max(1, (1 << 22) // max(inner, 1))
+    for a0 in range(0, plan.n[0], step):
+        a1 = min(plan.n[0], a0 + step)
+        x = r[a0:a1].astype(np.complex128)
+        if D == 1:
+            out += x @ vecs[0][a0:a1]
+            continue
+        y = x.reshape(-1, plan.n[-1]) @ vecs[-1]                     # [rows..., P]
+        for dd in range(D - 2, 0, -1):                               # middle dimensions
+            y = y.reshape(-1, plan.n[dd], P)
+            y = np.einsum("xsp,sp->xp", y, vecs[dd])
+        y = y.reshape(a1 - a0, P)
+        out += np.einsum("sp,sp->p", y, vecs[0][a0:a1])
+    return out
+
+
 def reverse_map(plan: OraclePlan, l: int, j) -> list:
     """R(j, sigma^{-1}) per dimension: {sigma^{-1} u mod N : jM <= u < (j+1)M} (Def. 4)."""
     out = []
@@ -194,11 +269,14 @@ def rsft(plan: OraclePlan, r, estimate: bool = True, keep: bool = True) -> dict:
     elif tuple(r.shape) != plan.n:
         raise ValueError("cube shape does not match the plan")
     votes = np.zeros(plan.n, dtype=np.int64)
-    folded, spectra, detected = [], [], []
+    folded, spectra, detected, gammas = [], [], [], []
     for l in range(plan.loops):
         f = fold_loop(plan, r[l] if segments else r, l)
         fh = bucket_spectrum(f)
-        c = np.abs(fh) ** 2 > plan.gamma[l]
+        power = np.abs(fh) ** 2
+        gam = noise_floor_gamma(power, plan.pfa1) if plan.estimate_noise else plan.gamma[l]
+        gammas.append(gam)
+        c = power > gam
         for j in np.argwhere(c):
             votes[np.ix_(*reverse_map(plan, l, j))] += 1
         if keep:
@@ -212,6 +290,7 @@ def rsft(plan: OraclePlan, r, estimate: bool = True, keep: bool = True) -> dict:
         "located_votes": votes.reshape(-1)[located],
         "spectrum": np.stack(spectra),
         "detected": np.stack(detected),
+        "gamma": np.asarray(gammas, dtype=np.float64),
     }
     if keep:
         out["folded"] = np.stack(folded)

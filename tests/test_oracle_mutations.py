@@ -17,6 +17,7 @@ import oracle.design as odes
 import tests.test_oracle_pins as pins
 import tests.test_oracle_refine as rpins
 import tests.test_oracle_bartlett as bpins
+import tests.test_oracle_estimate as epins
 
 
 def _perm_inverse(y, sigma_row):
@@ -103,6 +104,31 @@ def _dense_gain_squared(*args, **kwargs):         # amplitudes over (sum w)^2 in
     out["amplitudes"] = out["amplitudes"] / gain
     return out
 
+def _floor_upper_median(power, pfa1):          # rank B // 2 in place of floor((B - 1) / 2)
+    flat = np.sort(np.asarray(power, dtype=np.float64).reshape(-1))
+    return -flat[flat.size // 2] / math.log(2.0) * math.log(pfa1)
+
+
+def _floor_no_ln2(power, pfa1):                # the median taken as the mean itself
+    flat = np.sort(np.asarray(power, dtype=np.float64).reshape(-1))
+    return -flat[(flat.size - 1) // 2] * math.log(pfa1)
+
+
+def _floor_from_mean(power, pfa1):             # sample mean in place of median / ln 2
+    return -float(np.mean(power)) * math.log(pfa1)
+
+
+def _spectrum_at_sigma(plan, r, pairs, rows_per_chunk=0):   # weights indexed with sigma, not sigma^-1
+    saved = plan.sigma_inv
+    plan.sigma_inv = plan.sigma
+    try:
+        return _ORIG_SPEC_AT(plan, r, pairs, rows_per_chunk)
+    finally:
+        plan.sigma_inv = saved
+
+
+_ORIG_SPEC_AT = orsft.spectrum_at
+
 CASES = [
     ("permute with sigma^-1", [(orsft, "permute", _perm_inverse), (O, "permute", _perm_inverse)],
      lambda: pins.test_permutation_property((16, 8), (3, 7))),
@@ -131,6 +157,18 @@ CASES = [
      lambda: bpins.test_noise_only_power_is_exponential_and_pfa_holds()),
     ("dense detector: amplitude over the squared gain", [(O, "bartlett", _dense_gain_squared)],
      lambda: bpins.test_exact_recovery_of_on_grid_tones()),
+    ("noise floor: upper median", [(orsft, "noise_floor_gamma", _floor_upper_median),
+                                   (O, "noise_floor_gamma", _floor_upper_median)],
+     epins.test_noise_floor_rank_is_the_lower_median),
+    ("noise floor: median without ln 2", [(orsft, "noise_floor_gamma", _floor_no_ln2),
+                                          (O, "noise_floor_gamma", _floor_no_ln2)],
+     lambda: epins.test_noise_floor_threshold_closed_form(256, 0.01)),
+    ("noise floor: the mean in place of the median", [(orsft, "noise_floor_gamma", _floor_from_mean),
+                                                      (O, "noise_floor_gamma", _floor_from_mean)],
+     epins.test_estimate_mode_detects_strong_tones),
+    ("sampled spectrum: weights of sigma", [(orsft, "spectrum_at", _spectrum_at_sigma),
+                                            (O, "spectrum_at", _spectrum_at_sigma)],
+     lambda: epins.test_spectrum_at_equals_fft_of_fold((32, 16), (8, 4))),
 ]
 
 
