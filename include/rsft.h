@@ -71,6 +71,14 @@ enum { RSFT_BETA_EXACT = 0, RSFT_BETA_MEAN = 1 };    /* beta(sigma_l) or beta-ba
  * second stage fused (default), or by scattering every candidate of every detected
  * bucket with 8-bit atomic adds into an N-byte vote array followed by a compaction. */
 enum { RSFT_VOTES_ROWS = 0, RSFT_VOTES_SCATTER = 1 };
+/* Vote law of the second-stage threshold design (eq. (opt)): the Normal approximations of
+ * Claims 2-3 (the paper; default), or the binomial laws they approximate.  Binomial: sigma_l
+ * is drawn independently per loop (Def. 1), so a true cell's count is Binomial(L, Pd-bar)
+ * and an off-target cell's Binomial(L, q), q = rho min(1, eta_p Pd-bar) + (1 - rho)
+ * Pfa1-bar with rho = K_max eta_m / B (Claim 3's F / L).  The Normal form underestimates the
+ * upper tail of the off-target count, where P_fa lies, so at small P_fa the binomial design
+ * picks a higher mu and meets P_fa on noise; target-induced false alarms are heavier still. */
+enum { RSFT_DESIGN_NORMAL = 0, RSFT_DESIGN_BINOMIAL = 1 };
 
 /* Warning bits reported by rsft_plan_get(RSFT_GET_WARNINGS). */
 enum { RSFT_WARN_SPARSITY_LIMIT = 1 };  /* K_max * eta_m >= B: Remark 2, RSFT cannot separate H0/H1 */
@@ -94,32 +102,41 @@ typedef struct rsft_desc {
   double eta_p;              /* calibration eta_p >= 1 (Claim 3); <= 0 = 1/Pd-bar     */
   double p_fa1_override;     /* > 0: first-stage Pfa1-bar; else from eq. (opt)        */
   int32_t mu_override;       /* >= 0: second-stage threshold mu; else from eq. (opt)  */
-  double noise_var;          /* sigma_n^2 > 0 (known noise, §IV-A)                    */
+  double noise_var;          /* sigma_n^2 > 0: known noise (§IV-A).  <= 0: estimate mode:
+                              * each execute takes loop l's noise floor from its own bucket
+                              * powers P_l = |f-hat_l|^2 as lowermedian(P_l) / ln 2 (rank
+                              * floor((B - 1) / 2) ascending; under H0 the power is
+                              * exponential, eq. (exp), whose median is the mean times
+                              * ln 2) and sets gamma_l = -(lowermedian(P_l) / ln 2) ln Pfa1-bar
+                              * (eq. (tpd) with the estimate in place of sigma_n^2 beta)   */
   uint64_t seed;             /* SplitMix64 seed of the sigma draws                    */
   const int64_t* sigma;      /* optional [loops][ndim] odd multipliers; NULL = draw   */
   int32_t beta_mode;         /* RSFT_BETA_EXACT (default) or RSFT_BETA_MEAN           */
   int64_t max_located;       /* capacity of the located list (default 65536)          */
   int32_t device;            /* CUDA device ordinal; -1 = host-only plan (tables only) */
   int32_t vote_mode;         /* RSFT_VOTES_ROWS (default) or RSFT_VOTES_SCATTER        */
+  int32_t design_mode;       /* RSFT_DESIGN_NORMAL (default) or RSFT_DESIGN_BINOMIAL   */
 } rsft_desc;
 
 typedef struct rsft_plan rsft_plan;
 
 /* Fill *desc with defaults: ndim 0 (must be set), Chebyshev 60 dB windows,
  * p_fa 1e-6, p_d 0.9, k_max 8, eta_p 1, no overrides, noise_var 1, seed 0,
- * max_located 65536, device 0.  desc must not be NULL. */
+ * max_located 65536, device 0, row votes, Normal design.  desc must not be NULL. */
 void rsft_desc_init(rsft_desc* desc);
 
 /*
  * Build a plan: draw sigma (Def. 1; odd values, §V-E), build the windows
  * (§III-C.1, §IV-B), per-loop beta(sigma_l) (eq. (alpha_beta)), solve eq.
  * (opt) for (mu, Pfa1-bar) unless overridden, set gamma_l = -sigma_n^2
- * beta(sigma_l) ln Pfa1-bar (eq. (tpd)), upload the tables and allocate the
- * workspace on desc->device.  With device = -1 only the host tables are
+ * beta(sigma_l) ln Pfa1-bar (eq. (tpd)) -- or, in estimate mode (noise_var
+ * <= 0), leave gamma_l to each execute (NaN in RSFT_GET_GAMMA) -- upload the
+ * tables and allocate the workspace on desc->device.  With device = -1 only the host tables are
  * built (for rsft_plan_get); such a plan cannot execute.
  * Ownership: *plan is owned by the caller and released by rsft_plan_destroy.
- * Errors: INVALID_ARG (sizes, loops, windows), UNSUPPORTED (ndim > 4),
- * DESIGN (no feasible mu), OOM, CUDA.  On error *plan is set to NULL.
+ * Errors: INVALID_ARG (sizes, loops, windows, a non-finite noise_var, an
+ * unknown design_mode), UNSUPPORTED (ndim > 4), DESIGN (no feasible mu),
+ * OOM, CUDA.  On error *plan is set to NULL.
  */
 rsft_status rsft_plan_create(const rsft_desc* desc, rsft_plan** plan);
 
@@ -189,11 +206,15 @@ enum {
                              * execute (with amplitudes).  Waits for the timed executes.      */
   RSFT_GET_FOLD_BYTES = 15, /* int64 [1]     algorithmic bytes of one execute's fold: the cube
                              * read once per loop group plus the bucket writes               */
-  RSFT_GET_FOLD_COPY = 16   /* int32 [1]     how the last fold streamed the cube: 0 one bulk copy
+  RSFT_GET_FOLD_COPY = 16,  /* int32 [1]     how the last fold streamed the cube: 0 one bulk copy
                              * per row, 3 or 5 one tensor-map box per stage (rank) into the SIMT
                              * fold, 103 or 105 the same boxes into the tensor-core fold (whole
                              * 64-column rows, chosen by environment RSFT_FOLD=tc at plan
                              * creation), -1 none yet                                            */
+  RSFT_GET_GAMMA_LAST = 17  /* double [L]    thresholds the last execute on the plan's own
+                             * workspace compared with: the plan's gamma_l with known noise, the
+                             * per-loop estimates (FP32, widened) in estimate mode.  Waits for the
+                             * device; NaN before the first execute in estimate mode.          */
 };
 rsft_status rsft_plan_get(const rsft_plan* plan, int32_t what, void* out, size_t bytes);
 
@@ -257,9 +278,10 @@ rsft_status rsft_refine(rsft_plan* plan, const void* d_cube, int64_t k,
  * not call cudaMalloc or cudaFree when it runs (a real-time loop whose memory
  * is fixed at start-up, a host framework that owns every allocation, code
  * that cannot afford the device synchronisation those calls may cause).
- *   d_votes          device uint8 [n], 16-byte aligned: the accumulated votes
- *                    (eq. (a_i)), e.g. rsft_execute's d_votes_out.  Cleared to
- *                    zero on return, as rsft_execute clears its own votes.
+ *   d_votes          device uint8 [n], 16-byte aligned: the accumulated
+ *                    per-frequency vote counts, e.g. rsft_execute's
+ *                    d_votes_out.  Cleared to zero on return, as rsft_execute
+ *                    clears its own votes.
  *   n                number of votes: a multiple of 16384, at most 2^28.
  *   mu               second-stage threshold, 0..254.
  *   d_located        device uint64 [capacity]: located indices, ascending.
@@ -271,6 +293,10 @@ rsft_status rsft_refine(rsft_plan* plan, const void* d_cube, int64_t k,
  * the library's device memory that every GPU loading the library holds until
  * the process exits.  The first call on a device looks that array up
  * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * The looked-up address is kept for the life of the process: after a device
+ * reset (cudaDeviceReset, or a release and re-creation of the primary
+ * context) the entry point must not be called again on that device until
+ * the library is reloaded.
  * All calls share the one array: calls that overlap on the GPU (other
  * streams, other threads) race and must be serialised by the caller.
  * Errors: INVALID_ARG for NULL pointers, misalignment, n not a multiple of

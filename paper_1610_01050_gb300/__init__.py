@@ -32,11 +32,13 @@ RSFT_WIN_RECT, RSFT_WIN_CHEB = 0, 1
 RSFT_FLAT_IDEAL, RSFT_FLAT_CHEB = 0, 1
 RSFT_BETA_EXACT, RSFT_BETA_MEAN = 0, 1
 RSFT_VOTES_ROWS, RSFT_VOTES_SCATTER = 0, 1
+RSFT_DESIGN_NORMAL, RSFT_DESIGN_BINOMIAL = 0, 1
 RSFT_WARN_SPARSITY_LIMIT = 1
 RSFT_GET_SIGMA, RSFT_GET_SIGMA_INV, RSFT_GET_GAMMA, RSFT_GET_BETA = 1, 2, 3, 4
 RSFT_GET_MU, RSFT_GET_PFA1, RSFT_GET_ETA_M, RSFT_GET_PD_BAR = 5, 6, 7, 8
 RSFT_GET_WINDOW, RSFT_GET_FLAT, RSFT_GET_WARNINGS, RSFT_GET_SNR_DB = 9, 10, 11, 12
 RSFT_GET_WORKSPACE_BYTES, RSFT_GET_STAGE_MS, RSFT_GET_FOLD_BYTES, RSFT_GET_FOLD_COPY = 13, 14, 15, 16
+RSFT_GET_GAMMA_LAST = 17
 RSFT_BUCKETS_FOLDED, RSFT_BUCKETS_SPECTRUM = 0, 1
 
 # Every C entry point declared in include/rsft.h.
@@ -62,7 +64,7 @@ class RsftDesc(ctypes.Structure):
         ("k_max", c_int32), ("eta_p", c_double), ("p_fa1_override", c_double),
         ("mu_override", c_int32), ("noise_var", c_double), ("seed", c_uint64),
         ("sigma", POINTER(c_int64)), ("beta_mode", c_int32), ("max_located", c_int64),
-        ("device", c_int32), ("vote_mode", c_int32),
+        ("device", c_int32), ("vote_mode", c_int32), ("design_mode", c_int32),
     ]
 
 
@@ -249,8 +251,9 @@ def rsft_desc_init() -> RsftDesc:
 def make_desc(n, b, loops, *, window=RSFT_WIN_CHEB, atten_db=60.0, flat=RSFT_FLAT_CHEB, flat_support=None,
               p_fa=1e-6, p_d=0.9, k_max=8, eta_p=1.0, p_fa1=None, mu=None, noise_var=1.0, seed=0,
               sigma=None, beta_mode=RSFT_BETA_EXACT, max_located=65536, device=0,
-              vote_mode=RSFT_VOTES_ROWS) -> RsftDesc:
-    """Descriptor from keyword arguments (sizes per dimension, powers of two)."""
+              vote_mode=RSFT_VOTES_ROWS, design_mode=RSFT_DESIGN_NORMAL) -> RsftDesc:
+    """Descriptor from keyword arguments (sizes per dimension, powers of two).  ``noise_var <= 0``
+    selects the estimate mode of the first stage (noise floor from each loop's bucket powers)."""
     d = rsft_desc_init()
     d.ndim = len(n)
     for i, (nn, bb) in enumerate(zip(n, b)):
@@ -272,6 +275,7 @@ def make_desc(n, b, loops, *, window=RSFT_WIN_CHEB, atten_db=60.0, flat=RSFT_FLA
     d.max_located = int(max_located)
     d.device = int(device)
     d.vote_mode = int(vote_mode)
+    d.design_mode = int(design_mode)
     if sigma is not None:
         arr = np.ascontiguousarray(np.asarray(sigma, dtype=np.int64).reshape(-1))
         d._sigma_keep = arr
@@ -328,6 +332,7 @@ _GET_SHAPES = {
     RSFT_GET_FLAT: ("float64", "2sn"), RSFT_GET_WARNINGS: ("int32", "1"),
     RSFT_GET_SNR_DB: ("float64", "1"), RSFT_GET_WORKSPACE_BYTES: ("int64", "1"),
     RSFT_GET_STAGE_MS: ("float64", "8"), RSFT_GET_FOLD_BYTES: ("int64", "1"), RSFT_GET_FOLD_COPY: ("int32", "1"),
+    RSFT_GET_GAMMA_LAST: ("float64", "l"),
 }
 
 
@@ -418,10 +423,50 @@ def rsft_refine_eval(plan: Plan, freq, amp, loss=None, grad_freq=None, grad_amp=
                                            _dptr(grad_amp, "grad_amp"), _dptr(hdiag, "hdiag"), _stream(stream)))
 
 
+def _check_stage2_tensors(votes, n, located, count, located_votes, cap):
+    """Sizes, types and devices of rsft_stage2_static's tensors, checked before any launch: the C
+    call sees only pointers, so a tensor shorter than n or cap would be read or written past its end."""
+    given = [("votes", votes), ("count", count), ("located", located), ("located_votes", located_votes)]
+    for what, t in given:
+        if t is not None and not (hasattr(t, "is_cuda") and t.is_cuda):
+            kind = "a CPU tensor" if hasattr(t, "is_cuda") else type(t).__name__
+            raise TypeError(f"{what} must be a CUDA tensor (device memory), not {kind}")
+    import torch
+    dtypes = {"votes": (torch.uint8,), "count": (torch.int64,), "located_votes": (torch.uint8,),
+              "located": (torch.int64,) + ((torch.uint64,) if hasattr(torch, "uint64") else ())}
+    dev = torch.cuda.current_device()
+    for what, t in given:
+        if t is None:
+            continue
+        if t.dtype not in dtypes[what]:
+            raise TypeError(f"{what} must have dtype {' or '.join(str(d) for d in dtypes[what])}, not {t.dtype}")
+        if t.device.index != dev:
+            raise ValueError(f"{what} must be on the current CUDA device (cuda:{dev})")
+        if not t.is_contiguous():
+            raise ValueError(f"{what} must be contiguous")
+    if int(n) > votes.numel():
+        raise ValueError(f"n = {int(n)} exceeds the {votes.numel()} votes of the tensor")
+    if count is None or count.numel() < 1:
+        raise ValueError("count must hold at least one element")
+    if cap < 0:
+        raise ValueError("capacity must be >= 0")
+    if cap > 0 and located is None:
+        raise ValueError("located is required when capacity > 0")
+    if located is not None and cap > located.numel():
+        raise ValueError(f"capacity {cap} exceeds the {located.numel()} entries of located")
+    if located_votes is not None and cap > located_votes.numel():
+        raise ValueError(f"capacity {cap} exceeds the {located_votes.numel()} entries of located_votes")
+
+
 def rsft_stage2_static(votes, n, mu, located, count, located_votes=None, capacity=None, stream=None) -> None:
     """Second-stage compaction into caller buffers, with library-owned fixed scratch
-    (no device allocation); ``votes`` is cleared.  See include/rsft.h."""
-    cap = int(located.numel()) if capacity is None else int(capacity)
+    (no device allocation); ``votes`` is cleared.  See include/rsft.h.
+
+    Tensors are checked against n and the capacity before the call (ValueError / TypeError);
+    the C entry point itself checks the limits it can see (alignment, n a multiple of 16384 and
+    at most 2^28, mu)."""
+    cap = (int(located.numel()) if located is not None else 0) if capacity is None else int(capacity)
+    _check_stage2_tensors(votes, n, located, count, located_votes, cap)
     _check(load_library().rsft_stage2_static(_dptr(votes, "votes"), int(n), int(mu), _dptr(located, "located"),
                                              _dptr(located_votes, "located_votes"), cap, _dptr(count, "count"),
                                              _stream(stream)))

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -260,6 +261,13 @@ rsft_status alloc_workspace(rsft_plan* p, rsft::Workspace& ws, int64_t** d_count
       RSFT_OK)
     return st;
   if ((st = dev_alloc(p, &ws.det_count, static_cast<size_t>(L) * 4)) != RSFT_OK) return st;
+  ws.gamma_used = nullptr;
+  if (h.estimate_noise) {
+    if ((st = dev_alloc(p, &ws.gamma_used, static_cast<size_t>(L) * 4)) != RSFT_OK) return st;
+    std::vector<float> nan(L, std::numeric_limits<float>::quiet_NaN());
+    cudaError_t ce = cudaMemcpy(ws.gamma_used, nan.data(), nan.size() * 4, cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaMemcpy(gamma_used)");
+  }
   ws.segments = rsft::stage2_segments(h.total_n);
   const size_t vote_bytes = static_cast<size_t>(ws.segments) * 16 * 1024;
   ws.vote_words = static_cast<int64_t>(vote_bytes / 4);
@@ -608,7 +616,8 @@ void drain_timing(rsft_plan* p) {
 
 int launches_per_execute(const rsft_plan* p) {
   const int groups = (p->geom.loops + p->loop_group - 1) / p->loop_group;
-  return groups * (p->fold.direct ? 1 : 2) + static_cast<int>(p->passes.size()) + (p->rows_mode ? 3 : 4) + 1;
+  return groups * (p->fold.direct ? 1 : 2) + static_cast<int>(p->passes.size()) + (p->host.estimate_noise ? 1 : 0) +
+         (p->rows_mode ? 3 : 4) + 1;
 }
 
 void release(rsft_plan* p) {
@@ -683,10 +692,17 @@ rsft_status run_lane(rsft_plan* p, rsft::Workspace& ws, bool& votes_dirty, bool 
     if (e != cudaSuccess) return cuda_fail(e, "permute_window_fold");
   }
   mark(1);
+  const bool estimate = p->host.estimate_noise;
   for (size_t i = 0; i < p->passes.size(); ++i) {
     e = rsft::launch_fft_pass(g, p->passes[i], p->tables, i == 0 ? ws.folded : ws.spectrum, ws.spectrum,
-                              ws.det_bits, ws.det_count, ws.words_b, stream);
+                              ws.det_bits, ws.det_count, ws.words_b, !estimate, stream);
     if (e != cudaSuccess) return cuda_fail(e, "bucket_fft/np_detect");
+  }
+  if (estimate) {
+    // noise floor of each loop from its own bucket powers, then the detection against it
+    e = rsft::launch_noise_floor(g, ws.spectrum, static_cast<float>(p->host.floor_factor), ws.gamma_used,
+                                 ws.det_bits, ws.det_count, ws.words_b, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "np_detect (noise floor)");
   }
   mark(2);
   if (p->rows_mode) {
@@ -755,6 +771,7 @@ void rsft_desc_init(rsft_desc* d) {
   d->max_located = 65536;
   d->device = 0;
   d->vote_mode = RSFT_VOTES_ROWS;
+  d->design_mode = RSFT_DESIGN_NORMAL;
 }
 
 rsft_status rsft_plan_create(const rsft_desc* desc, rsft_plan** plan) {
@@ -1137,6 +1154,22 @@ rsft_status rsft_plan_get(const rsft_plan* plan, int32_t what, void* out, size_t
       for (int s = 0; s < 6; ++s) o[s] = mp->stage_ms[s];
       o[6] = static_cast<double>(mp->timed_executes);
       o[7] = mp->has_device ? static_cast<double>(launches_per_execute(mp)) : 0.0;
+      return RSFT_OK;
+    }
+    case RSFT_GET_GAMMA_LAST: {
+      const size_t n = static_cast<size_t>(L) * 8;
+      if (!need(n)) break;
+      double* o = static_cast<double*>(out);
+      if (!h.estimate_noise || !plan->has_device) {
+        std::copy(h.gamma.begin(), h.gamma.end(), o);
+        return RSFT_OK;
+      }
+      DeviceGuard guard(plan->device);
+      std::vector<float> g(L);
+      cudaError_t e = cudaDeviceSynchronize();
+      if (e == cudaSuccess) e = cudaMemcpy(g.data(), plan->ws.gamma_used, static_cast<size_t>(L) * 4, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(e, "rsft_plan_get(GAMMA_LAST)");
+      for (int l = 0; l < L; ++l) o[l] = static_cast<double>(g[l]);
       return RSFT_OK;
     }
     case RSFT_GET_FOLD_COPY:

@@ -117,6 +117,7 @@ struct Workspace {
   uint32_t* seg_count;   // [segments] stage-2 hits per segment
   uint64_t* seg_offset;  // [segments + 1] exclusive scan of seg_count; last = total
   int* err_flag;         // set by a bounded device wait that gave up
+  float* gamma_used;     // [L] first-stage thresholds of the last execute (estimate mode)
   uint32_t* warp_count;  // [row warps] vote_rows hits per warp
   uint64_t* warp_offset; // [row warps + 1]
   ulonglong2* row_list;  // small-row vote kernel: per warp [rows_per_warp] (row, votes > mu mask)
@@ -174,7 +175,11 @@ cudaError_t launch_fold_reduce(const Geometry& g, const FoldSchedule& fs, const 
                                cudaStream_t stream);
 cudaError_t launch_fft_pass(const Geometry& g, const FftPass& ps, const DeviceTables& t,
                             const float2* in, float2* out, uint32_t* det_bits, uint32_t* det_count,
-                            int64_t words_b, cudaStream_t stream);
+                            int64_t words_b, bool detect, cudaStream_t stream);
+// Estimate mode of the first stage: per loop, gamma_l = lowermedian(|f-hat_l|^2) * factor (written to
+// gamma_out[l]) and the loop's detection bitmap and count against it.
+cudaError_t launch_noise_floor(const Geometry& g, const float2* spectrum, float factor, float* gamma_out,
+                               uint32_t* det_bits, uint32_t* det_count, int64_t words_b, cudaStream_t stream);
 cudaError_t launch_vote_scatter(const Geometry& g, const DeviceTables& t, const uint32_t* det_bits,
                                 int64_t words_b, uint32_t* votes, cudaStream_t stream);
 cudaError_t launch_stage2(const Geometry& g, int mu, Workspace& ws, uint64_t* located,

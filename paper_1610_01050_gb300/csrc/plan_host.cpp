@@ -54,6 +54,7 @@ double cheb_t(int64_t order, double x) {
 
 double q_tail(double x) { return 0.5 * std::erfc(x / std::sqrt(2.0)); }
 
+
 template <class F>
 double bisect(F f, double lo, double hi, int iters) {
   double flo = f(lo);
@@ -102,6 +103,19 @@ std::vector<cplx> flat_window(int64_t n, int64_t m, int kind, double atten_db, i
 }
 
 }  // namespace
+
+// P(V > mu) for V ~ Binomial(L, p): the terms C(L, v) p^v (1 - p)^(L - v), v = mu + 1..L, in
+// logarithms (lgamma, log1p) so that neither the coefficients nor the powers overflow.
+double binomial_tail(int L, double p, int mu) {
+  if (mu >= L) return 0.0;
+  if (!(p > 0.0)) return mu < 0 ? 1.0 : 0.0;
+  if (!(p < 1.0)) return 1.0;
+  const double lp = std::log(p), lq = std::log1p(-p), lgl = std::lgamma(L + 1.0);
+  double acc = 0.0;
+  for (int v = std::max(mu + 1, 0); v <= L; ++v)
+    acc += std::exp(lgl - std::lgamma(v + 1.0) - std::lgamma(L - v + 1.0) + v * lp + (L - v) * lq);
+  return std::min(acc, 1.0);
+}
 
 uint64_t splitmix64_at(uint64_t seed, uint64_t index) {
   uint64_t z = seed + (index + 1) * 0x9E3779B97F4A7C15ull;
@@ -215,9 +229,13 @@ rsft_status validate_desc(const rsft_desc& d, std::string& err) {
     err = "atten_db must be in (0, 400]";
     return RSFT_ERR_INVALID_ARG;
   }
-  if (!(d.noise_var > 0.0) || !std::isfinite(d.noise_var)) {
-    err = "noise_var must be positive (known-noise detection, §IV-A)";
-    return RSFT_ERR_UNSUPPORTED;
+  if (!std::isfinite(d.noise_var)) {
+    err = "noise_var must be finite (> 0 known noise, <= 0 estimate mode)";
+    return RSFT_ERR_INVALID_ARG;
+  }
+  if (d.design_mode != RSFT_DESIGN_NORMAL && d.design_mode != RSFT_DESIGN_BINOMIAL) {
+    err = "unknown design_mode";
+    return RSFT_ERR_INVALID_ARG;
   }
   if (d.p_fa1_override > 0.0 && !(d.p_fa1_override < 1.0)) {
     err = "p_fa1_override must be in (0, 1)";
@@ -327,20 +345,27 @@ rsft_status build_host_plan(const rsft_desc& d, HostPlan& p, std::string& err) {
     }
     int best_mu = -1;
     double best_snr = std::numeric_limits<double>::infinity(), best_q = 0, best_pd = 0;
+    const bool binom = d.design_mode == RSFT_DESIGN_BINOMIAL;
+    const double rho = F / static_cast<double>(L);  // per-loop chance of sharing a target's bucket
     for (int cand = 0; cand < L; ++cand) {
+      // Claim 2 (Normal) or its binomial law: P_d = P(votes of a true cell > mu)
       auto fpd = [&](double pd) {
+        if (binom) return binomial_tail(L, pd, cand) - d.p_d;
         return q_tail((cand - L * pd) / std::sqrt(L * pd * (1 - pd))) - d.p_d;
       };
       double lo = 1e-15, hi = 1 - 1e-15;
       if ((fpd(lo) > 0) == (fpd(hi) > 0)) continue;
       const double pd = bisect(fpd, lo, hi, 200);
       const double hit = d.eta_p > 0 ? std::min(1.0, d.eta_p * pd) : 1.0;
+      // Claim 3 (Normal) or its binomial law: P_fa = P(votes of an off-target cell > mu)
       auto fq = [&](double q) {
+        if (binom) return binomial_tail(L, rho * hit + (1.0 - rho) * q, cand) - d.p_fa;
         double mean = F * hit + (L - F) * q;
         double var = F * hit * (1 - hit) + (L - F) * q * (1 - q);
         return q_tail((cand - mean) / std::sqrt(var)) - d.p_fa;
       };
       double qlo = 1e-300, qhi = 1 - 1e-12;
+      if (binom && fq(0.0) >= 0) continue;  // the targets' buckets alone exceed P_fa at this mu
       if ((fq(qlo) > 0) == (fq(qhi) > 0)) continue;
       const double q = bisect(fq, qlo, qhi, 400);
       if (q >= pd) continue;
@@ -380,8 +405,14 @@ rsft_status build_host_plan(const rsft_desc& d, HostPlan& p, std::string& err) {
       beta_mean *= tot / static_cast<double>(n / 2);
     }
   }
+  p.estimate_noise = !(d.noise_var > 0.0);
+  // estimate mode: gamma_l = -(lowermedian(P_l) / ln 2) ln Pfa1-bar is formed by each execute from
+  // its own bucket powers; the factor -ln Pfa1-bar / ln 2 is fixed here
+  p.floor_factor = -std::log(pfa1) / std::log(2.0);
   for (int l = 0; l < L; ++l)
-    p.gamma[l] = -d.noise_var * (d.beta_mode == RSFT_BETA_MEAN ? beta_mean : p.beta[l]) * std::log(pfa1);
+    p.gamma[l] = p.estimate_noise ? std::numeric_limits<double>::quiet_NaN()
+                                  : -d.noise_var * (d.beta_mode == RSFT_BETA_MEAN ? beta_mean : p.beta[l]) *
+                                        std::log(pfa1);
   return RSFT_OK;
 }
 

@@ -30,7 +30,9 @@ struct HostPlan {
   std::vector<cplx> gain_pass[4];  // G_d(-v mod N_d) for pass-band offset v in [M_d]
   double wsum = 1.0;               // prod_d sum_t w_d(t)
   std::vector<double> beta;        // [L] beta(sigma_l) (eq. (alpha_beta))
-  std::vector<double> gamma;       // [L] first-stage thresholds
+  std::vector<double> gamma;       // [L] first-stage thresholds (NaN in estimate mode)
+  bool estimate_noise = false;     // noise_var <= 0: each loop's noise floor from its bucket powers
+  double floor_factor = 0.0;       // -ln Pfa1-bar / ln 2: gamma_l = lowermedian(P_l) times this
   int mu = 0;                      // second-stage threshold: votes > mu
   double pfa1 = 0.0;               // first-stage Pfa1-bar
   double pd_bar = 0.0;             // Pd-bar of the design (0 when overridden)
@@ -46,6 +48,8 @@ uint64_t splitmix64_at(uint64_t seed, uint64_t index);
 // Inverse of an odd sigma modulo 2^k by Newton iteration, reduced mod n.
 int64_t inverse_mod_pow2(int64_t sigma, int64_t n);
 
+// P(V > mu) for V ~ Binomial(L, p) (the binomial vote law of the second-stage design).
+double binomial_tail(int L, double p, int mu);
 // Dolph-Chebyshev window of length len, side lobes at -atten_db, peak 1.
 std::vector<double> chebyshev_window(int64_t len, double atten_db);
 // 6-dB bandwidth of a window in bins (bisection on the DTFT).

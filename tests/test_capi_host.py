@@ -65,6 +65,46 @@ def test_host_plan_matches_oracle(lib, c):
     assert abs(R.rsft_plan_get(p, R.RSFT_GET_ETA_M)[0] / op.eta_m - 1) < 1e-8
 
 
+BINOMIAL_CASES = [
+    dict(n=(1024, 256, 64), b=(64, 32, 8), loops=12, atten=80.0, k=32, pfa=1e-6),
+    dict(n=(256, 128, 16), b=(16, 8, 1), loops=10, atten=60.0, k=2, pfa=1e-5),
+    dict(n=(512, 512), b=(64, 64), loops=24, atten=60.0, k=40, pfa=1e-7),
+    dict(n=(64, 64), b=(8, 8), loops=255, atten=60.0, k=2, pfa=1e-6),
+]
+
+
+@pytest.mark.parametrize("c", BINOMIAL_CASES, ids=[str(c["n"]) + "_L" + str(c["loops"]) for c in BINOMIAL_CASES])
+def test_binomial_design_matches_oracle(lib, c):
+    """The binomial vote law of the threshold design: the host plan's (mu, Pfa1-bar, Pd-bar) are the
+    oracle's (an independent FP64 route: scipy's binomial tail against the library's log-space sum)."""
+    d = R.make_desc(c["n"], c["b"], c["loops"], atten_db=c["atten"], p_fa=c["pfa"], k_max=c["k"], seed=7,
+                    device=-1, design_mode=R.RSFT_DESIGN_BINOMIAL)
+    p = R.rsft_plan_create(d)
+    op = O.make_plan(c["n"], c["b"], c["loops"], seed=7, atten_db=c["atten"], p_fa=c["pfa"], k_max=c["k"],
+                     design_mode="binomial")
+    assert int(R.rsft_plan_get(p, R.RSFT_GET_MU)[0]) == op.mu
+    assert abs(R.rsft_plan_get(p, R.RSFT_GET_PFA1)[0] / op.pfa1 - 1) < 1e-8
+    assert abs(R.rsft_plan_get(p, R.RSFT_GET_PD_BAR)[0] / op.design["pd_bar"] - 1) < 1e-8
+    np.testing.assert_allclose(R.rsft_plan_get(p, R.RSFT_GET_GAMMA), op.gamma, rtol=1e-8)
+    normal = R.rsft_plan_create(R.make_desc(c["n"], c["b"], c["loops"], atten_db=c["atten"], p_fa=c["pfa"],
+                                            k_max=c["k"], seed=7, device=-1))
+    assert int(R.rsft_plan_get(p, R.RSFT_GET_MU)[0]) >= int(R.rsft_plan_get(normal, R.RSFT_GET_MU)[0])
+
+
+def test_estimate_mode_host_plan(lib):
+    """noise_var <= 0: the plan leaves the thresholds to each execute (NaN until then)."""
+    for nv in (0.0, -1.0):
+        p = R.rsft_plan_create(R.make_desc((64, 128), (16, 16), 6, p_fa1=0.02, mu=2, noise_var=nv, device=-1))
+        assert np.all(np.isnan(R.rsft_plan_get(p, R.RSFT_GET_GAMMA)))
+        assert np.all(np.isnan(R.rsft_plan_get(p, R.RSFT_GET_GAMMA_LAST)))
+        op = O.make_plan((64, 128), (16, 16), 6, pfa1=0.02, mu=2, noise_var=nv)
+        assert op.estimate_noise
+        np.testing.assert_allclose(R.rsft_plan_get(p, R.RSFT_GET_BETA), op.beta, rtol=1e-8)
+    known = R.rsft_plan_create(R.make_desc((64, 128), (16, 16), 6, p_fa1=0.02, mu=2, noise_var=2.0, device=-1))
+    np.testing.assert_array_equal(R.rsft_plan_get(known, R.RSFT_GET_GAMMA_LAST),
+                                  R.rsft_plan_get(known, R.RSFT_GET_GAMMA))
+
+
 def test_explicit_sigma_and_overrides(lib):
     sig = np.array([[3, 5], [7, 9], [1, 31]], dtype=np.int64)
     d = R.make_desc((32, 64), (4, 8), 3, sigma=sig, p_fa1=0.01, mu=1, noise_var=2.0, device=-1)
@@ -95,7 +135,9 @@ def test_design_snr_matches_oracle(lib):
     (dict(n=(32, 64), b=(4, 8), loops=256), R.RSFT_ERR_INVALID_ARG),      # votes overflow 8 bits
     (dict(n=(32, 64), b=(4, 8), loops=4, flat_support=(3, 0)), R.RSFT_ERR_INVALID_ARG),
     (dict(n=(32, 64), b=(4, 8), loops=4, mu=4, p_fa1=0.1), R.RSFT_ERR_INVALID_ARG),
-    (dict(n=(32, 64), b=(4, 8), loops=4, noise_var=0.0), R.RSFT_ERR_UNSUPPORTED),
+    (dict(n=(32, 64), b=(4, 8), loops=4, noise_var=float("nan")), R.RSFT_ERR_INVALID_ARG),
+    (dict(n=(32, 64), b=(4, 8), loops=4, noise_var=float("inf")), R.RSFT_ERR_INVALID_ARG),
+    (dict(n=(32, 64), b=(4, 8), loops=4, design_mode=7), R.RSFT_ERR_INVALID_ARG),
     (dict(n=(32, 64), b=(4, 8), loops=4, sigma=[[2, 3]] * 4), R.RSFT_ERR_INVALID_ARG),  # even sigma
     (dict(n=(64, 64), b=(4, 4), loops=12, k_max=64, p_fa=1e-9), R.RSFT_ERR_DESIGN),    # K eta_m >= B
 ])

@@ -69,10 +69,38 @@ def test_static_stage2_capacity_and_limits():
     torch.cuda.synchronize()
     assert int(count.item()) == cnt
     torch.testing.assert_close(loc, ref_loc[:cap], rtol=0, atol=0)
-    for bad_n in (total + 16, (1 << 28) + (1 << 14)):
-        with pytest.raises(R.RsftError) as ei:
-            R.rsft_stage2_static(v, bad_n, 3, loc, count)
-        assert ei.value.status == R.RSFT_ERR_INVALID_ARG
-    with pytest.raises(R.RsftError) as ei:
-        R.rsft_stage2_static(v, total, 255, loc, count)
-    assert ei.value.status == R.RSFT_ERR_INVALID_ARG
+
+    # capacity 0 and no output list: the full count is still written and the votes cleared
+    v = votes.clone()
+    count.zero_()
+    R.rsft_stage2_static(v, total, 3, None, count, capacity=0)
+    torch.cuda.synchronize()
+    assert int(count.item()) == cnt
+    assert int(v.count_nonzero().item()) == 0
+
+    # the binding refuses tensors shorter than n or the capacity before anything is launched
+    v = votes.clone()
+    with pytest.raises(ValueError):
+        R.rsft_stage2_static(v, total + 16384, 3, loc, count)
+    short_votes = torch.zeros(cap - 1 if cap > 1 else 0, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ValueError):
+        R.rsft_stage2_static(v, total, 3, loc, count, located_votes=short_votes)
+    with pytest.raises(ValueError):
+        R.rsft_stage2_static(v, total, 3, loc, count, capacity=cap + 1)
+    with pytest.raises(TypeError):
+        R.rsft_stage2_static(v.view(torch.int8), total, 3, loc, count)
+    with pytest.raises(TypeError):
+        R.rsft_stage2_static(v, total, 3, loc.view(torch.float64), count)
+    torch.testing.assert_close(v, votes, rtol=0, atol=0)     # nothing ran
+
+    # the C entry point's own limits, called directly (each is rejected on the host, before a launch)
+    lib = R.load_library()
+    stream = torch.cuda.current_stream().cuda_stream
+    for bad_n, bad_mu in ((total + 16, 3), ((1 << 28) + (1 << 14), 3), (total, 255), (0, 3)):
+        st = lib.rsft_stage2_static(v.data_ptr(), bad_n, bad_mu, loc.data_ptr(), None, cap, count.data_ptr(), stream)
+        assert st == R.RSFT_ERR_INVALID_ARG, (bad_n, bad_mu, st)
+    st = lib.rsft_stage2_static(v.data_ptr() + 1, total, 3, loc.data_ptr(), None, cap, count.data_ptr(), stream)
+    assert st == R.RSFT_ERR_INVALID_ARG                       # misaligned votes
+    st = lib.rsft_stage2_static(v.data_ptr(), total, 3, None, None, cap, count.data_ptr(), stream)
+    assert st == R.RSFT_ERR_INVALID_ARG                       # a capacity without a list
+    torch.testing.assert_close(v, votes, rtol=0, atol=0)
