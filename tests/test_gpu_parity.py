@@ -315,7 +315,7 @@ def test_parity_c5_sampled():
     Def. 3, located = votes > mu)."""
     name = "c5_4d"
     cube, tg, wl, nv = ri.workload_frame(name, 0)
-    d, op = make_pair(wl.shape, wl.buckets, wl.loops, seed=ri.frame_seed(wl, 0), atten_db=wl.atten_db,
+    d, op = make_pair(wl.shape, wl.buckets, wl.loops, seed=ri.frame_seed(wl, 0), atten=wl.atten_db,
                       noise_var=nv, p_fa=wl.p_fa, k_max=wl.k_design, max_located=1 << 22)
     g = gpu_run(d, cube, want_votes=True)
     compare_tables(g["plan"], op)
