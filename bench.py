@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--frames", type=int, default=4)
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", type=int, default=0,
+                    help="run this many plain executes of the workload and exit without a JSON line: the small, "
+                         "fixed command that the ncu captures under profiles/ are taken on")
     return ap.parse_args()
 
 
@@ -879,9 +882,36 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_profile(args):
+    """`--profile N`: N back-to-back rsft_execute_async calls over the workload's ring of frames
+    (headline plan), then exit.  The ring is the timed one (4 frames, larger than L2)."""
+    import torch
+    import paper_1610_01050_gb300 as R
+    from paper_1610_01050_gb300 import build as B
+    import rsft_inputs as ri
+    B.build()
+    R.load_library()
+    wl = ri.WORKLOADS[args.workload]
+    cubes, nv = [], wl.noise_var
+    for fid in range(max(1, args.frames)):
+        cube, _, _, nv = ri.workload_frame(args.workload, fid)
+        cubes.append(torch.from_numpy(cube).cuda())
+    plan = R.rsft_plan_create(workload_desc(R, wl, nv, ri.frame_seed(wl, 0)))
+    cap = 1 << 20
+    located = torch.zeros(cap, dtype=torch.int64, device="cuda")
+    amp = torch.zeros(cap, dtype=torch.complex64, device="cuda")
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for k in range(args.profile):
+        R.rsft_execute_async(plan, cubes[k % len(cubes)], count, located=located, amp=amp)
+    torch.cuda.synchronize()
+    plan.close()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile > 0:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -65,6 +65,7 @@ struct rsft_plan {
   int fold_copy_mode = -1;          // last fold launch: 0 per-row bulk copies, 3/5 tensor box rank,
                                     // 100 + rank on the tensor cores
   bool fold_tc = false;             // the fold runs on the tensor cores (fold_tc.cu)
+  bool fft_cluster = false;         // the bucket FFT runs as one cluster launch (else shared-memory passes)
   int64_t partial_cap = 0;          // elements of every workspace's fold partial-sum buffer
   int loop_group = rsft::kMaxLoopGroup;  // loops folded per pass over the cube
   int sms = 152;                    // streaming multiprocessors of the plan's device (schedule balance)
@@ -307,12 +308,14 @@ rsft_status build_fold_tables(rsft_plan* p, int group, const float4** ftable, co
     // layout [class group][row chunk][row][class in group][loop]: a stage's rows are contiguous
     const int64_t R = fs.rows_per_chunk, C = fs.cps;
     const int64_t tunits = static_cast<int64_t>(fs.groups) * fs.row_chunks;
-    std::vector<float4> ft(static_cast<size_t>(L) * tunits * R * C);
+    // schedules whose fold forms the row weights itself (wide chunk rows) need no row table
+    const bool row_table = rsft::fold_uses_row_table(fs);
+    std::vector<float4> ft(row_table ? static_cast<size_t>(L) * tunits * R * C : 0);
     std::vector<float2> fc(static_cast<size_t>(L) * fs.col_chunks * fs.width);
     for (int l0 = 0; l0 < L; l0 += group) {
       const int lg = std::min(group, L - l0);
       const size_t tbase = static_cast<size_t>(l0) * tunits * R * C;
-      for (int64_t e = 0; e < tunits * R * C; ++e) {
+      for (int64_t e = 0; row_table && e < tunits * R * C; ++e) {
         const int64_t ci = e % C, r = (e / C) % R, tu = e / (C * R);
         const int64_t cls = (tu / fs.row_chunks) * C + ci, rc = tu % fs.row_chunks;
         {
@@ -348,7 +351,7 @@ rsft_status build_fold_tables(rsft_plan* p, int group, const float4** ftable, co
           }
     }
     float4* f4 = nullptr;
-    if ((st = upload(p, &f4, ft)) != RSFT_OK) return st;
+    if (row_table && (st = upload(p, &f4, ft)) != RSFT_OK) return st;
     *ftable = f4;
     float2* f2p = nullptr;
     if ((st = upload(p, &f2p, fc)) != RSFT_OK) return st;
@@ -445,6 +448,11 @@ rsft_status build_device(rsft_plan* p) {
                  static_cast<int64_t>(8) * ((p->rows.n_in + 3) / 4) * 4 <= 200 * 1024;
   if (!plan_fft_passes(g, p->passes))
     return fail(RSFT_ERR_UNSUPPORTED, "a bucket dimension is too large for the shared-memory FFT");
+  {
+    // one cluster launch for the bucket FFT where the grid allows it; RSFT_FFT=passes keeps the passes
+    const char* env = std::getenv("RSFT_FFT");
+    p->fft_cluster = rsft::fft_cluster_size(g) > 0 && !(env && std::string(env) == "passes");
+  }
 
   const int L = h.loops, D = h.ndim;
   rsft_status st;
@@ -616,7 +624,8 @@ void drain_timing(rsft_plan* p) {
 
 int launches_per_execute(const rsft_plan* p) {
   const int groups = (p->geom.loops + p->loop_group - 1) / p->loop_group;
-  return groups * (p->fold.direct ? 1 : 2) + static_cast<int>(p->passes.size()) + (p->host.estimate_noise ? 1 : 0) +
+  return groups * (p->fold.direct ? 1 : 2) + (p->fft_cluster ? 1 : static_cast<int>(p->passes.size())) +
+         (p->host.estimate_noise ? 1 : 0) +
          (p->rows_mode ? 3 : 4) + 1;
 }
 
@@ -693,10 +702,16 @@ rsft_status run_lane(rsft_plan* p, rsft::Workspace& ws, bool& votes_dirty, bool 
   }
   mark(1);
   const bool estimate = p->host.estimate_noise;
-  for (size_t i = 0; i < p->passes.size(); ++i) {
-    e = rsft::launch_fft_pass(g, p->passes[i], p->tables, i == 0 ? ws.folded : ws.spectrum, ws.spectrum,
-                              ws.det_bits, ws.det_count, ws.words_b, !estimate, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "bucket_fft/np_detect");
+  if (p->fft_cluster) {
+    e = rsft::launch_fft_cluster(g, p->tables, ws.folded, ws.spectrum, ws.det_bits, ws.det_count, ws.words_b,
+                                 !estimate, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "bucket_fft/np_detect (cluster)");
+  } else {
+    for (size_t i = 0; i < p->passes.size(); ++i) {
+      e = rsft::launch_fft_pass(g, p->passes[i], p->tables, i == 0 ? ws.folded : ws.spectrum, ws.spectrum,
+                                ws.det_bits, ws.det_count, ws.words_b, !estimate, stream);
+      if (e != cudaSuccess) return cuda_fail(e, "bucket_fft/np_detect");
+    }
   }
   if (estimate) {
     // noise floor of each loop from its own bucket powers, then the detection against it

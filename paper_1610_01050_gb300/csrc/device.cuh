@@ -176,6 +176,12 @@ cudaError_t launch_fold_reduce(const Geometry& g, const FoldSchedule& fs, const 
 cudaError_t launch_fft_pass(const Geometry& g, const FftPass& ps, const DeviceTables& t,
                             const float2* in, float2* out, uint32_t* det_bits, uint32_t* det_count,
                             int64_t words_b, bool detect, cudaStream_t stream);
+// The whole N-D bucket FFT of every loop in one launch: C CTAs per loop in a thread-block cluster
+// (fft_cluster_size: 0 when the bucket grid does not allow it), detection fused when `detect`.
+int fft_cluster_size(const Geometry& g);
+cudaError_t launch_fft_cluster(const Geometry& g, const DeviceTables& t, const float2* in, float2* out,
+                               uint32_t* det_bits, uint32_t* det_count, int64_t words_b, bool detect,
+                               cudaStream_t stream);
 // Estimate mode of the first stage: per loop, gamma_l = lowermedian(|f-hat_l|^2) * factor (written to
 // gamma_out[l]) and the loop's detection bitmap and count against it.
 cudaError_t launch_noise_floor(const Geometry& g, const float2* spectrum, float factor, float* gamma_out,
@@ -200,6 +206,9 @@ cudaError_t vote_rows_small_residency(const Geometry& g, const VoteRowSchedule& 
                                       int* warps_per_sm);
 
 int fold_smem_bytes(const Geometry& g, const FoldSchedule& fs, int lg);
+// Whether the SIMT fold of this schedule reads the precomputed row table (narrow chunk rows) or
+// forms each row weight from the per-dimension tables (rows of 64 or more columns).
+bool fold_uses_row_table(const FoldSchedule& fs);
 // One CTA waits on a barrier that never completes, through the fold's bounded wait with the
 // given limit; *err is set to 1 when the wait gives up.
 cudaError_t launch_wait_selftest(int* err, uint64_t limit_ns, cudaStream_t stream);

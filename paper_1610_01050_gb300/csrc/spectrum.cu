@@ -12,13 +12,27 @@
 // exactly by a radix select on the powers' bit patterns (non-negative floats
 // order as their unsigned bits), then the loop's buckets are tested against it.
 //
+// Cluster form (one launch, used when the bucket grid allows): the C CTAs of a thread-block
+// cluster share one loop's B buckets.  CTA c loads rows [c B_0 / C, (c + 1) B_0 / C) of the
+// first dimension and transforms dimensions 1..D-1 of its rows in its own shared memory; after
+// a cluster barrier it gathers, through distributed shared memory, the columns
+// [c S / C, (c + 1) S / C) of all B_0 rows (S = B / B_0) and transforms dimension 0, then writes
+// the spectrum and the detection bits of its columns.  Every transform is radix-2
+// decimation in time: the bit reversal is applied where the data is stored into shared memory,
+// so each stage is one pass of butterflies between barriers.  With C = 1 one CTA does every
+// dimension of its loop in place.
+//
 // A pass transforms dimensions [da, db) of a slab held in shared memory: the
 // slab is `opc` consecutive outer indices x all group indices x `width`
 // consecutive inner indices.  Each dimension is an in-place radix-2 DIT
 // transform (bit reversal, then log2 B_d butterfly stages) with FP64-derived
 // twiddles.  The last pass always holds the last dimension, so its slabs are
 // contiguous bucket ranges and detection bits are formed by warp ballots.
+#include <cooperative_groups.h>
+
 #include "device.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace rsft {
 namespace {
@@ -149,6 +163,144 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const FftArgs a) 
   }
 }
 
+struct ClusterFftArgs {
+  Geometry g;
+  DeviceTables t;
+  const float2* in;      // [L][B] folded buckets
+  float2* out;           // [L][B] spectrum
+  uint32_t* det_bits;
+  uint32_t* det_count;
+  int64_t words_b;
+  int csize;             // C: CTAs per loop (a cluster)
+  int detect;
+};
+
+// Reverse the bits of each dimension's digit of a row-major index over dimensions [d0, D).
+__device__ __forceinline__ uint32_t digit_reverse(uint32_t q, const Geometry& g, int d0) {
+  uint32_t out = 0u;
+  int shift = 0;
+#pragma unroll
+  for (int d = kMaxDim - 1; d >= 0; --d) {
+    if (d < d0 || d >= g.ndim) continue;
+    const int lb = g.log_b[d];
+    const uint32_t dig = (q >> shift) & ((1u << lb) - 1u);
+    out |= (lb ? (__brev(dig) >> (32 - lb)) : 0u) << shift;
+    shift += lb;
+  }
+  return out | ((q >> shift) << shift);  // digits of dimensions below d0 pass through
+}
+
+// All radix-2 decimation-in-time stages of dimension d (size n = 2^ln, element stride 2^lst) of an
+// E-element shared-memory buffer whose input along d is in bit-reversed order.
+__device__ __forceinline__ void dit_dimension(float2* buf, uint32_t E, int ln, int lst, const float2* __restrict__ tw) {
+  const uint32_t half = E >> 1;
+  for (int lh = 0; lh < ln; ++lh) {
+    for (uint32_t bf = threadIdx.x; bf < half; bf += blockDim.x) {
+      const uint32_t low = bf & ((1u << lst) - 1u);
+      const uint32_t t = bf >> lst;
+      const uint32_t b = t & ((1u << (ln - 1)) - 1u);
+      const uint32_t line = t >> (ln - 1);
+      const uint32_t pos = b & ((1u << lh) - 1u);
+      const uint32_t grp = b >> lh;
+      const uint32_t i0 = (((line << ln) + (grp << (lh + 1)) + pos) << lst) + low;
+      const uint32_t i1 = i0 + (1u << (lh + lst));
+      const float2 w = __ldg(tw + (pos << (ln - 1 - lh)));
+      const float2 x0 = buf[i0], x1 = buf[i1];
+      const float2 y = make_float2(x1.x * w.x - x1.y * w.y, x1.x * w.y + x1.y * w.x);
+      buf[i0] = make_float2(x0.x + y.x, x0.y + y.y);
+      buf[i1] = make_float2(x0.x - y.x, x0.y - y.y);
+    }
+    __syncthreads();
+  }
+}
+
+// Spectrum and detections of the E buffer elements of a CTA: element e is row e >> lq (of 2^lq
+// elements each) and column e & (2^lq - 1) of the CTA's column block, i.e. bucket
+// ((e >> lq) << lS) + col0 + (e & (2^lq - 1)) of loop l.  Rows of at least 32 elements keep a
+// warp's 32 consecutive elements on one aligned detection word.
+__device__ __forceinline__ void store_block(const ClusterFftArgs& a, int l, const float2* src, uint32_t E, int lq,
+                                            int lS, uint32_t col0, float gamma, uint32_t* hits) {
+  float2* dst = a.out + static_cast<int64_t>(l) * a.g.total_b;
+  uint32_t* bits = a.det_bits + static_cast<int64_t>(l) * a.words_b;
+  const int lane = threadIdx.x & 31;
+  const uint32_t qmask = (1u << lq) - 1u;
+  for (uint32_t e0 = 0; e0 < E; e0 += blockDim.x) {
+    const uint32_t e = e0 + threadIdx.x;
+    const uint32_t k = ((e >> lq) << lS) + col0 + (e & qmask);
+    bool hit = false;
+    if (e < E) {
+      const float2 v = src[e];
+      dst[k] = v;
+      hit = a.detect && bucket_power(v) > gamma;
+    }
+    if (!a.detect) continue;
+    const unsigned ballot = __ballot_sync(0xffffffffu, hit);
+    if (lane == 0 && ballot) {
+      const uint32_t kw = k;                 // bucket of lane 0
+      if ((kw & 31u) == 0u && (qmask >= 31u || E <= 32u)) {
+        atomicOr(bits + (kw >> 5), ballot);
+      } else {
+        for (int i = 0; i < 32; ++i)
+          if ((ballot >> i) & 1u) {
+            const uint32_t ki = (((e + i) >> lq) << lS) + col0 + ((e + i) & qmask);   // lane 0: e is lane 0's
+            atomicOr(bits + (ki >> 5), 1u << (ki & 31u));
+          }
+      }
+      atomicAdd(hits, static_cast<uint32_t>(__popc(ballot)));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(512) fft_cluster_kernel(const ClusterFftArgs a) {
+  extern __shared__ __align__(16) float2 sbuf[];
+  __shared__ uint32_t hits;
+  const Geometry& g = a.g;
+  const int C = a.csize;
+  const int l = static_cast<int>(blockIdx.x) / C;
+  const uint32_t c = blockIdx.x % C;           // rank in the cluster (clusters run along x)
+  const uint32_t B = static_cast<uint32_t>(g.total_b);
+  const uint32_t E = B / C;                     // this CTA's elements in each phase
+  const uint32_t S = B >> g.log_b[0];           // elements of one row of dimension 0
+  const int lS = 31 - __clz(S);
+  const float2* src = a.in + static_cast<int64_t>(l) * B + static_cast<int64_t>(c) * E;
+  const int d_first = C == 1 ? 0 : 1;           // dimensions transformed in place
+  if (threadIdx.x == 0) hits = 0u;
+  // phase 1: rows [c E / S, (c + 1) E / S) of the loop, bit-reversed along dimensions d_first..D-1
+  for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) sbuf[digit_reverse(e, g, d_first)] = src[e];
+  __syncthreads();
+  for (int d = g.ndim - 1; d >= d_first; --d)
+    if (g.log_b[d] > 0)
+      dit_dimension(sbuf, E, g.log_b[d], g.b_shift[d], a.t.twiddle[d]);
+  const float gamma = a.detect ? a.t.gamma[l] : 0.f;
+  if (C == 1) {
+    const int lB = 31 - __clz(B);                // the loop as one row: bucket k = e
+    store_block(a, l, sbuf, B, lB, lB, 0u, gamma, &hits);
+  } else {
+    // phase 2: columns [c Q, (c + 1) Q) of every row of dimension 0, from the cluster's shared memory
+    cg::cluster_group cluster = cg::this_cluster();
+    cluster.sync();                              // every CTA's phase-1 rows are complete and visible
+    const uint32_t Q = S / C;
+    const uint32_t rows_per = E >> lS;           // rows of dimension 0 held by each CTA
+    const int lq = 31 - __clz(Q);
+    const int lb0 = g.log_b[0];
+    float2* gbuf = sbuf + E;
+    for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) {
+      const uint32_t row = e >> lq, q = e & (Q - 1u);
+      const uint32_t owner = row / rows_per;
+      const float2* remote = cluster.map_shared_rank(sbuf, owner);
+      const uint32_t rrev = lb0 ? (__brev(row) >> (32 - lb0)) : 0u;
+      gbuf[(rrev << lq) + q] = remote[((row - owner * rows_per) << lS) + c * Q + q];
+    }
+    cluster.sync();                              // no CTA leaves while others still read its rows
+    if (lb0 > 0) dit_dimension(gbuf, E, lb0, lq, a.t.twiddle[0]);
+    store_block(a, l, gbuf, E, lq, lS, c * Q, gamma, &hits);
+  }
+  if (a.detect) {
+    __syncthreads();
+    if (threadIdx.x == 0 && hits) atomicAdd(a.det_count + l, hits);
+  }
+}
+
 struct FloorArgs {
   const float2* spectrum;  // [L][B]
   int64_t total_b;
@@ -276,6 +428,60 @@ cudaError_t launch_noise_floor(const Geometry& g, const float2* spectrum, float 
   }
   noise_floor_kernel<<<g.loops, kFloorThreads, smem, stream>>>(args);
   return cudaGetLastError();
+}
+
+int fft_cluster_size(const Geometry& g) {
+  const int64_t B = g.total_b;
+  const int64_t S = B / g.b[0];
+  if (B < 2 || B > (int64_t(1) << 20)) return 0;
+  int64_t c = B / 2048;  // about 2048 buckets per CTA
+  if (c < 1) c = 1;
+  while (c > 8 || c > g.b[0] || c > S) c >>= 1;
+  for (; c > 1; c >>= 1)
+    if (B / c <= 8192 && S / c >= 32) return static_cast<int>(c);  // two buffers of B / C; whole detection words
+  return B <= 16384 ? 1 : 0;                   // one CTA holds the loop in place (128 KiB)
+}
+
+cudaError_t launch_fft_cluster(const Geometry& g, const DeviceTables& t, const float2* in, float2* out,
+                               uint32_t* det_bits, uint32_t* det_count, int64_t words_b, bool detect,
+                               cudaStream_t stream) {
+  const int csize = fft_cluster_size(g);
+  if (csize < 1) return cudaErrorInvalidConfiguration;
+  ClusterFftArgs args;
+  args.g = g;
+  args.t = t;
+  args.in = in;
+  args.out = out;
+  args.det_bits = det_bits;
+  args.det_count = det_count;
+  args.words_b = words_b;
+  args.csize = csize;
+  args.detect = detect ? 1 : 0;
+  const int64_t E = g.total_b / csize;
+  const int smem = static_cast<int>(E * sizeof(float2) * (csize > 1 ? 2 : 1));
+  static int set_smem[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 64 || set_smem[dev] < smem) {
+    e = cudaFuncSetAttribute(fft_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem > 48 * 1024 ? smem : 48 * 1024);
+    if (e != cudaSuccess) return e;
+    if (dev < 64) set_smem[dev] = smem;
+  }
+  const int threads = E >= 2048 ? 512 : 256;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(g.loops * csize));
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = static_cast<size_t>(smem);
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = static_cast<unsigned>(csize);
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fft_cluster_kernel, args);
 }
 
 cudaError_t launch_fft_pass(const Geometry& g, const FftPass& ps, const DeviceTables& t,
