@@ -308,14 +308,12 @@ rsft_status build_fold_tables(rsft_plan* p, int group, const float4** ftable, co
     // layout [class group][row chunk][row][class in group][loop]: a stage's rows are contiguous
     const int64_t R = fs.rows_per_chunk, C = fs.cps;
     const int64_t tunits = static_cast<int64_t>(fs.groups) * fs.row_chunks;
-    // schedules whose fold forms the row weights itself (wide chunk rows) need no row table
-    const bool row_table = rsft::fold_uses_row_table(fs);
-    std::vector<float4> ft(row_table ? static_cast<size_t>(L) * tunits * R * C : 0);
+    std::vector<float4> ft(static_cast<size_t>(L) * tunits * R * C);
     std::vector<float2> fc(static_cast<size_t>(L) * fs.col_chunks * fs.width);
     for (int l0 = 0; l0 < L; l0 += group) {
       const int lg = std::min(group, L - l0);
       const size_t tbase = static_cast<size_t>(l0) * tunits * R * C;
-      for (int64_t e = 0; row_table && e < tunits * R * C; ++e) {
+      for (int64_t e = 0; e < tunits * R * C; ++e) {
         const int64_t ci = e % C, r = (e / C) % R, tu = e / (C * R);
         const int64_t cls = (tu / fs.row_chunks) * C + ci, rc = tu % fs.row_chunks;
         {
@@ -351,7 +349,7 @@ rsft_status build_fold_tables(rsft_plan* p, int group, const float4** ftable, co
           }
     }
     float4* f4 = nullptr;
-    if (row_table && (st = upload(p, &f4, ft)) != RSFT_OK) return st;
+    if ((st = upload(p, &f4, ft)) != RSFT_OK) return st;
     *ftable = f4;
     float2* f2p = nullptr;
     if ((st = upload(p, &f2p, fc)) != RSFT_OK) return st;

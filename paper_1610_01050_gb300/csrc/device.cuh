@@ -206,9 +206,6 @@ cudaError_t vote_rows_small_residency(const Geometry& g, const VoteRowSchedule& 
                                       int* warps_per_sm);
 
 int fold_smem_bytes(const Geometry& g, const FoldSchedule& fs, int lg);
-// Whether the SIMT fold of this schedule reads the precomputed row table (narrow chunk rows) or
-// forms each row weight from the per-dimension tables (rows of 64 or more columns).
-bool fold_uses_row_table(const FoldSchedule& fs);
 // One CTA waits on a barrier that never completes, through the fold's bounded wait with the
 // given limit; *err is set to 1 when the wait gives up.
 cudaError_t launch_wait_selftest(int* err, uint64_t limit_ns, cudaStream_t stream);

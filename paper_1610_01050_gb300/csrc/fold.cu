@@ -69,9 +69,6 @@ struct FoldArgs {
   float2* partial;
   int* err;
   const float4* table;    // this loop group's row table: [group][row chunk][row][class][lg] (d - c, c + d, c, c)
-  const float2* wrow[kMaxDim];  // per-dimension weights a_{l,d}(s) [L][N_d] (computed-weight schedules)
-  int computed;           // 1: row weights formed per warp in shared memory (fold_weights_computed)
-  int wbuf_off;           // computed weights: per-warp buffers [warps][row steps][lg] float4 (bytes)
   const float2* colw;     // this loop group's column weights: [col chunk][lg][W]
   int smem_colw;          // one column chunk: its weights staged in shared memory once
   int ring;               // stages in the ring
@@ -110,19 +107,10 @@ constexpr int kRedCap = 24 * 1024;  // epilogue partials: loops go through in pa
 
 // Shared memory: [ring x (stage data | stage row table)] [column weights] [epilogue partials] [barriers].
 // The partials hold lch loops at a time (all of them unless that would pass kRedCap).
-// Row weights formed in shared memory instead of streamed from the row table: schedules whose
-// chunk rows are at least 64 columns wide, so a warp's threads share one row slot per step and a
-// weight is used by 32 threads (each warp forms its own slot's weights from the per-dimension
-// tables, which stay in L1).  Narrower rows read the precomputed table.
-__host__ __device__ __forceinline__ bool fold_weights_computed(const FoldSchedule& fs) { return fs.width >= 64; }
-
 __host__ __device__ __forceinline__ int fold_layout(const FoldSchedule& fs, int lg, int* ring, int* slot_bytes,
-                                                    int* colw_off, int* red_off, int* bar_off, int* lch,
-                                                    int* wbuf_off = nullptr) {
+                                                    int* colw_off, int* red_off, int* bar_off, int* lch) {
   const StageShape sh = stage_shape(fs, lg);
-  const bool computed = fold_weights_computed(fs);
-  *slot_bytes = kStageBytes + (computed ? 0 : sh.table_bytes);
-  const int wbuf = computed ? kWarps * sh.spst * lg * 16 : 0;
+  *slot_bytes = kStageBytes + sh.table_bytes;
   const int colw = colw_staged(fs, lg) ? lg * fs.width * 8 : 0;
   const int red_loop = kWarps * fs.leaders * 2 * 8;
   int lc = kRedCap / red_loop;
@@ -131,13 +119,11 @@ __host__ __device__ __forceinline__ int fold_layout(const FoldSchedule& fs, int 
   *lch = lc;
   const int red = red_loop * lc;
   const int bars = (kMaxRing + 1) * 8 + kMaxRing * 4 + 16;
-  int r = (kSmemBudget - colw - red - bars - wbuf) / *slot_bytes;
+  int r = (kSmemBudget - colw - red - bars) / *slot_bytes;
   if (r > kMaxRing) r = kMaxRing;
   if (r < 2) r = 2;
   *ring = r;
   int off = r * *slot_bytes;
-  if (wbuf_off) *wbuf_off = off;
-  off += wbuf;
   *colw_off = off;
   off += colw;
   *red_off = off;
@@ -152,7 +138,7 @@ __host__ __device__ __forceinline__ int fold_layout(const FoldSchedule& fs, int 
 // next unit's rows arrive during this unit's epilogue): the last warp to finish with stage i
 // (a shared-memory count per slot) issues stage i + ring into the same slot.  Each stage
 // brings its rows and their row-table slice.
-template <int LG, bool CHUNK, bool COMPUTED>
+template <int LG, bool CHUNK>
 __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant__ FoldArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const Geometry& g = a.g;
@@ -201,12 +187,11 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
     const int slot = i % ring;
     unsigned char* base = smem + slot * a.slot_bytes;
     float2* dst = reinterpret_cast<float2*>(base);
-    mbar_arrive_expect_tx(full + slot, static_cast<uint32_t>(sh.data_bytes + (COMPUTED ? 0 : sh.table_bytes)));
+    mbar_arrive_expect_tx(full + slot, static_cast<uint32_t>(sh.data_bytes + sh.table_bytes));
     const int r0 = rc * R + k * spst * fs.crow;  // first row (within each class) of the stage
-    if (!COMPUTED)
-      bulk_g2s(base + kStageBytes,
-               a.table + ((static_cast<int64_t>(u / chunks) * fs.row_chunks + rc) * R + k * spst * fs.crow) * C * LG,
-               static_cast<uint32_t>(sh.table_bytes), full + slot, pol_keep);
+    bulk_g2s(base + kStageBytes,
+             a.table + ((static_cast<int64_t>(u / chunks) * fs.row_chunks + rc) * R + k * spst * fs.crow) * C * LG,
+             static_cast<uint32_t>(sh.table_bytes), full + slot, pol_keep);
     if (a.tensor_rank == 3) {
       tensor_g2s_3d(dst, &a.tmap, cc * W, cls0 & static_cast<int>(g.b[0] - 1), r0, full + slot, pol_stream);
     } else if (a.tensor_rank == 5) {
@@ -252,7 +237,6 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
   const int cp = (2 * pq) & (W - 1);
   const int ro = (2 * pq) >> a.log_width;
   const bool active = ro < RS;
-  float4* wbuf = reinterpret_cast<float4*>(smem + a.wbuf_off) + warp * (spst * LG);  // this warp's weights
   bool ok = true;
   if (smem_colw) ok = mbar_wait(cbar, 0u, abort_flag, a.err);
 
@@ -290,36 +274,11 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
       k3[l] = make_float2(0.f, 0.f);
     }
     for (int k = 0; k < nst; ++k, ++i) {
-      if (COMPUTED && active) {
-        // this warp's row slot ro: the weight of each of the stage's row steps and loops, the product of
-        // the row dimensions' a_{l,d}(s_d) (s_d = x_d + B_d m_d), as (d - c, c + d, c, c)
-        const int cls = cls0 + ro % C;
-        const int rbase = rc * R + k * spst * fs.crow + ro / C;
-        for (int e = lane; e < spst * LG; e += 32) {
-          const int step = e / LG, l = e - step * LG;
-          int r = rbase + step * fs.crow, cres = cls;
-          float2 w = make_float2(1.f, 0.f);
-#pragma unroll
-          for (int d = kMaxDim - 1; d >= 0; --d) {
-            if (d < fs.d_in) {
-              const int md = r & static_cast<int>(g.m[d] - 1);
-              r >>= g.log_m[d];
-              const int xd = cres & static_cast<int>(g.b[d] - 1);
-              cres >>= g.log_b[d];
-              const float2 f = __ldg(a.wrow[d] + static_cast<int64_t>(a.loop0 + l) * g.n[d] + xd + (md << g.log_b[d]));
-              w = cmul(w, f);
-            }
-          }
-          wbuf[e] = make_float4(w.y - w.x, w.x + w.y, w.x, w.x);
-        }
-        __syncwarp();
-      }
       if (ok && !mbar_try_wait(full + slot, parity) && !mbar_wait(full + slot, parity, abort_flag, a.err)) ok = false;
       if (ok && active) {
         const float4* src = reinterpret_cast<const float4*>(smem + slot * a.slot_bytes) + pq;
         // row-table entries (d - c, c + d, c, c): pairs for the paired multiply-adds
-        const float4* tr = COMPUTED ? wbuf : reinterpret_cast<const float4*>(smem + slot * a.slot_bytes + kStageBytes) + ro * LG;
-        const int tstep = COMPUTED ? LG : RS * LG;   // entries per row step
+        const float4* tr = reinterpret_cast<const float4*>(smem + slot * a.slot_bytes + kStageBytes) + ro * LG;
 #pragma unroll
         for (int step = 0; step < kStepsPerStage; ++step) {
           if (step < spst) {
@@ -328,7 +287,7 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
             const float2 ss = make_float2(v.x + v.y, v.z + v.w);                  // (a + b) of both
 #pragma unroll
             for (int l = 0; l < LG; ++l) {
-              const float4 w = tr[step * tstep + l];
+              const float4 w = tr[step * RS * LG + l];
               k12a[l] = __ffma2_rn(make_float2(w.x, w.y), x0, k12a[l]);  // (K2, K3), column cp
               k12b[l] = __ffma2_rn(make_float2(w.x, w.y), x1, k12b[l]);  // (K2, K3), column cp + 1
               k3[l] = __ffma2_rn(make_float2(w.z, w.w), ss, k3[l]);      // K1 of both columns
@@ -475,18 +434,18 @@ __global__ void fold_reduce_kernel(const ReduceArgs a) {
   }
 }
 
-template <int LG, bool CHUNK, bool COMPUTED>
-cudaError_t launch_fold_lgc(const FoldArgs& args, int smem, cudaStream_t stream) {
+template <int LG, bool CHUNK>
+cudaError_t launch_fold_lg(const FoldArgs& args, int smem, cudaStream_t stream) {
   static int cached_smem[64] = {0};
   static int cached_grid[64] = {0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 64 || cached_smem[dev] != smem) {
-    e = cudaFuncSetAttribute(fold_kernel<LG, CHUNK, COMPUTED>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(fold_kernel<LG, CHUNK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fold_kernel<LG, CHUNK, COMPUTED>, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fold_kernel<LG, CHUNK>, kThreads, smem);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -498,14 +457,8 @@ cudaError_t launch_fold_lgc(const FoldArgs& args, int smem, cudaStream_t stream)
   const int units = args.fs.groups * args.fs.row_chunks * args.fs.col_chunks;
   const int resident = dev < 64 ? cached_grid[dev] : 2 * 152;
   const int grid = units < resident ? units : resident;
-  fold_kernel<LG, CHUNK, COMPUTED><<<grid, kThreads, smem, stream>>>(args);
+  fold_kernel<LG, CHUNK><<<grid, kThreads, smem, stream>>>(args);
   return cudaGetLastError();
-}
-
-template <int LG, bool CHUNK>
-cudaError_t launch_fold_lg(const FoldArgs& args, int smem, cudaStream_t stream) {
-  return args.computed ? launch_fold_lgc<LG, CHUNK, true>(args, smem, stream)
-                       : launch_fold_lgc<LG, CHUNK, false>(args, smem, stream);
 }
 
 // One CTA waits, through the fold's bounded barrier wait, on a barrier that nothing
@@ -529,8 +482,6 @@ cudaError_t launch_wait_selftest(int* err, uint64_t limit_ns, cudaStream_t strea
   wait_selftest_kernel<<<1, 32, 0, stream>>>(err, limit_ns);
   return cudaGetLastError();
 }
-
-bool fold_uses_row_table(const FoldSchedule& fs) { return !fold_weights_computed(fs); }
 
 int fold_smem_bytes(const Geometry& g, const FoldSchedule& fs, int lg) {
   (void)g;
@@ -627,9 +578,7 @@ cudaError_t launch_fold(const Geometry& g, const FoldSchedule& fs, const DeviceT
   for (int i = 0; i < nslots && i < 512; ++i) args.slots[i] = t.h_slots[i];
   for (int i = 0; i < fs.xcount * 4 && i < 2048; ++i) args.xdig[i] = t.h_xdig[i];
   const int smem = fold_layout(fs, lg, &args.ring, &args.slot_bytes, &args.colw_off, &args.red_off, &args.bar_off,
-                               &args.lch, &args.wbuf_off);
-  args.computed = fold_weights_computed(fs) ? 1 : 0;
-  for (int d = 0; d < kMaxDim; ++d) args.wrow[d] = t.wtab[d];
+                               &args.lch);
   // the epilogue partials of at most 6 loops always fit: multi-pass kernels only above that
   const bool chunk = args.lch < lg;
   switch (lg) {
