@@ -529,14 +529,18 @@ MIXED = ("c3_small", "c3_mid", "c3_large")
 MIXED_CAP = 1 << 17
 
 
-def mixed_batch(R, torch, ri, dev, ws, stream, n_frames=512, per_shape=2, lanes=4, chunk=64):
+def mixed_batch(R, torch, ri, dev, ws, stream, n_frames=512, per_shape=2, lanes=4, chunk=64, group=16):
     """Batched frames of uneven shapes: 512 frames drawn uniformly from the three sizes of the
     mixed-size workload, each shape with its own plan (fold schedule picked by
-    rsft_plan_autotune on one of its frames) and every frame one recorded execute (a CUDA
-    graph) on one of 4 lanes of its plan, launched in chunks with rsft_graph_launch_batch.
-    The same sequence through rsft_execute_async on one stream is the plain comparison."""
+    rsft_plan_autotune on one of its frames).  Headline form: each shape's frames go 16 at a time
+    through one launch per stage (rsft_execute_frames), recorded as CUDA graphs
+    (rsft_graph_create_frames) and launched together, so the three shapes' graphs overlap.  Also
+    timed: every frame its own recorded execute over 4 lanes per plan, and the same sequence
+    through rsft_execute_async on one stream."""
     rng = np.random.default_rng(1610)
-    plans, rings, graphs, outs, tuned = {}, {}, {}, [], {}
+    shape_of = [MIXED[i] for i in rng.integers(0, len(MIXED), n_frames)]
+    counts_by = {n: sum(1 for x in shape_of if x == n) for n in MIXED}
+    plans, rings, graphs, outs, tuned, fgraphs, together = {}, {}, {}, [], {}, {}, {}
     for name in MIXED:
         wl = ri.WORKLOADS[name]
         cubes, nv = [], wl.noise_var
@@ -549,13 +553,24 @@ def mixed_batch(R, torch, ri, dev, ws, stream, n_frames=512, per_shape=2, lanes=
                                                 design=R.RSFT_DESIGN_NORMAL))
         us, chosen = R.rsft_plan_autotune(plan, cubes[0], candidates=4, reps=5, stream=stream)
         tuned[name] = {"fold_us": us, "candidate": chosen}
+        together[name] = R.rsft_plan_frames_together(plan)
         plans[name], rings[name], graphs[name] = plan, cubes, []
         for g in range(lanes):  # graph g: resident frame g % per_shape on lane g
             o = (torch.zeros(MIXED_CAP, dtype=torch.int64, device=dev),
                  torch.zeros(MIXED_CAP, dtype=torch.complex64, device=dev), torch.zeros(1, dtype=torch.int64, device=dev))
             outs.append(o)
             graphs[name].append(R.rsft_graph_create(plan, cubes[g % per_shape], o[2], located=o[0], amp=o[1], lane=g))
-    shape_of = [MIXED[i] for i in rng.integers(0, len(MIXED), n_frames)]
+        # frames form: one graph of `group` frames (resident frames in turn) and one of the remainder
+        fgraphs[name] = []
+        for size in (group, counts_by[name] % group):
+            if size == 0:
+                continue
+            o = (torch.zeros(size * MIXED_CAP, dtype=torch.int64, device=dev),
+                 torch.zeros(size * MIXED_CAP, dtype=torch.complex64, device=dev),
+                 torch.zeros(size, dtype=torch.int64, device=dev))
+            outs.append(o)
+            fgraphs[name].append(R.rsft_graph_create_frames(plan, [cubes[k % per_shape] for k in range(size)], o[2],
+                                                            located=o[0], amp=o[1]))
     seen = {n: 0 for n in MIXED}
     seq, plain = [], []
     for name in shape_of:
@@ -563,6 +578,14 @@ def mixed_batch(R, torch, ri, dev, ws, stream, n_frames=512, per_shape=2, lanes=
         seen[name] += 1
         seq.append(graphs[name][k % lanes])
         plain.append((plans[name], rings[name][k % lanes % per_shape]))
+    # frames form: each shape's full groups then its remainder, the shapes interleaved
+    per_shape_seq = {n: [fgraphs[n][0]] * (counts_by[n] // group) + (fgraphs[n][1:] if counts_by[n] % group else [])
+                     for n in MIXED}
+    fseq = []
+    while any(per_shape_seq.values()):
+        for n in MIXED:
+            if per_shape_seq[n]:
+                fseq.append(per_shape_seq[n].pop(0))
     frame_bytes = sum(int(np.prod(ri.WORKLOADS[n].shape)) * 8 for n in shape_of)
 
     def run_graphs(frames):
@@ -578,31 +601,38 @@ def mixed_batch(R, torch, ri, dev, ws, stream, n_frames=512, per_shape=2, lanes=
             R.rsft_execute_async(plan, x, count, stream=stream, located=loc, amp=amp)
 
     run_graphs(seq[:2 * chunk])
+    run_graphs(fseq)
     run_plain(plain[:16])
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     ev[0].record(stream)
-    run_graphs(seq)
+    R.rsft_graph_launch_batch(fseq, stream=stream)
     ev[1].record(stream)
-    run_plain(plain)
+    run_graphs(seq)
     ev[2].record(stream)
+    run_plain(plain)
+    ev[3].record(stream)
     torch.cuda.synchronize()
     ms = max_over_ranks(ev[0].elapsed_time(ev[1]), ws, dev)
-    ms_plain = max_over_ranks(ev[1].elapsed_time(ev[2]), ws, dev)
+    ms_graphs = max_over_ranks(ev[1].elapsed_time(ev[2]), ws, dev)
+    ms_plain = max_over_ranks(ev[2].elapsed_time(ev[3]), ws, dev)
     for name in MIXED:
-        for g in graphs[name]:
+        for g in graphs[name] + fgraphs[name]:
             g.close()
         plans[name].close()
     value = whole_job_rate(ws, n_frames, ms)
     return {"value": value, "unit": "frames/s", "frames": n_frames,
-            "shapes": {n: int(sum(1 for x in shape_of if x == n)) for n in MIXED},
+            "shapes": counts_by, "frames_together": together,
             "ms_per_frame": ms / n_frames, "hbm_gbs_cube_reads": frame_bytes / (ms / 1e3) / 1e9,
+            "per_frame_graphs": {"value": whole_job_rate(ws, n_frames, ms_graphs), "unit": "frames/s",
+                                 "note": f"every frame one recorded execute, over {lanes} lanes per plan"},
             "plain": {"value": whole_job_rate(ws, n_frames, ms_plain), "unit": "frames/s",
                       "note": "the same sequence, one rsft_execute_async per frame on one stream"},
-            "graph_speedup": ms_plain / ms, "autotune": tuned,
+            "speedup_over_plain": ms_plain / ms, "autotune": tuned,
             "note": f"shapes {', '.join('x'.join(map(str, ri.WORKLOADS[n].shape)) for n in MIXED)} (B = N/16 per "
-                    f"dim, L = 10, Pfa = 1e-5, the paper's eq. (opt) thresholds), {per_shape} resident frames per shape; one CUDA graph per frame "
-                    f"over {lanes} lanes per plan, {chunk} graphs per rsft_graph_launch_batch"}
+                    f"dim, L = 10, Pfa = 1e-5, the paper's eq. (opt) thresholds), {per_shape} resident frames per "
+                    f"shape; {group} frames per launch of each stage (rsft_execute_frames) recorded as CUDA graphs, "
+                    f"all {len(fseq)} graphs in one rsft_graph_launch_batch"}
 
 
 def per_pass_roofline(R, torch, wl, nv, seed, cubes, stream, peak, steps, lpp=4):

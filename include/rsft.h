@@ -319,6 +319,31 @@ rsft_status rsft_execute_segments_async(rsft_plan* plan, const void* const* d_se
                                         uint64_t* d_located, uint8_t* d_located_votes, void* d_amp,
                                         uint8_t* d_votes_out, int64_t* d_n_located);
 
+/*
+ * Frames of this plan's shape in one launch per stage: the fold of up to 16
+ * frames is one persistent launch whose work units run over (frame, unit),
+ * each frame's cube with its own tensor map; the bucket FFT, the detection,
+ * the vote count, the second stage and the median estimate each take all those
+ * frames' loops in one launch (frames along the grid's second dimension).
+ * Larger counts go in groups of 16.  Frame f reads d_cubes[f] (a host array of
+ * device pointers, each 16-byte aligned), writes its located list to d_located +
+ * f * max_located (ascending), its amplitudes (when d_amp is not NULL) to d_amp +
+ * f * max_located, and its located count to d_counts[f] (device int64; above
+ * max_located means the list was truncated).  Stream-ordered, no host
+ * synchronisation, results identical to one rsft_execute_async per frame.  The
+ * first call allocates the frames' workspace (kept by the plan), so make it
+ * before any stream capture; calls on one plan must not overlap.  Plans whose
+ * stages cannot take several frames (rsft_plan_frames_together gives 0: a
+ * chunked or tensor-core fold, loops in several passes, shared-memory FFT
+ * passes, scatter votes) run the frames one after another instead.  The paper
+ * processes one cube at a time and has no counterpart.
+ * Errors: INVALID_ARG (NULL pointers, n_frames < 0, a misaligned cube), OOM, CUDA.
+ */
+rsft_status rsft_execute_frames(rsft_plan* plan, const void* const* d_cubes, int64_t n_frames, void* stream,
+                                uint64_t* d_located, void* d_amp, int64_t* d_counts);
+/* *together = 1 when rsft_execute_frames runs this plan's frames together, else 0. */
+rsft_status rsft_plan_frames_together(const rsft_plan* plan, int32_t* together);
+
 /* Batched executes of n_frames equally shaped device cubes (this plan's shape):
  * frame f reads d_cubes[f] (a host array of device pointers, each 16-byte
  * aligned), writes its located list to d_located + f * max_located, its
@@ -351,6 +376,11 @@ typedef struct rsft_graph rsft_graph;
 rsft_status rsft_graph_create(rsft_plan* plan, const void* d_cube, int32_t lane, uint64_t* d_located, void* d_amp,
                               int64_t* d_n_located, rsft_graph** graph);
 /* One launch of a recorded execute on `stream` (cudaGraphLaunch).  Errors: INVALID_ARG, CUDA. */
+/* rsft_execute_frames of n_frames cubes recorded as one CUDA graph (results to
+ * d_located / d_amp / d_counts as there); launched like any other graph of this
+ * plan, on the stream of its lane 0.  The paper has no counterpart. */
+rsft_status rsft_graph_create_frames(rsft_plan* plan, const void* const* d_cubes, int64_t n_frames,
+                                     uint64_t* d_located, void* d_amp, int64_t* d_counts, rsft_graph** graph);
 rsft_status rsft_graph_launch(rsft_graph* graph, void* stream);
 /* A batch of recorded executes, possibly of different plans (frames of different shapes):
  * the lanes the graphs belong to start after the work queued on `stream`, each runs its

@@ -50,7 +50,8 @@ C_SYMBOLS = (
     "rsft_execute_segments_async", "rsft_bartlett_plan_create", "rsft_bartlett_plan_destroy", "rsft_bartlett_execute",
     "rsft_bartlett_execute_async", "rsft_bartlett_get", "rsft_bartlett_copy_spectrum",
     "rsft_graph_create", "rsft_graph_launch", "rsft_graph_launch_batch", "rsft_graph_destroy", "rsft_plan_autotune",
-    "rsft_plan_set_loops_per_pass", "rsft_check_wait_timeout",
+    "rsft_plan_set_loops_per_pass", "rsft_check_wait_timeout", "rsft_execute_frames", "rsft_plan_frames_together",
+    "rsft_graph_create_frames",
 )
 RSFT_BARTLETT_GAMMA, RSFT_BARTLETT_GAIN, RSFT_BARTLETT_WINDOW, RSFT_BARTLETT_WORKSPACE_BYTES = 1, 2, 3, 4
 
@@ -121,6 +122,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rsft_bartlett_copy_spectrum.argtypes = [c_void_p, c_void_p, c_void_p]
     lib.rsft_graph_create.argtypes = [c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p, POINTER(c_void_p)]
     lib.rsft_graph_launch.argtypes = [c_void_p, c_void_p]
+    lib.rsft_execute_frames.argtypes = [c_void_p, POINTER(c_void_p), c_int64, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.rsft_plan_frames_together.argtypes = [c_void_p, POINTER(c_int32)]
+    lib.rsft_graph_create_frames.argtypes = [c_void_p, POINTER(c_void_p), c_int64, c_void_p, c_void_p, c_void_p,
+                                             POINTER(c_void_p)]
     lib.rsft_graph_launch_batch.argtypes = [POINTER(c_void_p), c_int64, c_void_p]
     lib.rsft_graph_destroy.argtypes = [c_void_p]
     lib.rsft_graph_destroy.restype = None
@@ -135,7 +140,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rsft_last_error.restype = c_char_p
     for name in ("rsft_plan_create", "rsft_execute", "rsft_execute_async", "rsft_execute_host",
                  "rsft_plan_get", "rsft_plan_timing", "rsft_copy_buckets", "rsft_copy_detections",
-                 "rsft_refine", "rsft_stage2_static"):
+                 "rsft_refine", "rsft_stage2_static", "rsft_execute_frames", "rsft_plan_frames_together",
+                 "rsft_graph_create_frames"):
         getattr(lib, name).restype = c_int32
     _lib = lib
     return lib
@@ -367,6 +373,21 @@ def rsft_execute_batch(plan: Plan, cubes, counts, lanes: int = 2, located=None, 
                                              _dptr(counts, "counts")))
 
 
+def rsft_execute_frames(plan: Plan, cubes, counts, located=None, amp=None, stream=None) -> None:
+    """Frames of the plan's shape in one launch per stage (16 frames per launch); frame f's
+    count lands in counts[f], its located list in located[f * max_located:], its amplitudes
+    likewise.  Stream-ordered."""
+    _check(load_library().rsft_execute_frames(plan.handle, _dptr_array(cubes, "cubes"), len(cubes), _stream(stream),
+                                              _dptr(located, "located"), _dptr(amp, "amp"), _dptr(counts, "counts")))
+
+
+def rsft_plan_frames_together(plan: Plan) -> bool:
+    """Whether rsft_execute_frames runs this plan's frames together (else one after another)."""
+    out = c_int32(0)
+    _check(load_library().rsft_plan_frames_together(plan.handle, ctypes.byref(out)))
+    return bool(out.value)
+
+
 def rsft_execute_host_batch(plan: Plan, h_cubes, located, counts, amp=None, stream=None, allow_capacity=False) -> None:
     """Host cubes in, host results out (counts[f], located[f * max_located:], amp likewise)."""
     st = load_library().rsft_execute_host_batch(plan.handle, _hptr_array(h_cubes, "h_cubes"), len(h_cubes),
@@ -516,6 +537,15 @@ def rsft_graph_create(plan: Plan, cube, count, located=None, amp=None, lane: int
                                             _dptr(amp, "amp"), _dptr(count, "count"),
                                             ctypes.byref(h)))
     return Graph(h, plan, (cube, count, located, amp))
+
+
+def rsft_graph_create_frames(plan: Plan, cubes, counts, located=None, amp=None) -> Graph:
+    """Record rsft_execute_frames of `cubes` (results to located / amp / counts) as one CUDA graph."""
+    h = c_void_p()
+    _check(load_library().rsft_graph_create_frames(plan.handle, _dptr_array(cubes, "cubes"), len(cubes),
+                                                   _dptr(located, "located"), _dptr(amp, "amp"),
+                                                   _dptr(counts, "counts"), ctypes.byref(h)))
+    return Graph(h, plan, (list(cubes), counts, located, amp))
 
 
 def rsft_graph_launch_batch(graphs, stream=None) -> None:

@@ -35,6 +35,21 @@ struct rsft_lane {
   float2* d_amp_stage = nullptr;
 };
 
+// Workspace of rsft_execute_frames: the per-frame arrays of up to kMaxFrames frames, one
+// frame after another (grown on first use, kept by the plan).
+struct rsft_frame_work {
+  int cap = 0;                   // frames it holds
+  int64_t frame_bits = 0;        // detection words per frame (L * words_b rounded up to whole 16 bytes)
+  float2* folded = nullptr;      // [frame][L][B]
+  float2* spectrum = nullptr;    // [frame][L][B]
+  uint32_t* det_bits = nullptr;  // [frame][frame_bits]
+  uint32_t* det_count = nullptr; // [frame][L]
+  float* gamma_used = nullptr;   // [frame][L] (estimate mode)
+  uint32_t* warp_count = nullptr;
+  uint32_t* warp_rows = nullptr;
+  ulonglong2* row_list = nullptr;
+};
+
 struct rsft_plan {
   rsft::HostPlan host;
   bool has_device = false;
@@ -66,6 +81,7 @@ struct rsft_plan {
                                     // 100 + rank on the tensor cores
   bool fold_tc = false;             // the fold runs on the tensor cores (fold_tc.cu)
   bool fft_cluster = false;         // the bucket FFT runs as one cluster launch (else shared-memory passes)
+  rsft_frame_work frames{};         // rsft_execute_frames workspace
   int64_t partial_cap = 0;          // elements of every workspace's fold partial-sum buffer
   int loop_group = rsft::kMaxLoopGroup;  // loops folded per pass over the cube
   int sms = 152;                    // streaming multiprocessors of the plan's device (schedule balance)
@@ -869,9 +885,124 @@ rsft_status ensure_lanes(rsft_plan* p, int n, bool staging) {
   return RSFT_OK;
 }
 
+// Whether rsft_execute_frames runs frames together (one launch per stage over all frames): a
+// direct SIMT fold schedule with every loop in one pass, the cluster FFT and the small-row votes.
+bool frames_together(const rsft_plan* p) {
+  return p->fold.direct && !p->fold_tc && p->loop_group >= p->host.loops && p->fft_cluster && p->rows_mode &&
+         p->rows.small;
+}
+
+rsft_status ensure_frames(rsft_plan* p) {
+  rsft_frame_work& fw = p->frames;
+  if (fw.cap >= rsft::kMaxFrames) return RSFT_OK;
+  const int F = rsft::kMaxFrames;
+  const int L = p->host.loops;
+  const size_t lb = static_cast<size_t>(L) * p->host.total_b;
+  const int64_t words_b = p->ws.words_b;
+  fw.frame_bits = (static_cast<int64_t>(L) * words_b + 3) & ~int64_t(3);
+  rsft_status st;
+  if ((st = dev_alloc(p, &fw.folded, F * lb * sizeof(float2))) != RSFT_OK) return st;
+  if ((st = dev_alloc(p, &fw.spectrum, F * lb * sizeof(float2))) != RSFT_OK) return st;
+  if ((st = dev_alloc(p, &fw.det_bits, static_cast<size_t>(F) * fw.frame_bits * 4)) != RSFT_OK) return st;
+  if ((st = dev_alloc(p, &fw.det_count, static_cast<size_t>(F) * L * 4)) != RSFT_OK) return st;
+  if ((st = dev_alloc(p, &fw.gamma_used, static_cast<size_t>(F) * L * 4)) != RSFT_OK) return st;
+  const size_t warps = static_cast<size_t>(p->rows.warps);
+  if ((st = dev_alloc(p, &fw.warp_count, F * warps * 4)) != RSFT_OK) return st;
+  if ((st = dev_alloc(p, &fw.warp_rows, F * warps * 4)) != RSFT_OK) return st;
+  if ((st = dev_alloc(p, &fw.row_list, F * warps * p->rows.rows_per_warp * 16)) != RSFT_OK) return st;
+  fw.cap = F;
+  return RSFT_OK;
+}
+
+// Frames [0, n) of one plan, kMaxFrames per launch of each stage: frame f reads d_cubes[f] and
+// writes d_located + f * max_located, d_amp + f * max_located and d_counts[f].
+rsft_status run_frames(rsft_plan* p, const void* const* d_cubes, int64_t n, cudaStream_t s, uint64_t* d_located,
+                       float2* d_amp, int64_t* d_counts) {
+  const rsft::Geometry& g = p->geom;
+  const int L = g.loops;
+  const int64_t cap = p->host.desc.max_located;
+  rsft_frame_work& fw = p->frames;
+  const int64_t words_b = p->ws.words_b;
+  const bool estimate = p->host.estimate_noise;
+  cudaError_t e = cudaSuccess;
+  for (int64_t f0 = 0; f0 < n; f0 += rsft::kMaxFrames) {
+    const int nf = static_cast<int>(std::min<int64_t>(rsft::kMaxFrames, n - f0));
+    e = cudaMemsetAsync(fw.det_bits, 0, static_cast<size_t>(nf) * fw.frame_bits * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(fw.det_count, 0, static_cast<size_t>(nf) * L * 4, s);
+    if (e != cudaSuccess) return cuda_fail(e, "clear detections");
+    const float2* cubes[rsft::kMaxFrames];
+    for (int f = 0; f < nf; ++f) cubes[f] = static_cast<const float2*>(d_cubes[f0 + f]);
+    e = rsft::launch_fold_frames(g, p->fold, p->tables, cubes, nf, static_cast<int64_t>(L) * g.total_b, 0, L,
+                                 fw.folded, nullptr, p->ws.err_flag, &p->fold_copy_mode, s);
+    if (e != cudaSuccess) return cuda_fail(e, "permute_window_fold (frames)");
+    e = rsft::launch_fft_cluster(g, p->tables, fw.folded, fw.spectrum, fw.det_bits, fw.det_count, words_b, !estimate,
+                                 s, nf, fw.frame_bits);
+    if (e != cudaSuccess) return cuda_fail(e, "bucket_fft/np_detect (frames)");
+    if (estimate) {
+      e = rsft::launch_noise_floor(g, fw.spectrum, static_cast<float>(p->host.floor_factor), fw.gamma_used,
+                                   fw.det_bits, fw.det_count, words_b, s, nf, fw.frame_bits);
+      if (e != cudaSuccess) return cuda_fail(e, "np_detect noise floor (frames)");
+    }
+    uint64_t* loc = d_located ? d_located + f0 * cap : nullptr;
+    e = rsft::launch_vote_rows(g, p->rows, p->tables, fw.det_bits, words_b, p->host.mu, fw.warp_count, nullptr, loc,
+                               nullptr, nullptr, cap, d_counts + f0, p->ws.err_flag, fw.row_list, fw.warp_rows, s, nf,
+                               fw.frame_bits);
+    if (e != cudaSuccess) return cuda_fail(e, "vote_rows (frames)");
+    if (d_amp && cap > 0) {
+      e = rsft::launch_median(g, p->tables, fw.spectrum, loc, d_counts + f0, cap, d_amp + f0 * cap, s, nf);
+      if (e != cudaSuccess) return cuda_fail(e, "median_estimate (frames)");
+    }
+  }
+  return RSFT_OK;
+}
+
+// Frames one after another on the plan's own workspace (plans whose stages cannot take several
+// frames per launch).
+rsft_status run_frames_in_turn(rsft_plan* p, const void* const* d_cubes, int64_t n, cudaStream_t s,
+                               uint64_t* d_located, float2* d_amp, int64_t* d_counts) {
+  const int64_t cap = p->host.desc.max_located;
+  for (int64_t f = 0; f < n; ++f) {
+    rsft_status st = run_lane(p, p->ws, p->votes_dirty, false, d_cubes[f], s, d_located ? d_located + f * cap : nullptr,
+                              nullptr, d_amp ? d_amp + f * cap : nullptr, nullptr, d_counts + f);
+    if (st != RSFT_OK) return st;
+  }
+  return RSFT_OK;
+}
+
+rsft_status check_frames_args(rsft_plan* plan, const void* const* d_cubes, int64_t n_frames, uint64_t* d_located,
+                              int64_t* d_counts) {
+  if (!plan || n_frames < 0 || (n_frames > 0 && (!d_cubes || !d_counts)))
+    return fail(RSFT_ERR_INVALID_ARG, "NULL plan, cubes or counts, or negative frame count");
+  if (!plan->has_device) return fail(RSFT_ERR_INVALID_ARG, "host-only plan cannot execute");
+  if (plan->host.desc.max_located > 0 && n_frames > 0 && !d_located) return fail(RSFT_ERR_INVALID_ARG, "d_located is NULL");
+  for (int64_t f = 0; f < n_frames; ++f)
+    if (!d_cubes[f] || reinterpret_cast<uintptr_t>(d_cubes[f]) % 16 != 0)
+      return fail(RSFT_ERR_INVALID_ARG, "every cube must be non-NULL and 16-byte aligned");
+  return RSFT_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+rsft_status rsft_execute_frames(rsft_plan* plan, const void* const* d_cubes, int64_t n_frames, void* stream,
+                                uint64_t* d_located, void* d_amp, int64_t* d_counts) {
+  rsft_status st = check_frames_args(plan, d_cubes, n_frames, d_located, d_counts);
+  if (st != RSFT_OK || n_frames == 0) return st;
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return fail(RSFT_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!frames_together(plan))
+    return run_frames_in_turn(plan, d_cubes, n_frames, s, d_located, static_cast<float2*>(d_amp), d_counts);
+  if ((st = ensure_frames(plan)) != RSFT_OK) return st;
+  return run_frames(plan, d_cubes, n_frames, s, d_located, static_cast<float2*>(d_amp), d_counts);
+}
+
+rsft_status rsft_plan_frames_together(const rsft_plan* plan, int32_t* together) {
+  if (!plan || !together) return fail(RSFT_ERR_INVALID_ARG, "NULL plan or output");
+  *together = plan->has_device && frames_together(plan) ? 1 : 0;
+  return RSFT_OK;
+}
 
 rsft_status rsft_execute_batch(rsft_plan* plan, const void* const* d_cubes, int64_t n_frames, int32_t lanes,
                                void* stream, uint64_t* d_located, void* d_amp, int64_t* d_counts) {
@@ -1502,6 +1633,62 @@ rsft_status rsft_graph_create(rsft_plan* plan, const void* d_cube, int32_t lane,
   rsft_graph* out = new rsft_graph;
   out->plan = plan;
   out->lane = lane;
+  out->graph = g;
+  out->exec = x;
+  *graph = out;
+  return RSFT_OK;
+}
+
+rsft_status rsft_graph_create_frames(rsft_plan* plan, const void* const* d_cubes, int64_t n_frames, uint64_t* d_located,
+                                     void* d_amp, int64_t* d_counts, rsft_graph** graph) {
+  if (!graph) return fail(RSFT_ERR_INVALID_ARG, "NULL graph pointer");
+  *graph = nullptr;
+  rsft_status st = check_frames_args(plan, d_cubes, n_frames, d_located, d_counts);
+  if (st != RSFT_OK) return st;
+  if (n_frames < 1) return fail(RSFT_ERR_INVALID_ARG, "a frames graph needs at least one frame");
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return fail(RSFT_ERR_CUDA, "cudaSetDevice failed");
+  const bool together = frames_together(plan);
+  if ((st = ensure_lanes(plan, 1, false)) != RSFT_OK) return st;   // graph batches run on lane 0's stream
+  if (together && (st = ensure_frames(plan)) != RSFT_OK) return st;
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "graph capture stream");
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return cuda_fail(e, "cudaStreamBeginCapture");
+  }
+  if (together) {
+    st = run_frames(plan, d_cubes, n_frames, cs, d_located, static_cast<float2*>(d_amp), d_counts);
+  } else {
+    // recorded on lane 0's workspace (a recorded execute always clears its votes first)
+    rsft_lane& ln = plan->lanes[0];
+    const int64_t cap = plan->host.desc.max_located;
+    for (int64_t f = 0; f < n_frames && st == RSFT_OK; ++f) {
+      bool dirty = true;
+      st = run_lane(plan, ln.ws, dirty, false, d_cubes[f], cs, d_located ? d_located + f * cap : nullptr, nullptr,
+                    d_amp ? static_cast<float2*>(d_amp) + f * cap : nullptr, nullptr, d_counts + f);
+    }
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+  cudaStreamDestroy(cs);
+  if (st != RSFT_OK) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return st;
+  }
+  if (ec != cudaSuccess) return cuda_fail(ec, "cudaStreamEndCapture");
+  cudaGraphExec_t x = nullptr;
+  e = cudaGraphInstantiate(&x, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  rsft_graph* out = new rsft_graph;
+  out->plan = plan;
+  out->lane = 0;
   out->graph = g;
   out->exec = x;
   *graph = out;

@@ -9,6 +9,7 @@ namespace rsft {
 constexpr int kMaxDim = 4;
 constexpr int kMaxLoopGroup = 16;    // loops folded per pass over the cube
 constexpr int kFoldConsumers = 256;  // fold consumer threads per CTA (two columns each)
+constexpr int kMaxFrames = 16;       // frames of one plan processed by one launch per stage
 
 // Sizes of the cube and the bucket grid, in the form the kernels index with.
 struct Geometry {
@@ -170,6 +171,11 @@ cudaError_t launch_count_scan(const uint32_t* counts, int64_t n, uint64_t* offse
 cudaError_t launch_fold(const Geometry& g, const FoldSchedule& fs, const DeviceTables& t,
                         const float2* cube, int loop0, int lg, float2* folded, float2* partial, int* err,
                         int* copy_mode, cudaStream_t stream);
+// The fold of `nframes` cubes of one plan in one persistent launch (direct schedules): frame f's
+// buckets go to folded + f * folded_stride.
+cudaError_t launch_fold_frames(const Geometry& g, const FoldSchedule& fs, const DeviceTables& t,
+                               const float2* const* cubes, int nframes, int64_t folded_stride, int loop0, int lg,
+                               float2* folded, float2* partial, int* err, int* copy_mode, cudaStream_t stream);
 cudaError_t launch_fold_reduce(const Geometry& g, const FoldSchedule& fs, const DeviceTables& t,
                                int loop0, int lg, const float2* partial, float2* folded,
                                cudaStream_t stream);
@@ -179,13 +185,16 @@ cudaError_t launch_fft_pass(const Geometry& g, const FftPass& ps, const DeviceTa
 // The whole N-D bucket FFT of every loop in one launch: C CTAs per loop in a thread-block cluster
 // (fft_cluster_size: 0 when the bucket grid does not allow it), detection fused when `detect`.
 int fft_cluster_size(const Geometry& g);
+// With nframes > 1 the arrays hold frames one after another ([frame][L][B] buckets, [frame][L] counts,
+// frame_bits detection words per frame).
 cudaError_t launch_fft_cluster(const Geometry& g, const DeviceTables& t, const float2* in, float2* out,
                                uint32_t* det_bits, uint32_t* det_count, int64_t words_b, bool detect,
-                               cudaStream_t stream);
+                               cudaStream_t stream, int nframes = 1, int64_t frame_bits = 0);
 // Estimate mode of the first stage: per loop, gamma_l = lowermedian(|f-hat_l|^2) * factor (written to
 // gamma_out[l]) and the loop's detection bitmap and count against it.
 cudaError_t launch_noise_floor(const Geometry& g, const float2* spectrum, float factor, float* gamma_out,
-                               uint32_t* det_bits, uint32_t* det_count, int64_t words_b, cudaStream_t stream);
+                               uint32_t* det_bits, uint32_t* det_count, int64_t words_b, cudaStream_t stream,
+                               int nframes = 1, int64_t frame_bits = 0);
 cudaError_t launch_vote_scatter(const Geometry& g, const DeviceTables& t, const uint32_t* det_bits,
                                 int64_t words_b, uint32_t* votes, cudaStream_t stream);
 cudaError_t launch_stage2(const Geometry& g, int mu, Workspace& ws, uint64_t* located,
@@ -193,13 +202,14 @@ cudaError_t launch_stage2(const Geometry& g, int mu, Workspace& ws, uint64_t* lo
                           int64_t* d_count, cudaStream_t stream);
 cudaError_t launch_median(const Geometry& g, const DeviceTables& t, const float2* spectrum,
                           const uint64_t* located, const int64_t* d_count, int64_t capacity,
-                          float2* amp, cudaStream_t stream);
+                          float2* amp, cudaStream_t stream, int nframes = 1);
 int64_t stage2_segments(int64_t total_n);   // 16 KiB vote segments covering N bytes
 cudaError_t launch_vote_rows(const Geometry& g, const VoteRowSchedule& vs, const DeviceTables& t,
                              const uint32_t* det_bits, int64_t words_b, int mu, uint32_t* warp_count,
                              uint64_t* warp_offset, uint64_t* located, uint8_t* located_votes,
                              uint8_t* votes_out, int64_t capacity, int64_t* d_count, int* err,
-                             ulonglong2* row_list, uint32_t* warp_rows, cudaStream_t stream);
+                             ulonglong2* row_list, uint32_t* warp_rows, cudaStream_t stream, int nframes = 1,
+                             int64_t frame_bits = 0);
 // Shared memory and resident blocks per SM of the small-row vote kernel.
 size_t vote_rows_small_smem(const Geometry& g, const VoteRowSchedule& vs, int64_t words_b);
 cudaError_t vote_rows_small_residency(const Geometry& g, const VoteRowSchedule& vs, int64_t words_b,

@@ -57,9 +57,11 @@ constexpr int kStageBytes = kStepsPerStage * kStepElems * 8;
 constexpr int kSmemBudget = 110 * 1024;    // two CTAs per SM
 
 struct FoldArgs {
-  CUtensorMap tmap;       // rows of C classes as one box (tensor mode)
+  CUtensorMap tmap[kMaxFrames];  // per frame: rows of C classes as one box (tensor mode)
   int tensor_rank;        // 0: one 1-D bulk copy per row; 3 or 5: one tensor copy per stage
-  const float2* cube;
+  const float2* cube[kMaxFrames];
+  int nframes;            // frames of one launch (units of frame f follow those of frame f - 1)
+  int64_t folded_stride;  // elements between consecutive frames' folded buckets
   Geometry g;
   FoldSchedule fs;
   int loop0;
@@ -152,7 +154,8 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
   const int RS = sh.rs, spst = sh.spst, nst = sh.nst;
   const int ring = a.ring;
   const int chunks = fs.row_chunks * fs.col_chunks;
-  const int units = fs.groups * chunks;
+  const int units_pf = fs.groups * chunks;          // units of one frame
+  const int units = units_pf * a.nframes;
   const int my_units = (units - static_cast<int>(blockIdx.x) + static_cast<int>(gridDim.x) - 1) /
                        static_cast<int>(gridDim.x);
   const int total = my_units * nst;  // stages of this CTA
@@ -179,7 +182,8 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
   const uint64_t pol_keep = policy_evict_last();
   // Stage i of this CTA (one thread): unit blockIdx.x + (i / nst) grid, stage i % nst of it.
   auto issue = [&](int i) {
-    const int u = static_cast<int>(blockIdx.x) + (i / nst) * static_cast<int>(gridDim.x);
+    const int uf = static_cast<int>(blockIdx.x) + (i / nst) * static_cast<int>(gridDim.x);
+    const int f = uf / units_pf, u = uf - f * units_pf;  // frame, unit within the frame
     const int k = i % nst;
     const int cc = u % fs.col_chunks;
     const int rc = (u / fs.col_chunks) % fs.row_chunks;
@@ -193,11 +197,11 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
              a.table + ((static_cast<int64_t>(u / chunks) * fs.row_chunks + rc) * R + k * spst * fs.crow) * C * LG,
              static_cast<uint32_t>(sh.table_bytes), full + slot, pol_keep);
     if (a.tensor_rank == 3) {
-      tensor_g2s_3d(dst, &a.tmap, cc * W, cls0 & static_cast<int>(g.b[0] - 1), r0, full + slot, pol_stream);
+      tensor_g2s_3d(dst, &a.tmap[f], cc * W, cls0 & static_cast<int>(g.b[0] - 1), r0, full + slot, pol_stream);
     } else if (a.tensor_rank == 5) {
       const int x1 = cls0 & static_cast<int>(g.b[1] - 1);
       const int x0 = (cls0 >> g.log_b[1]) & static_cast<int>(g.b[0] - 1);
-      tensor_g2s_5d(dst, &a.tmap, cc * W, x1, r0 & static_cast<int>(g.m[1] - 1), x0, r0 >> g.log_m[1], full + slot,
+      tensor_g2s_5d(dst, &a.tmap[f], cc * W, x1, r0 & static_cast<int>(g.m[1] - 1), x0, r0 >> g.log_m[1], full + slot,
                     pol_stream);
     } else {
       for (int j = 0; j < spst * RS; ++j) {
@@ -216,7 +220,7 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
             stride *= g.n[d];
           }
         }
-        bulk_g2s(dst + step * RS * W + ro * W, a.cube + row * fs.row_len + static_cast<int64_t>(cc) * W,
+        bulk_g2s(dst + step * RS * W + ro * W, a.cube[f] + row * fs.row_len + static_cast<int64_t>(cc) * W,
                  static_cast<uint32_t>(W * 8), full + slot, pol_stream);
       }
     }
@@ -262,7 +266,9 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
   uint32_t parity = 0u;
   int i = 0;  // stage counter
   for (int q = 0; q < my_units; ++q) {
-    const int u = static_cast<int>(blockIdx.x) + q * static_cast<int>(gridDim.x);
+    const int uf = static_cast<int>(blockIdx.x) + q * static_cast<int>(gridDim.x);
+    const int frame = uf / units_pf, u = uf - frame * units_pf;
+    float2* folded = a.folded + static_cast<int64_t>(frame) * a.folded_stride;
     const int cc = u % fs.col_chunks;
     const int rc = (u / fs.col_chunks) % fs.row_chunks;
     const int cls0 = (u / chunks) * C;
@@ -373,7 +379,7 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
             j += static_cast<int64_t>(jd) << g.b_shift[d];
           }
         }
-        a.folded[static_cast<int64_t>(a.loop0 + l) * g.total_b + j] = sum;
+        folded[static_cast<int64_t>(a.loop0 + l) * g.total_b + j] = sum;
       } else {
         const int ch = rc * fs.col_chunks + cc;
         a.partial[((static_cast<int64_t>(l) * fs.classes + cls) * chunks + ch) * X + x] = sum;
@@ -454,7 +460,7 @@ cudaError_t launch_fold_lg(const FoldArgs& args, int smem, cudaStream_t stream) 
       cached_grid[dev] = per_sm * sms;
     }
   }
-  const int units = args.fs.groups * args.fs.row_chunks * args.fs.col_chunks;
+  const int units = args.fs.groups * args.fs.row_chunks * args.fs.col_chunks * args.nframes;
   const int resident = dev < 64 ? cached_grid[dev] : 2 * 152;
   const int grid = units < resident ? units : resident;
   fold_kernel<LG, CHUNK><<<grid, kThreads, smem, stream>>>(args);
@@ -550,13 +556,18 @@ int encode_fold_map(const Geometry& g, const FoldSchedule& fs, const float2* cub
   return r == CUDA_SUCCESS ? rank : 0;
 }
 
-cudaError_t launch_fold(const Geometry& g, const FoldSchedule& fs, const DeviceTables& t,
-                        const float2* cube, int loop0, int lg, float2* folded, float2* partial, int* err,
-                        int* copy_mode, cudaStream_t stream) {
+cudaError_t launch_fold_frames(const Geometry& g, const FoldSchedule& fs, const DeviceTables& t,
+                               const float2* const* cubes, int nframes, int64_t folded_stride, int loop0, int lg,
+                               float2* folded, float2* partial, int* err, int* copy_mode, cudaStream_t stream) {
+  if (nframes < 1 || nframes > kMaxFrames || (nframes > 1 && !fs.direct)) return cudaErrorInvalidValue;
   thread_local FoldArgs args;  // large (parameter tables); filled, then copied by the launch
-  args.tensor_rank = encode_fold_map(g, fs, cube, &args.tmap);
+  args.tensor_rank = encode_fold_map(g, fs, cubes[0], &args.tmap[0]);
+  for (int f = 1; f < nframes; ++f)
+    if (encode_fold_map(g, fs, cubes[f], &args.tmap[f]) != args.tensor_rank) return cudaErrorInvalidValue;
   if (copy_mode) *copy_mode = args.tensor_rank;
-  args.cube = cube;
+  for (int f = 0; f < kMaxFrames; ++f) args.cube[f] = cubes[f < nframes ? f : 0];
+  args.nframes = nframes;
+  args.folded_stride = folded_stride;
   args.g = g;
   args.fs = fs;
   args.loop0 = loop0;
@@ -600,6 +611,12 @@ cudaError_t launch_fold(const Geometry& g, const FoldSchedule& fs, const DeviceT
     case 16: return chunk ? launch_fold_lg<16, true>(args, smem, stream) : launch_fold_lg<16, false>(args, smem, stream);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_fold(const Geometry& g, const FoldSchedule& fs, const DeviceTables& t,
+                        const float2* cube, int loop0, int lg, float2* folded, float2* partial, int* err,
+                        int* copy_mode, cudaStream_t stream) {
+  return launch_fold_frames(g, fs, t, &cube, 1, 0, loop0, lg, folded, partial, err, copy_mode, stream);
 }
 
 cudaError_t launch_fold_reduce(const Geometry& g, const FoldSchedule& fs, const DeviceTables& t,

@@ -173,6 +173,7 @@ struct ClusterFftArgs {
   int64_t words_b;
   int csize;             // C: CTAs per loop (a cluster)
   int detect;
+  int64_t frame_bits;    // frames (blockIdx.y): detection words between consecutive frames
 };
 
 // Reverse the bits of each dimension's digit of a row-major index over dimensions [d0, D).
@@ -190,13 +191,49 @@ __device__ __forceinline__ uint32_t digit_reverse(uint32_t q, const Geometry& g,
   return out | ((q >> shift) << shift);  // digits of dimensions below d0 pass through
 }
 
-// All radix-2 decimation-in-time stages of dimension d (size n = 2^ln, element stride 2^lst) of an
-// E-element shared-memory buffer whose input along d is in bit-reversed order.
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// All decimation-in-time stages of dimension d (size n = 2^ln, element stride 2^lst) of an
+// E-element shared-memory buffer whose input along d is in bit-reversed order, two radix-2
+// stages per pass between barriers where two remain (a radix-2^2 butterfly on four elements
+// spaced h apart: stage h pairs (a0, a1) and (a2, a3) with W_2h^p, stage 2h pairs (b0, b2) with
+// W_4h^p and (b1, b3) with W_4h^(p + h) = -j W_4h^p), else one.  tw[k] = e^{-j 2 pi k / n}.
 __device__ __forceinline__ void dit_dimension(float2* buf, uint32_t E, int ln, int lst, const float2* __restrict__ tw) {
-  const uint32_t half = E >> 1;
-  for (int lh = 0; lh < ln; ++lh) {
+  const uint32_t smask = (1u << lst) - 1u;
+  int lh = 0;
+  for (; lh + 1 < ln; lh += 2) {
+    const uint32_t quarter = E >> 2;
+    for (uint32_t qi = threadIdx.x; qi < quarter; qi += blockDim.x) {
+      const uint32_t low = qi & smask;
+      const uint32_t t = qi >> lst;                        // [lines * n / 4]
+      const uint32_t b = t & ((1u << (ln - 2)) - 1u);
+      const uint32_t line = t >> (ln - 2);
+      const uint32_t pos = b & ((1u << lh) - 1u);          // position within a block of 4h
+      const uint32_t grp = b >> lh;
+      const uint32_t i0 = (((line << ln) + (grp << (lh + 2)) + pos) << lst) + low;
+      const uint32_t hs = 1u << (lh + lst);
+      const float2 w1 = tw[pos << (ln - 1 - lh)];          // W_2h^pos
+      const float2 w2 = tw[pos << (ln - 2 - lh)];          // W_4h^pos
+      const float2 a0 = buf[i0], a1 = buf[i0 + hs], a2 = buf[i0 + 2 * hs], a3 = buf[i0 + 3 * hs];
+      const float2 y1 = cmulf(w1, a1), y3 = cmulf(w1, a3);
+      const float2 b0 = make_float2(a0.x + y1.x, a0.y + y1.y), b1 = make_float2(a0.x - y1.x, a0.y - y1.y);
+      const float2 b2 = make_float2(a2.x + y3.x, a2.y + y3.y), b3 = make_float2(a2.x - y3.x, a2.y - y3.y);
+      const float2 z2 = cmulf(w2, b2);
+      const float2 u3 = cmulf(w2, b3);
+      const float2 z3 = make_float2(u3.y, -u3.x);          // -j W_4h^pos b3
+      buf[i0] = make_float2(b0.x + z2.x, b0.y + z2.y);
+      buf[i0 + 2 * hs] = make_float2(b0.x - z2.x, b0.y - z2.y);
+      buf[i0 + hs] = make_float2(b1.x + z3.x, b1.y + z3.y);
+      buf[i0 + 3 * hs] = make_float2(b1.x - z3.x, b1.y - z3.y);
+    }
+    __syncthreads();
+  }
+  if (lh < ln) {  // the last stage, when log2 n is odd
+    const uint32_t half = E >> 1;
     for (uint32_t bf = threadIdx.x; bf < half; bf += blockDim.x) {
-      const uint32_t low = bf & ((1u << lst) - 1u);
+      const uint32_t low = bf & smask;
       const uint32_t t = bf >> lst;
       const uint32_t b = t & ((1u << (ln - 1)) - 1u);
       const uint32_t line = t >> (ln - 1);
@@ -204,9 +241,9 @@ __device__ __forceinline__ void dit_dimension(float2* buf, uint32_t E, int ln, i
       const uint32_t grp = b >> lh;
       const uint32_t i0 = (((line << ln) + (grp << (lh + 1)) + pos) << lst) + low;
       const uint32_t i1 = i0 + (1u << (lh + lst));
-      const float2 w = __ldg(tw + (pos << (ln - 1 - lh)));
+      const float2 w = tw[pos << (ln - 1 - lh)];
       const float2 x0 = buf[i0], x1 = buf[i1];
-      const float2 y = make_float2(x1.x * w.x - x1.y * w.y, x1.x * w.y + x1.y * w.x);
+      const float2 y = cmulf(w, x1);
       buf[i0] = make_float2(x0.x + y.x, x0.y + y.y);
       buf[i1] = make_float2(x0.x - y.x, x0.y - y.y);
     }
@@ -220,8 +257,9 @@ __device__ __forceinline__ void dit_dimension(float2* buf, uint32_t E, int ln, i
 // warp's 32 consecutive elements on one aligned detection word.
 __device__ __forceinline__ void store_block(const ClusterFftArgs& a, int l, const float2* src, uint32_t E, int lq,
                                             int lS, uint32_t col0, float gamma, uint32_t* hits) {
-  float2* dst = a.out + static_cast<int64_t>(l) * a.g.total_b;
-  uint32_t* bits = a.det_bits + static_cast<int64_t>(l) * a.words_b;
+  const int64_t f = blockIdx.y;
+  float2* dst = a.out + (f * a.g.loops + l) * a.g.total_b;
+  uint32_t* bits = a.det_bits + f * a.frame_bits + static_cast<int64_t>(l) * a.words_b;
   const int lane = threadIdx.x & 31;
   const uint32_t qmask = (1u << lq) - 1u;
   for (uint32_t e0 = 0; e0 < E; e0 += blockDim.x) {
@@ -262,15 +300,30 @@ __global__ void __launch_bounds__(512) fft_cluster_kernel(const ClusterFftArgs a
   const uint32_t E = B / C;                     // this CTA's elements in each phase
   const uint32_t S = B >> g.log_b[0];           // elements of one row of dimension 0
   const int lS = 31 - __clz(S);
-  const float2* src = a.in + static_cast<int64_t>(l) * B + static_cast<int64_t>(c) * E;
+  const float2* src = a.in + (static_cast<int64_t>(blockIdx.y) * g.loops + l) * B + static_cast<int64_t>(c) * E;
   const int d_first = C == 1 ? 0 : 1;           // dimensions transformed in place
   if (threadIdx.x == 0) hits = 0u;
+  // every dimension's twiddles e^{-j 2 pi k / B_d}, k < B_d / 2, after the two data buffers
+  float2* twb = sbuf + (C > 1 ? 2 * E : E);
+  const float2* tws[kMaxDim];
+  {
+    uint32_t off = 0;
+#pragma unroll
+    for (int d = 0; d < kMaxDim; ++d) {
+      tws[d] = twb + off;
+      if (d < g.ndim && g.log_b[d] > 0) {
+        const uint32_t nh = 1u << (g.log_b[d] - 1);
+        for (uint32_t k = threadIdx.x; k < nh; k += blockDim.x) twb[off + k] = __ldg(a.t.twiddle[d] + k);
+        off += nh;
+      }
+    }
+  }
   // phase 1: rows [c E / S, (c + 1) E / S) of the loop, bit-reversed along dimensions d_first..D-1
   for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) sbuf[digit_reverse(e, g, d_first)] = src[e];
   __syncthreads();
   for (int d = g.ndim - 1; d >= d_first; --d)
     if (g.log_b[d] > 0)
-      dit_dimension(sbuf, E, g.log_b[d], g.b_shift[d], a.t.twiddle[d]);
+      dit_dimension(sbuf, E, g.log_b[d], g.b_shift[d], tws[d]);
   const float gamma = a.detect ? a.t.gamma[l] : 0.f;
   if (C == 1) {
     const int lB = 31 - __clz(B);                // the loop as one row: bucket k = e
@@ -292,12 +345,12 @@ __global__ void __launch_bounds__(512) fft_cluster_kernel(const ClusterFftArgs a
       gbuf[(rrev << lq) + q] = remote[((row - owner * rows_per) << lS) + c * Q + q];
     }
     cluster.sync();                              // no CTA leaves while others still read its rows
-    if (lb0 > 0) dit_dimension(gbuf, E, lb0, lq, a.t.twiddle[0]);
+    if (lb0 > 0) dit_dimension(gbuf, E, lb0, lq, tws[0]);
     store_block(a, l, gbuf, E, lq, lS, c * Q, gamma, &hits);
   }
   if (a.detect) {
     __syncthreads();
-    if (threadIdx.x == 0 && hits) atomicAdd(a.det_count + l, hits);
+    if (threadIdx.x == 0 && hits) atomicAdd(a.det_count + static_cast<int64_t>(blockIdx.y) * g.loops + l, hits);
   }
 }
 
@@ -310,6 +363,8 @@ struct FloorArgs {
   float* gamma_out;        // [L] thresholds used
   uint32_t* det_bits;      // [L][words_b], zero on entry
   uint32_t* det_count;     // [L]
+  int64_t frame_bits;      // frames (blockIdx.y): detection words between consecutive frames
+  int loops;               // L (per frame)
 };
 
 // One CTA per loop: radix select of the lower median of the B bucket powers (four 8-bit digits,
@@ -321,9 +376,10 @@ __global__ void __launch_bounds__(kFloorThreads) noise_floor_kernel(const FloorA
   __shared__ uint32_t pick[2];   // selected digit, count of smaller keys under the prefix
   __shared__ uint32_t hits;
   const int l = blockIdx.x;
+  const int64_t fl = static_cast<int64_t>(blockIdx.y) * a.loops + l;   // frame-major loop index
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t B = a.total_b;
-  const float2* sp = a.spectrum + static_cast<int64_t>(l) * B;
+  const float2* sp = a.spectrum + fl * B;
   uint32_t prefix = 0u;
   uint32_t rank = static_cast<uint32_t>((B - 1) / 2);
   for (int pass = 0; pass < 4; ++pass) {
@@ -387,11 +443,11 @@ __global__ void __launch_bounds__(kFloorThreads) noise_floor_kernel(const FloorA
   }
   const float gamma = __uint_as_float(prefix) * a.factor;
   if (tid == 0) {
-    a.gamma_out[l] = gamma;
+    a.gamma_out[fl] = gamma;
     hits = 0u;
   }
   __syncthreads();
-  uint32_t* bits = a.det_bits + static_cast<int64_t>(l) * a.words_b;
+  uint32_t* bits = a.det_bits + static_cast<int64_t>(blockIdx.y) * a.frame_bits + static_cast<int64_t>(l) * a.words_b;
   uint32_t mine = 0u;
   for (int64_t e0 = 0; e0 < B; e0 += kFloorThreads) {
     const int64_t e = e0 + tid;
@@ -405,14 +461,17 @@ __global__ void __launch_bounds__(kFloorThreads) noise_floor_kernel(const FloorA
   for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
   if (lane == 0 && mine) atomicAdd(&hits, mine);
   __syncthreads();
-  if (tid == 0) a.det_count[l] = hits;
+  if (tid == 0) a.det_count[fl] = hits;
 }
 
 }  // namespace
 
 cudaError_t launch_noise_floor(const Geometry& g, const float2* spectrum, float factor, float* gamma_out,
-                               uint32_t* det_bits, uint32_t* det_count, int64_t words_b, cudaStream_t stream) {
+                               uint32_t* det_bits, uint32_t* det_count, int64_t words_b, cudaStream_t stream,
+                               int nframes, int64_t frame_bits) {
   FloorArgs args;
+  args.frame_bits = frame_bits;
+  args.loops = g.loops;
   args.spectrum = spectrum;
   args.total_b = g.total_b;
   args.words_b = words_b;
@@ -426,7 +485,7 @@ cudaError_t launch_noise_floor(const Geometry& g, const float2* spectrum, float 
     cudaError_t e = cudaFuncSetAttribute(noise_floor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
-  noise_floor_kernel<<<g.loops, kFloorThreads, smem, stream>>>(args);
+  noise_floor_kernel<<<dim3(g.loops, nframes), kFloorThreads, smem, stream>>>(args);
   return cudaGetLastError();
 }
 
@@ -437,6 +496,9 @@ int fft_cluster_size(const Geometry& g) {
   int64_t c = B / 2048;  // about 2048 buckets per CTA
   if (c < 1) c = 1;
   while (c > 8 || c > g.b[0] || c > S) c >>= 1;
+  int64_t twiddles = 0;
+  for (int d = 0; d < g.ndim; ++d) twiddles += g.b[d] / 2;
+  if (twiddles > 8192) return 0;
   for (; c > 1; c >>= 1)
     if (B / c <= 8192 && S / c >= 32) return static_cast<int>(c);  // two buffers of B / C; whole detection words
   return B <= 16384 ? 1 : 0;                   // one CTA holds the loop in place (128 KiB)
@@ -444,7 +506,7 @@ int fft_cluster_size(const Geometry& g) {
 
 cudaError_t launch_fft_cluster(const Geometry& g, const DeviceTables& t, const float2* in, float2* out,
                                uint32_t* det_bits, uint32_t* det_count, int64_t words_b, bool detect,
-                               cudaStream_t stream) {
+                               cudaStream_t stream, int nframes, int64_t frame_bits) {
   const int csize = fft_cluster_size(g);
   if (csize < 1) return cudaErrorInvalidConfiguration;
   ClusterFftArgs args;
@@ -457,8 +519,11 @@ cudaError_t launch_fft_cluster(const Geometry& g, const DeviceTables& t, const f
   args.words_b = words_b;
   args.csize = csize;
   args.detect = detect ? 1 : 0;
+  args.frame_bits = frame_bits;
   const int64_t E = g.total_b / csize;
-  const int smem = static_cast<int>(E * sizeof(float2) * (csize > 1 ? 2 : 1));
+  int64_t twiddles = 0;
+  for (int d = 0; d < g.ndim; ++d) twiddles += g.b[d] / 2;
+  const int smem = static_cast<int>((E * (csize > 1 ? 2 : 1) + twiddles) * sizeof(float2));
   static int set_smem[64] = {0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -470,7 +535,7 @@ cudaError_t launch_fft_cluster(const Geometry& g, const DeviceTables& t, const f
   }
   const int threads = E >= 2048 ? 512 : 256;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(static_cast<unsigned>(g.loops * csize));
+  cfg.gridDim = dim3(static_cast<unsigned>(g.loops * csize), static_cast<unsigned>(nframes));
   cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = static_cast<size_t>(smem);
   cfg.stream = stream;

@@ -256,10 +256,23 @@ struct MedianArgs {
   float2* amp;
 };
 
+// The median kernels' view of frame blockIdx.y (frames one after another: [frame][L][B] spectra,
+// capacity located entries and one count per frame).
+__device__ __forceinline__ MedianArgs median_frame(const MedianArgs& a) {
+  MedianArgs v = a;
+  const int64_t f = blockIdx.y;
+  v.spectrum = a.spectrum + f * a.g.loops * a.g.total_b;
+  v.located = a.located + f * a.capacity;
+  v.d_count = a.d_count + f;
+  v.amp = a.amp + f * a.capacity;
+  return v;
+}
+
 constexpr int kMedianWarps = 4;
 
 // One warp per located index; per-loop values in shared memory, median by rank.
-__global__ void __launch_bounds__(kMedianWarps * 32) median_kernel(const MedianArgs a) {
+__global__ void __launch_bounds__(kMedianWarps * 32) median_kernel(const MedianArgs args) {
+  const MedianArgs a = median_frame(args);
   __shared__ float vre[kMedianWarps][256];
   __shared__ float vim[kMedianWarps][256];
   __shared__ float sel[kMedianWarps][4];
@@ -318,7 +331,8 @@ __global__ void __launch_bounds__(kMedianWarps * 32) median_kernel(const MedianA
 // Loops of G lanes (L <= G): 32 / G located indices per warp, the per-loop
 // values stay in registers and the ranks come from shuffles within the group.
 template <int G>
-__global__ void __launch_bounds__(kMedianWarps * 32) median_group_kernel(const MedianArgs a) {
+__global__ void __launch_bounds__(kMedianWarps * 32) median_group_kernel(const MedianArgs args) {
+  const MedianArgs a = median_frame(args);
   const Geometry& g = a.g;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int sub = lane / G, l = lane % G;
@@ -412,7 +426,24 @@ struct RowArgs {
   int64_t* d_count;         // small rows: the total located count (written by the emit kernel)
   ulonglong2* row_list;     // small rows, per warp [rows_per_warp]: (row, its votes > mu mask) of emitting rows
   uint32_t* warp_rows;      // small rows: [warps] entries in the warp's row list
+  int64_t frame_bits;       // small rows, frames along blockIdx.y: detection words between frames (multiple of 4)
 };
+
+// The small-row kernels' view of frame blockIdx.y: its detection bitmaps, warp counts and row
+// lists, located list and count (frame 0 is the arguments themselves).
+__device__ __forceinline__ RowArgs frame_view(const RowArgs& a) {
+  RowArgs v = a;
+  const int64_t f = blockIdx.y;
+  if (f == 0) return v;
+  v.det_bits = a.det_bits + f * a.frame_bits;
+  v.warp_count = a.warp_count + f * a.warps;
+  v.warp_rows = a.warp_rows + f * a.warps;
+  v.row_list = a.row_list + f * a.warps * a.rows_per_warp;
+  v.located = a.located + f * a.capacity;
+  if (a.located_votes) v.located_votes = a.located_votes + f * a.capacity;
+  v.d_count = a.d_count + f;
+  return v;
+}
 
 constexpr int kRowWarps = 8;
 
@@ -738,8 +769,9 @@ __device__ __forceinline__ uint64_t write_rows(const RowArgs& a, int lane, int64
 constexpr int kSmallWarps = 16;
 
 template <int PASS, int DV, int NP>
-__global__ void __launch_bounds__(kSmallWarps * 32) vote_rows_small_kernel(const RowArgs a) {
+__global__ void __launch_bounds__(kSmallWarps * 32) vote_rows_small_kernel(const RowArgs args) {
   extern __shared__ __align__(16) unsigned char smem_small[];
+  const RowArgs a = frame_view(args);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const SmallRowLayout lay = small_row_layout(a.g, a.d_v, a.b_in, a.words_b);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_small);
@@ -802,7 +834,9 @@ __global__ void __launch_bounds__(kSmallWarps * 32) vote_rows_small_kernel(const
 // is issued up front.  Votes of the located indices, when asked for, are recounted from
 // the global tables.
 template <int DV, int NP>
-__global__ void __launch_bounds__(kRowWarps * 32) emit_rows_kernel(const RowArgs a, RowTables gt_tables) {
+__global__ void __launch_bounds__(kRowWarps * 32) emit_rows_kernel(const RowArgs args, RowTables gt_tables) {
+  const RowArgs a = frame_view(args);
+  gt_tables.bits = a.det_bits;
   __shared__ unsigned long long red[kRowWarps];
   __shared__ unsigned int wcnt[kRowWarps];
   __shared__ unsigned long long warp_pos[kRowWarps];
@@ -921,8 +955,9 @@ static cudaError_t small_rows_smem(const Geometry& g, const VoteRowSchedule& vs,
 }
 
 template <int DV, int NP>
-cudaError_t small_rows_run(const RowArgs& a, const RowTables& gtab, size_t smem, bool full, cudaStream_t stream) {
-  const unsigned blocks = static_cast<unsigned>((a.warps + kSmallWarps - 1) / kSmallWarps);
+cudaError_t small_rows_run(const RowArgs& a, const RowTables& gtab, size_t smem, bool full, cudaStream_t stream,
+                           int nframes) {
+  const dim3 blocks(static_cast<unsigned>((a.warps + kSmallWarps - 1) / kSmallWarps), static_cast<unsigned>(nframes));
   vote_rows_small_kernel<0, DV, NP><<<blocks, kSmallWarps * 32, smem, stream>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -934,7 +969,7 @@ cudaError_t small_rows_run(const RowArgs& a, const RowTables& gtab, size_t smem,
     vote_rows_small_kernel<1, DV, NP><<<blocks, kSmallWarps * 32, smem, stream>>>(a);
     return cudaGetLastError();
   }
-  const unsigned eblocks = static_cast<unsigned>((a.warps + kRowWarps - 1) / kRowWarps);
+  const dim3 eblocks(static_cast<unsigned>((a.warps + kRowWarps - 1) / kRowWarps), static_cast<unsigned>(nframes));
   emit_rows_kernel<DV, NP><<<eblocks, kRowWarps * 32, 0, stream>>>(a, gtab);
   return cudaGetLastError();
 }
@@ -958,9 +993,12 @@ cudaError_t launch_vote_rows(const Geometry& g, const VoteRowSchedule& vs, const
                              const uint32_t* det_bits, int64_t words_b, int mu, uint32_t* warp_count,
                              uint64_t* warp_offset, uint64_t* located, uint8_t* located_votes,
                              uint8_t* votes_out, int64_t capacity, int64_t* d_count, int* err,
-                             ulonglong2* row_list, uint32_t* warp_rows, cudaStream_t stream) {
+                             ulonglong2* row_list, uint32_t* warp_rows, cudaStream_t stream, int nframes,
+                             int64_t frame_bits) {
+  if (nframes > 1 && (!vs.small || votes_out)) return cudaErrorInvalidValue;  // frames: small rows, no vote array
   if (vs.small) {
     RowArgs a;
+    a.frame_bits = frame_bits;
     a.g = g;
     a.t = t;
     a.det_bits = det_bits;
@@ -992,14 +1030,14 @@ cudaError_t launch_vote_rows(const Geometry& g, const VoteRowSchedule& vs, const
     gtab.bits = det_bits;
     const bool few = g.loops <= 15;  // four counter planes hold the votes
     switch (vs.d_v * 2 + (few ? 1 : 0)) {
-      case 0: return small_rows_run<0, 8>(a, gtab, smem, votes_out != nullptr, stream);
-      case 1: return small_rows_run<0, 4>(a, gtab, smem, votes_out != nullptr, stream);
-      case 2: return small_rows_run<1, 8>(a, gtab, smem, votes_out != nullptr, stream);
-      case 3: return small_rows_run<1, 4>(a, gtab, smem, votes_out != nullptr, stream);
-      case 4: return small_rows_run<2, 8>(a, gtab, smem, votes_out != nullptr, stream);
-      case 5: return small_rows_run<2, 4>(a, gtab, smem, votes_out != nullptr, stream);
-      case 6: return small_rows_run<3, 8>(a, gtab, smem, votes_out != nullptr, stream);
-      case 7: return small_rows_run<3, 4>(a, gtab, smem, votes_out != nullptr, stream);
+      case 0: return small_rows_run<0, 8>(a, gtab, smem, votes_out != nullptr, stream, nframes);
+      case 1: return small_rows_run<0, 4>(a, gtab, smem, votes_out != nullptr, stream, nframes);
+      case 2: return small_rows_run<1, 8>(a, gtab, smem, votes_out != nullptr, stream, nframes);
+      case 3: return small_rows_run<1, 4>(a, gtab, smem, votes_out != nullptr, stream, nframes);
+      case 4: return small_rows_run<2, 8>(a, gtab, smem, votes_out != nullptr, stream, nframes);
+      case 5: return small_rows_run<2, 4>(a, gtab, smem, votes_out != nullptr, stream, nframes);
+      case 6: return small_rows_run<3, 8>(a, gtab, smem, votes_out != nullptr, stream, nframes);
+      case 7: return small_rows_run<3, 4>(a, gtab, smem, votes_out != nullptr, stream, nframes);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -1046,7 +1084,7 @@ cudaError_t launch_vote_rows(const Geometry& g, const VoteRowSchedule& vs, const
 
 cudaError_t launch_median(const Geometry& g, const DeviceTables& t, const float2* spectrum,
                           const uint64_t* located, const int64_t* d_count, int64_t capacity,
-                          float2* amp, cudaStream_t stream) {
+                          float2* amp, cudaStream_t stream, int nframes) {
   MedianArgs args;
   args.g = g;
   args.t = t;
@@ -1064,14 +1102,14 @@ cudaError_t launch_median(const Geometry& g, const DeviceTables& t, const float2
     int64_t gb = (capacity + kMedianWarps * per_warp - 1) / (kMedianWarps * per_warp);
     if (gb > 152 * 8) gb = 152 * 8;
     if (gb < 1) gb = 1;
-    const unsigned gu = static_cast<unsigned>(gb);
+    const dim3 gu(static_cast<unsigned>(gb), static_cast<unsigned>(nframes));
     if (per_warp == 8) median_group_kernel<4><<<gu, kMedianWarps * 32, 0, stream>>>(args);
     else if (per_warp == 4) median_group_kernel<8><<<gu, kMedianWarps * 32, 0, stream>>>(args);
     else if (per_warp == 2) median_group_kernel<16><<<gu, kMedianWarps * 32, 0, stream>>>(args);
     else median_group_kernel<32><<<gu, kMedianWarps * 32, 0, stream>>>(args);
     return cudaGetLastError();
   }
-  median_kernel<<<static_cast<unsigned>(blocks), kMedianWarps * 32, 0, stream>>>(args);
+  median_kernel<<<dim3(static_cast<unsigned>(blocks), static_cast<unsigned>(nframes)), kMedianWarps * 32, 0, stream>>>(args);
   return cudaGetLastError();
 }
 
