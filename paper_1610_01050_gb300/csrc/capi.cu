@@ -310,9 +310,10 @@ rsft_status alloc_workspace(rsft_plan* p, rsft::Workspace& ws, int64_t** d_count
 }
 
 // Fold tables in FP64, rounded once: per row the product of the row dimensions' weights
-// a_{l,d}(s_d) as (d - c, c + d, c, c) of w = c + jd, and per column the product of the
+// a_{l,d}(s_d), w = c + jd, as one record per (row, class) (fold_record_f4: the pairs (d - c, c + d)
+// of two loops per float4, then c of four loops per float4), and per column the product of the
 // rest; loops grouped by `group` (one fold launch per group).
-rsft_status build_fold_tables(rsft_plan* p, int group, const float4** ftable, const float2** fcolw) {
+rsft_status build_fold_tables(rsft_plan* p, int group, rsft::DeviceTables& tabs) {
   const rsft::HostPlan& h = p->host;
   const int L = h.loops, D = h.ndim;
   rsft_status st;
@@ -321,33 +322,36 @@ rsft_status build_fold_tables(rsft_plan* p, int group, const float4** ftable, co
     auto weight = [&](int l, int d, int64_t sd) {
       return h.wbar[d][(h.sigma_inv[l * D + d] * sd) & (h.n[d] - 1)] * h.w[d][sd];
     };
-    // layout [class group][row chunk][row][class in group][loop]: a stage's rows are contiguous
+    // layout [class group][row chunk][row][class in group][record]: a stage's rows are contiguous
     const int64_t R = fs.rows_per_chunk, C = fs.cps;
     const int64_t tunits = static_cast<int64_t>(fs.groups) * fs.row_chunks;
-    std::vector<float4> ft(static_cast<size_t>(L) * tunits * R * C);
+    const int full = std::min(group, L);
+    const int64_t group_f4 = tunits * R * C * rsft::fold_record_f4(full);
+    const int ngroups = (L + group - 1) / group;
+    std::vector<float4> ft(static_cast<size_t>(group_f4) * ngroups, make_float4(0.f, 0.f, 0.f, 0.f));
     std::vector<float2> fc(static_cast<size_t>(L) * fs.col_chunks * fs.width);
     for (int l0 = 0; l0 < L; l0 += group) {
       const int lg = std::min(group, L - l0);
-      const size_t tbase = static_cast<size_t>(l0) * tunits * R * C;
+      const int rec = rsft::fold_record_f4(lg), npair = (lg + 1) / 2;
+      const size_t tbase = static_cast<size_t>(l0 / group) * group_f4;
       for (int64_t e = 0; e < tunits * R * C; ++e) {
         const int64_t ci = e % C, r = (e / C) % R, tu = e / (C * R);
         const int64_t cls = (tu / fs.row_chunks) * C + ci, rc = tu % fs.row_chunks;
-        {
-          int64_t sdig[rsft::kMaxDim] = {0, 0, 0, 0};
-          int64_t rr = rc * R + r, cres = cls;
-          for (int d = fs.d_in - 1; d >= 0; --d) {
-            const int64_t md = rr % h.m[d], xd = cres % h.b[d];
-            rr /= h.m[d];
-            cres /= h.b[d];
-            sdig[d] = xd + h.b[d] * md;
-          }
-          for (int l = 0; l < lg; ++l) {
-            cplx wv(1.0, 0.0);
-            for (int d = 0; d < fs.d_in; ++d) wv *= weight(l0 + l, d, sdig[d]);
-            ft[tbase + static_cast<size_t>(e) * lg + l] =
-                make_float4(static_cast<float>(wv.imag() - wv.real()), static_cast<float>(wv.real() + wv.imag()),
-                            static_cast<float>(wv.real()), static_cast<float>(wv.real()));
-          }
+        int64_t sdig[rsft::kMaxDim] = {0, 0, 0, 0};
+        int64_t rr = rc * R + r, cres = cls;
+        for (int d = fs.d_in - 1; d >= 0; --d) {
+          const int64_t md = rr % h.m[d], xd = cres % h.b[d];
+          rr /= h.m[d];
+          cres /= h.b[d];
+          sdig[d] = xd + h.b[d] * md;
+        }
+        float* out = reinterpret_cast<float*>(&ft[tbase + static_cast<size_t>(e) * rec]);
+        for (int l = 0; l < lg; ++l) {
+          cplx wv(1.0, 0.0);
+          for (int d = 0; d < fs.d_in; ++d) wv *= weight(l0 + l, d, sdig[d]);
+          out[2 * l] = static_cast<float>(wv.imag() - wv.real());      // pair float4 l / 2, half l % 2
+          out[2 * l + 1] = static_cast<float>(wv.real() + wv.imag());
+          out[4 * npair + l] = static_cast<float>(wv.real());           // c-value float4 l / 4, lane l % 4
         }
       }
       const size_t cbase = static_cast<size_t>(l0) * fs.col_chunks * fs.width;
@@ -366,10 +370,12 @@ rsft_status build_fold_tables(rsft_plan* p, int group, const float4** ftable, co
     }
     float4* f4 = nullptr;
     if ((st = upload(p, &f4, ft)) != RSFT_OK) return st;
-    *ftable = f4;
+    tabs.ftable = f4;
+    tabs.ftable_group_f4 = group_f4;
+    tabs.ftable_group = group;
     float2* f2p = nullptr;
     if ((st = upload(p, &f2p, fc)) != RSFT_OK) return st;
-    *fcolw = f2p;
+    tabs.fcolw = f2p;
   }
   return RSFT_OK;
 }
@@ -422,7 +428,7 @@ rsft_status apply_fold_schedule(rsft_plan* p) {
       p->h_xres[c] = static_cast<unsigned char>(rsft::fold_residue(h.n, h.b, D, fs, c));
     p->tables.h_xres = p->h_xres.data();
   }
-  if ((st = build_fold_tables(p, p->loop_group, &p->tables.ftable, &p->tables.fcolw)) != RSFT_OK) return st;
+  if ((st = build_fold_tables(p, p->loop_group, p->tables)) != RSFT_OK) return st;
   return RSFT_OK;
 }
 
@@ -1050,7 +1056,7 @@ rsft_status rsft_execute_segments_async(rsft_plan* plan, const void* const* d_se
   if (!guard.ok) return fail(RSFT_ERR_CUDA, "cudaSetDevice failed");
   if (!plan->seg_ready) {
     plan->seg_tables = plan->tables;
-    rsft_status st = build_fold_tables(plan, 1, &plan->seg_tables.ftable, &plan->seg_tables.fcolw);
+    rsft_status st = build_fold_tables(plan, 1, plan->seg_tables);
     if (st != RSFT_OK) return st;
     plan->seg_ready = true;
   }

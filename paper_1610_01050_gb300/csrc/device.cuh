@@ -59,6 +59,11 @@ __host__ __device__ __forceinline__ int fold_pair_of(int tid, unsigned lane_perm
   return q;
 }
 
+// Fold row-table record of one (row, class) for a group of lg loops (float4 units): ceil(lg / 2)
+// float4 holding the pairs (d - c, c + d) of two loops each, then ceil(lg / 4) float4 holding c of
+// four loops each (w = c + jd the loop's row weight; entries past lg are zero).
+__host__ __device__ __forceinline__ constexpr int fold_record_f4(int lg) { return (lg + 1) / 2 + (lg + 3) / 4; }
+
 // One FFT pass over the bucket arrays: transforms dimensions [da, db) in shared memory.
 struct FftPass {
   int da, db;
@@ -95,8 +100,10 @@ struct DeviceTables {
   const float2* twiddle[kMaxDim];// [B_d / 2]: e^{-j 2 pi k / B_d}
   const float2* ginv[kMaxDim];   // [M_d]: 1 / G_d(-v) (dimension 0 also holds 1 / sum w)
   const unsigned short* slots_by_x; // [X][slots_per_x]: epilogue partial sums of each residue
-  const float4* ftable;          // fold row table [loop group][class group][row chunk][row][class][lg]:
-                                 // (d-c, c+d, c, c)
+  const float4* ftable;          // fold row table [loop group][class group][row chunk][row][class][record]
+                                 // (fold_record_f4: (d-c, c+d) pairs, then c values)
+  int64_t ftable_group_f4;       // float4 of the row table per full loop group
+  int ftable_group;              // loops per group the row table was built for
   const float2* fcolw;           // fold column weights [loop group][col chunk][lg][W]
   const int* h_sinvb;            // host copies of small tables passed as kernel parameters
   const unsigned short* h_slots;

@@ -70,7 +70,7 @@ struct FoldArgs {
   float2* folded;
   float2* partial;
   int* err;
-  const float4* table;    // this loop group's row table: [group][row chunk][row][class][lg] (d - c, c + d, c, c)
+  const float4* table;    // this loop group's row table: [group][row chunk][row][class][record] (fold_record_f4)
   const float2* colw;     // this loop group's column weights: [col chunk][lg][W]
   int smem_colw;          // one column chunk: its weights staged in shared memory once
   int ring;               // stages in the ring
@@ -95,7 +95,7 @@ __host__ __device__ __forceinline__ StageShape stage_shape(const FoldSchedule& f
   s.spst = steps < kStepsPerStage ? steps : kStepsPerStage;
   s.nst = steps / s.spst;
   s.data_bytes = s.spst * s.rs * fs.width * 8;
-  s.table_bytes = s.spst * s.rs * lg * 16;
+  s.table_bytes = s.spst * s.rs * fold_record_f4(lg) * 16;
   return s;
 }
 
@@ -143,6 +143,9 @@ __host__ __device__ __forceinline__ int fold_layout(const FoldSchedule& fs, int 
 template <int LG, bool CHUNK>
 __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant__ FoldArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
+  constexpr int NP = (LG + 1) / 2;        // float4 of (d - c, c + d) pairs in a row record (two loops each)
+  constexpr int NC = (LG + 3) / 4;        // float4 of c values (four loops each)
+  constexpr int REC = NP + NC;
   const Geometry& g = a.g;
   const FoldSchedule& fs = a.fs;
   const int tid = threadIdx.x;
@@ -184,6 +187,16 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
   auto issue = [&](int i) {
     const int uf = static_cast<int>(blockIdx.x) + (i / nst) * static_cast<int>(gridDim.x);
     const int f = uf / units_pf, u = uf - f * units_pf;  // frame, unit within the frame
+    // the frame's tensor map and cube by constant indices (a dynamic index into the parameter
+    // block would make the compiler copy it to local memory)
+    const CUtensorMap* fmap = &a.tmap[0];
+    const float2* fcube = a.cube[0];
+#pragma unroll
+    for (int ff = 1; ff < kMaxFrames; ++ff)
+      if (ff == f) {
+        fmap = &a.tmap[ff];
+        fcube = a.cube[ff];
+      }
     const int k = i % nst;
     const int cc = u % fs.col_chunks;
     const int rc = (u / fs.col_chunks) % fs.row_chunks;
@@ -194,14 +207,14 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
     mbar_arrive_expect_tx(full + slot, static_cast<uint32_t>(sh.data_bytes + sh.table_bytes));
     const int r0 = rc * R + k * spst * fs.crow;  // first row (within each class) of the stage
     bulk_g2s(base + kStageBytes,
-             a.table + ((static_cast<int64_t>(u / chunks) * fs.row_chunks + rc) * R + k * spst * fs.crow) * C * LG,
+             a.table + ((static_cast<int64_t>(u / chunks) * fs.row_chunks + rc) * R + k * spst * fs.crow) * C * REC,
              static_cast<uint32_t>(sh.table_bytes), full + slot, pol_keep);
     if (a.tensor_rank == 3) {
-      tensor_g2s_3d(dst, &a.tmap[f], cc * W, cls0 & static_cast<int>(g.b[0] - 1), r0, full + slot, pol_stream);
+      tensor_g2s_3d(dst, fmap, cc * W, cls0 & static_cast<int>(g.b[0] - 1), r0, full + slot, pol_stream);
     } else if (a.tensor_rank == 5) {
       const int x1 = cls0 & static_cast<int>(g.b[1] - 1);
       const int x0 = (cls0 >> g.log_b[1]) & static_cast<int>(g.b[0] - 1);
-      tensor_g2s_5d(dst, &a.tmap[f], cc * W, x1, r0 & static_cast<int>(g.m[1] - 1), x0, r0 >> g.log_m[1], full + slot,
+      tensor_g2s_5d(dst, fmap, cc * W, x1, r0 & static_cast<int>(g.m[1] - 1), x0, r0 >> g.log_m[1], full + slot,
                     pol_stream);
     } else {
       for (int j = 0; j < spst * RS; ++j) {
@@ -220,7 +233,7 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
             stride *= g.n[d];
           }
         }
-        bulk_g2s(dst + step * RS * W + ro * W, a.cube[f] + row * fs.row_len + static_cast<int64_t>(cc) * W,
+        bulk_g2s(dst + step * RS * W + ro * W, fcube + row * fs.row_len + static_cast<int64_t>(cc) * W,
                  static_cast<uint32_t>(W * 8), full + slot, pol_stream);
       }
     }
@@ -272,31 +285,53 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
     const int cc = u % fs.col_chunks;
     const int rc = (u / fs.col_chunks) % fs.row_chunks;
     const int cls0 = (u / chunks) * C;
-    float2 k12a[LG], k12b[LG], k3[LG];
+    // (K2, K3) of loop l for columns cp (k12a) and cp + 1 (k12b); K1 of loops 2p and 2p + 1 for
+    // column cp (k1a[p]) and cp + 1 (k1b[p])
+    float2 k12a[LG], k12b[LG], k1a[NP], k1b[NP];
 #pragma unroll
     for (int l = 0; l < LG; ++l) {
       k12a[l] = make_float2(0.f, 0.f);
       k12b[l] = make_float2(0.f, 0.f);
-      k3[l] = make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      k1a[q] = make_float2(0.f, 0.f);
+      k1b[q] = make_float2(0.f, 0.f);
     }
     for (int k = 0; k < nst; ++k, ++i) {
       if (ok && !mbar_try_wait(full + slot, parity) && !mbar_wait(full + slot, parity, abort_flag, a.err)) ok = false;
       if (ok && active) {
         const float4* src = reinterpret_cast<const float4*>(smem + slot * a.slot_bytes) + pq;
-        // row-table entries (d - c, c + d, c, c): pairs for the paired multiply-adds
-        const float4* tr = reinterpret_cast<const float4*>(smem + slot * a.slot_bytes + kStageBytes) + ro * LG;
+        // this row slot's record in each row step: (d - c, c + d) pairs of two loops per float4, then
+        // c of four loops per float4
+        const float4* tr = reinterpret_cast<const float4*>(smem + slot * a.slot_bytes + kStageBytes) + ro * REC;
 #pragma unroll
         for (int step = 0; step < kStepsPerStage; ++step) {
           if (step < spst) {
             const float4 v = src[step * (RS * W / 2)];
             const float2 x0 = make_float2(v.x, v.y), x1 = make_float2(v.z, v.w);  // (a, b) of the columns
-            const float2 ss = make_float2(v.x + v.y, v.z + v.w);                  // (a + b) of both
+            const float s0 = v.x + v.y, s1 = v.z + v.w;                           // (a + b) of each column
+            const float2 ss0 = make_float2(s0, s0), ss1 = make_float2(s1, s1);
+            const float4* rec = tr + step * RS * REC;
 #pragma unroll
-            for (int l = 0; l < LG; ++l) {
-              const float4 w = tr[step * RS * LG + l];
-              k12a[l] = __ffma2_rn(make_float2(w.x, w.y), x0, k12a[l]);  // (K2, K3), column cp
-              k12b[l] = __ffma2_rn(make_float2(w.x, w.y), x1, k12b[l]);  // (K2, K3), column cp + 1
-              k3[l] = __ffma2_rn(make_float2(w.z, w.w), ss, k3[l]);      // K1 of both columns
+            for (int q = 0; q < NP; ++q) {
+              const float4 w = rec[q];
+              k12a[2 * q] = __ffma2_rn(make_float2(w.x, w.y), x0, k12a[2 * q]);  // (K2, K3), column cp
+              k12b[2 * q] = __ffma2_rn(make_float2(w.x, w.y), x1, k12b[2 * q]);  // (K2, K3), column cp + 1
+              if (2 * q + 1 < LG) {
+                k12a[2 * q + 1] = __ffma2_rn(make_float2(w.z, w.w), x0, k12a[2 * q + 1]);
+                k12b[2 * q + 1] = __ffma2_rn(make_float2(w.z, w.w), x1, k12b[2 * q + 1]);
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < NC; ++q) {
+              const float4 cv = rec[NP + q];
+              k1a[2 * q] = __ffma2_rn(make_float2(cv.x, cv.y), ss0, k1a[2 * q]);  // K1 of loops 4q, 4q + 1
+              k1b[2 * q] = __ffma2_rn(make_float2(cv.x, cv.y), ss1, k1b[2 * q]);
+              if (2 * q + 1 < NP) {
+                k1a[2 * q + 1] = __ffma2_rn(make_float2(cv.z, cv.w), ss0, k1a[2 * q + 1]);
+                k1b[2 * q + 1] = __ffma2_rn(make_float2(cv.z, cv.w), ss1, k1b[2 * q + 1]);
+              }
             }
           }
         }
@@ -322,9 +357,11 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
 #pragma unroll
     for (int l = 0; l < LG; ++l) {
       if (CHUNK && (l < lc0 || l >= lc0 + lch)) continue;  // another pass's loop (warp-uniform)
-      const float2 pa = k12a[l], pb = k12b[l], p1 = k3[l];
-      float2 v0 = make_float2(p1.x - pa.y, p1.x + pa.x);  // (K1 - K3, K1 + K2)
-      float2 v1 = make_float2(p1.y - pb.y, p1.y + pb.x);
+      const float2 pa = k12a[l], pb = k12b[l];
+      const float c1a = (l & 1) ? k1a[l >> 1].y : k1a[l >> 1].x;  // K1 of loop l, column cp
+      const float c1b = (l & 1) ? k1b[l >> 1].y : k1b[l >> 1].x;  // and column cp + 1
+      float2 v0 = make_float2(c1a - pa.y, c1a + pa.x);  // (K1 - K3, K1 + K2)
+      float2 v1 = make_float2(c1b - pb.y, c1b + pb.x);
       const float2 w0 = smem_colw ? colw[l * W + cp] : __ldg(cw_g + l * W + cp);
       const float2 w1 = smem_colw ? colw[l * W + cp + 1] : __ldg(cw_g + l * W + cp + 1);
       v0 = (ok && active) ? cmul(w0, v0) : make_float2(0.f, 0.f);
@@ -578,8 +615,8 @@ cudaError_t launch_fold_frames(const Geometry& g, const FoldSchedule& fs, const 
   args.folded = folded;
   args.partial = partial;
   args.err = err;
-  const int64_t rows_tab = static_cast<int64_t>(fs.classes) * fs.row_chunks * fs.rows_per_chunk;
-  args.table = t.ftable + static_cast<int64_t>(loop0) * rows_tab;
+  if (t.ftable_group < 1 || loop0 % t.ftable_group != 0 || lg > t.ftable_group) return cudaErrorInvalidValue;
+  args.table = t.ftable + static_cast<int64_t>(loop0 / t.ftable_group) * t.ftable_group_f4;
   args.colw = t.fcolw + static_cast<int64_t>(loop0) * fs.col_chunks * fs.width;
   args.smem_colw = colw_staged(fs, lg) ? 1 : 0;
   for (int l = 0; l < kMaxLoopGroup; ++l)

@@ -256,35 +256,42 @@ struct MedianArgs {
   float2* amp;
 };
 
-// The median kernels' view of frame blockIdx.y (frames one after another: [frame][L][B] spectra,
-// capacity located entries and one count per frame).
-__device__ __forceinline__ MedianArgs median_frame(const MedianArgs& a) {
-  MedianArgs v = a;
+// The median kernels' pointers of frame blockIdx.y (frames one after another: [frame][L][B]
+// spectra, capacity located entries and one count per frame).
+struct MedianFrame {
+  const float2* spectrum;
+  const uint64_t* located;
+  const int64_t* d_count;
+  float2* amp;
+};
+
+__device__ __forceinline__ MedianFrame median_frame(const MedianArgs& a) {
   const int64_t f = blockIdx.y;
-  v.spectrum = a.spectrum + f * a.g.loops * a.g.total_b;
-  v.located = a.located + f * a.capacity;
-  v.d_count = a.d_count + f;
-  v.amp = a.amp + f * a.capacity;
-  return v;
+  MedianFrame m;
+  m.spectrum = a.spectrum + f * a.g.loops * a.g.total_b;
+  m.located = a.located + f * a.capacity;
+  m.d_count = a.d_count + f;
+  m.amp = a.amp + f * a.capacity;
+  return m;
 }
 
 constexpr int kMedianWarps = 4;
 
 // One warp per located index; per-loop values in shared memory, median by rank.
-__global__ void __launch_bounds__(kMedianWarps * 32) median_kernel(const MedianArgs args) {
-  const MedianArgs a = median_frame(args);
+__global__ void __launch_bounds__(kMedianWarps * 32) median_kernel(const MedianArgs a) {
+  const MedianFrame mf = median_frame(a);
   __shared__ float vre[kMedianWarps][256];
   __shared__ float vim[kMedianWarps][256];
   __shared__ float sel[kMedianWarps][4];
   const Geometry& g = a.g;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int64_t count = *a.d_count;
+  int64_t count = *mf.d_count;
   if (count > a.capacity) count = a.capacity;
   const int L = g.loops;
   const int lo_rank = (L - 1) / 2, hi_rank = L / 2;
   for (int64_t q = static_cast<int64_t>(blockIdx.x) * kMedianWarps + wid; q < count;
        q += static_cast<int64_t>(gridDim.x) * kMedianWarps) {
-    const uint64_t i = a.located[q];
+    const uint64_t i = mf.located[q];
     uint32_t id[kMaxDim];
 #pragma unroll
     for (int d = 0; d < kMaxDim; ++d)
@@ -304,7 +311,7 @@ __global__ void __launch_bounds__(kMedianWarps * 32) median_kernel(const MedianA
           val = make_float2(val.x * gi.x - val.y * gi.y, val.x * gi.y + val.y * gi.x);
         }
       }
-      const float2 f = a.spectrum[static_cast<int64_t>(l) * g.total_b + k];
+      const float2 f = mf.spectrum[static_cast<int64_t>(l) * g.total_b + k];
       vre[wid][l] = f.x * val.x - f.y * val.y;
       vim[wid][l] = f.x * val.y + f.y * val.x;
     }
@@ -323,7 +330,7 @@ __global__ void __launch_bounds__(kMedianWarps * 32) median_kernel(const MedianA
       if (ri == hi_rank) sel[wid][3] = xi;
     }
     __syncwarp();
-    if (lane == 0) a.amp[q] = make_float2(0.5f * (sel[wid][0] + sel[wid][1]), 0.5f * (sel[wid][2] + sel[wid][3]));
+    if (lane == 0) mf.amp[q] = make_float2(0.5f * (sel[wid][0] + sel[wid][1]), 0.5f * (sel[wid][2] + sel[wid][3]));
     __syncwarp();
   }
 }
@@ -331,13 +338,13 @@ __global__ void __launch_bounds__(kMedianWarps * 32) median_kernel(const MedianA
 // Loops of G lanes (L <= G): 32 / G located indices per warp, the per-loop
 // values stay in registers and the ranks come from shuffles within the group.
 template <int G>
-__global__ void __launch_bounds__(kMedianWarps * 32) median_group_kernel(const MedianArgs args) {
-  const MedianArgs a = median_frame(args);
+__global__ void __launch_bounds__(kMedianWarps * 32) median_group_kernel(const MedianArgs a) {
+  const MedianFrame mf = median_frame(a);
   const Geometry& g = a.g;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int sub = lane / G, l = lane % G;
   constexpr int kPerWarp = 32 / G;
-  int64_t count = *a.d_count;
+  int64_t count = *mf.d_count;
   if (count > a.capacity) count = a.capacity;
   const int L = g.loops;
   const int lo_rank = (L - 1) / 2, hi_rank = L / 2;
@@ -349,7 +356,7 @@ __global__ void __launch_bounds__(kMedianWarps * 32) median_group_kernel(const M
     const bool active = q < count && l < L;
     float xr = 0.f, xi = 0.f;
     if (active) {
-      const uint64_t i = a.located[q];
+      const uint64_t i = mf.located[q];
       int64_t k = 0;
       float2 val = make_float2(1.f, 0.f);
 #pragma unroll
@@ -365,7 +372,7 @@ __global__ void __launch_bounds__(kMedianWarps * 32) median_group_kernel(const M
           val = make_float2(val.x * gi.x - val.y * gi.y, val.x * gi.y + val.y * gi.x);
         }
       }
-      const float2 f = a.spectrum[static_cast<int64_t>(l) * g.total_b + k];
+      const float2 f = mf.spectrum[static_cast<int64_t>(l) * g.total_b + k];
       xr = f.x * val.x - f.y * val.y;
       xi = f.x * val.y + f.y * val.x;
     }
@@ -385,7 +392,7 @@ __global__ void __launch_bounds__(kMedianWarps * 32) median_group_kernel(const M
     const float r1 = __shfl_sync(0xffffffffu, xr, b1 ? __ffs(b1) - 1 : lane);
     const float i0 = __shfl_sync(0xffffffffu, xi, b2 ? __ffs(b2) - 1 : lane);
     const float i1 = __shfl_sync(0xffffffffu, xi, b3 ? __ffs(b3) - 1 : lane);
-    if (active && l == 0) a.amp[q] = make_float2(0.5f * (r0 + r1), 0.5f * (i0 + i1));
+    if (active && l == 0) mf.amp[q] = make_float2(0.5f * (r0 + r1), 0.5f * (i0 + i1));
   }
 }
 
@@ -429,20 +436,29 @@ struct RowArgs {
   int64_t frame_bits;       // small rows, frames along blockIdx.y: detection words between frames (multiple of 4)
 };
 
-// The small-row kernels' view of frame blockIdx.y: its detection bitmaps, warp counts and row
-// lists, located list and count (frame 0 is the arguments themselves).
-__device__ __forceinline__ RowArgs frame_view(const RowArgs& a) {
-  RowArgs v = a;
+// The small-row kernels' pointers of frame blockIdx.y: its detection bitmaps, warp counts and
+// row lists, located list and count (frame 0 is the arguments themselves).
+struct FramePtrs {
+  const uint32_t* det_bits;
+  uint32_t* warp_count;
+  uint32_t* warp_rows;
+  ulonglong2* row_list;
+  uint64_t* located;
+  uint8_t* located_votes;
+  int64_t* d_count;
+};
+
+__device__ __forceinline__ FramePtrs frame_ptrs(const RowArgs& a) {
   const int64_t f = blockIdx.y;
-  if (f == 0) return v;
-  v.det_bits = a.det_bits + f * a.frame_bits;
-  v.warp_count = a.warp_count + f * a.warps;
-  v.warp_rows = a.warp_rows + f * a.warps;
-  v.row_list = a.row_list + f * a.warps * a.rows_per_warp;
-  v.located = a.located + f * a.capacity;
-  if (a.located_votes) v.located_votes = a.located_votes + f * a.capacity;
-  v.d_count = a.d_count + f;
-  return v;
+  FramePtrs p;
+  p.det_bits = a.det_bits + f * a.frame_bits;
+  p.warp_count = a.warp_count + f * a.warps;
+  p.warp_rows = a.warp_rows + f * a.warps;
+  p.row_list = a.row_list + f * a.warps * a.rows_per_warp;
+  p.located = a.located + f * a.capacity;
+  p.located_votes = a.located_votes ? a.located_votes + f * a.capacity : nullptr;
+  p.d_count = a.d_count + f;
+  return p;
 }
 
 constexpr int kRowWarps = 8;
@@ -738,8 +754,8 @@ __device__ __forceinline__ uint8_t votes_of(const uint64_t* c, int bit) {
 }
 
 // Write the located indices (and votes) of one row per lane, in lane order, from `pos`.
-__device__ __forceinline__ uint64_t write_rows(const RowArgs& a, int lane, int64_t row, uint64_t gt, const uint64_t* c,
-                                               uint64_t pos) {
+__device__ __forceinline__ uint64_t write_rows(const RowArgs& a, const FramePtrs& fp, int lane, int64_t row, uint64_t gt,
+                                               const uint64_t* c, uint64_t pos) {
   const int h = __popcll(gt);
   int incl = h;
 #pragma unroll
@@ -754,8 +770,8 @@ __device__ __forceinline__ uint64_t write_rows(const RowArgs& a, int lane, int64
     const int bit = __ffsll(static_cast<long long>(rem)) - 1;
     rem &= rem - 1;
     if (out < static_cast<uint64_t>(a.capacity)) {
-      a.located[out] = static_cast<uint64_t>(row * a.n_in + bit);
-      if (a.located_votes) a.located_votes[out] = votes_of(c, bit);
+      fp.located[out] = static_cast<uint64_t>(row * a.n_in + bit);
+      if (fp.located_votes) fp.located_votes[out] = votes_of(c, bit);
     }
     ++out;
   }
@@ -769,9 +785,9 @@ __device__ __forceinline__ uint64_t write_rows(const RowArgs& a, int lane, int64
 constexpr int kSmallWarps = 16;
 
 template <int PASS, int DV, int NP>
-__global__ void __launch_bounds__(kSmallWarps * 32) vote_rows_small_kernel(const RowArgs args) {
+__global__ void __launch_bounds__(kSmallWarps * 32) vote_rows_small_kernel(const RowArgs a) {
   extern __shared__ __align__(16) unsigned char smem_small[];
-  const RowArgs a = frame_view(args);
+  const FramePtrs fp = frame_ptrs(a);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const SmallRowLayout lay = small_row_layout(a.g, a.d_v, a.b_in, a.words_b);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_small);
@@ -785,7 +801,7 @@ __global__ void __launch_bounds__(kSmallWarps * 32) vote_rows_small_kernel(const
     mbar_arrive_expect_tx(bar, lay.kb_bytes + lay.cand_bytes + lay.bit_bytes);
     if (lay.kb_bytes) bulk_g2s(smem_small + lay.kb_off, a.t.kb16, lay.kb_bytes, bar, pol);  // none when d_v == 0
     bulk_g2s(smem_small + lay.cand_off, a.t.rowmask, lay.cand_bytes, bar, pol);
-    bulk_g2s(smem_small + lay.bit_off, a.det_bits, lay.bit_bytes, bar, pol);
+    bulk_g2s(smem_small + lay.bit_off, fp.det_bits, lay.bit_bytes, bar, pol);
   }
   if (!mbar_wait_bounded(bar, 0u, a.err)) return;  // no block-wide barriers below
   const int64_t gw = static_cast<int64_t>(blockIdx.x) * kSmallWarps + wid;
@@ -795,7 +811,7 @@ __global__ void __launch_bounds__(kSmallWarps * 32) vote_rows_small_kernel(const
   t.cand = reinterpret_cast<const uint64_t*>(smem_small + lay.cand_off);
   t.bits = reinterpret_cast<const uint32_t*>(smem_small + lay.bit_off);
   const int64_t row0 = gw * a.rows_per_warp;
-  ulonglong2* list = a.row_list + row0;
+  ulonglong2* list = fp.row_list + row0;
   uint64_t pos = PASS == 1 ? a.warp_offset[gw] : 0ull;
   uint32_t hits = 0, nlist = 0;
   for (int rb = 0; rb < a.rows_per_warp; rb += 32) {
@@ -813,7 +829,7 @@ __global__ void __launch_bounds__(kSmallWarps * 32) vote_rows_small_kernel(const
       if (gt != 0ull) list[nlist + __popc(emit & ((1u << lane) - 1u))] = make_ulonglong2(static_cast<uint64_t>(row), gt);
       nlist += static_cast<uint32_t>(__popc(emit));
     } else {
-      pos = write_rows(a, lane, row, gt, c, pos);
+      pos = write_rows(a, fp, lane, row, gt, c, pos);
       if (valid)
         for (int bit = 0; bit < a.n_in; ++bit) a.votes_out[row * a.n_in + bit] = votes_of(c, bit);
     }
@@ -822,8 +838,8 @@ __global__ void __launch_bounds__(kSmallWarps * 32) vote_rows_small_kernel(const
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) hits += __shfl_xor_sync(0xffffffffu, hits, o);
     if (lane == 0) {
-      a.warp_count[gw] = hits;
-      a.warp_rows[gw] = nlist;
+      fp.warp_count[gw] = hits;
+      fp.warp_rows[gw] = nlist;
     }
   }
 }
@@ -834,9 +850,9 @@ __global__ void __launch_bounds__(kSmallWarps * 32) vote_rows_small_kernel(const
 // is issued up front.  Votes of the located indices, when asked for, are recounted from
 // the global tables.
 template <int DV, int NP>
-__global__ void __launch_bounds__(kRowWarps * 32) emit_rows_kernel(const RowArgs args, RowTables gt_tables) {
-  const RowArgs a = frame_view(args);
-  gt_tables.bits = a.det_bits;
+__global__ void __launch_bounds__(kRowWarps * 32) emit_rows_kernel(const RowArgs a, RowTables gt_tables) {
+  const FramePtrs fp = frame_ptrs(a);
+  gt_tables.bits = fp.det_bits;
   __shared__ unsigned long long red[kRowWarps];
   __shared__ unsigned int wcnt[kRowWarps];
   __shared__ unsigned long long warp_pos[kRowWarps];
@@ -844,14 +860,14 @@ __global__ void __launch_bounds__(kRowWarps * 32) emit_rows_kernel(const RowArgs
   const int64_t first = static_cast<int64_t>(blockIdx.x) * kRowWarps;
   const int64_t gw = first + wid;
   const bool live = gw < a.warps;
-  const ulonglong2* list = a.row_list + (live ? gw : 0) * a.rows_per_warp;
+  const ulonglong2* list = fp.row_list + (live ? gw : 0) * a.rows_per_warp;
   // speculative: the first 32 entries of the warp's list (the list has rows_per_warp >= 32 slots)
   const ulonglong2 e0 = live ? list[lane] : make_ulonglong2(0ull, 0ull);
-  const unsigned int n = live ? a.warp_rows[gw] : 0u;
-  if (lane == 0) wcnt[wid] = live ? a.warp_count[gw] : 0u;
+  const unsigned int n = live ? fp.warp_rows[gw] : 0u;
+  if (lane == 0) wcnt[wid] = live ? fp.warp_count[gw] : 0u;
   unsigned long long s = 0ull;
 #pragma unroll 8
-  for (int64_t w = threadIdx.x; w < first; w += kRowWarps * 32) s += a.warp_count[w];
+  for (int64_t w = threadIdx.x; w < first; w += kRowWarps * 32) s += fp.warp_count[w];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) red[wid] = s;
@@ -868,7 +884,7 @@ __global__ void __launch_bounds__(kRowWarps * 32) emit_rows_kernel(const RowArgs
       if (lane >= o) incl += y;
     }
     if (lane < kRowWarps) warp_pos[lane] = base + incl - v;
-    if (lane == kRowWarps - 1 && first + kRowWarps >= a.warps) *a.d_count = static_cast<int64_t>(base + incl);
+    if (lane == kRowWarps - 1 && first + kRowWarps >= a.warps) *fp.d_count = static_cast<int64_t>(base + incl);
   }
   __syncthreads();
   if (!live) return;
@@ -881,7 +897,7 @@ __global__ void __launch_bounds__(kRowWarps * 32) emit_rows_kernel(const RowArgs
 #pragma unroll
     for (int p = 0; p < 8; ++p) c[p] = 0ull;
     if (act && a.located_votes) count_row<DV, NP>(a, gt_tables, static_cast<int64_t>(e.x), c);
-    pos = write_rows(a, lane, static_cast<int64_t>(e.x), e.y, c, pos);
+    pos = write_rows(a, fp, lane, static_cast<int64_t>(e.x), e.y, c, pos);
   }
 }
 
