@@ -28,11 +28,11 @@
  *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
  *    default stream).  Calls are stream-ordered unless stated otherwise.
  *  - Threads: a plan (its workspaces, lanes, events and the graphs recorded
- *    on it) is used by one host thread at a time.  The kernels' launch
- *    attributes (dynamic shared-memory limits, cached occupancies) are
- *    process-wide and set without a lock, so calls from several host threads
- *    must be serialised by the caller, whether or not they share a plan;
- *    plans do not otherwise share state.
+ *    on it) is used by one host thread at a time; different plans may be
+ *    used from different host threads at once.  The kernels' process-wide
+ *    launch attributes (dynamic shared-memory limits, which are only ever
+ *    raised, and cached occupancies) are set under one lock.  The one shared
+ *    device array, that of rsft_stage2_static, is described there.
  *  - Errors: every call returns an rsft_status; on failure nothing is
  *    guaranteed about the outputs and rsft_last_error() holds a message.
  *    The library never traps and never falls back to the CPU: without a

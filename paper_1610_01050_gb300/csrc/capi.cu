@@ -11,7 +11,10 @@
 #include <cstdlib>
 #include <cstring>
 #include <limits>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "device.cuh"
@@ -776,6 +779,48 @@ rsft_status run(rsft_plan* p, const void* d_cube, cudaStream_t stream, uint64_t*
 
 namespace rsft {
 void set_last_error(const char* msg) { g_last_error = msg; }
+
+namespace {
+std::mutex g_attr_mutex;
+std::map<std::pair<int, const void*>, int> g_smem_limit;                  // (device, kernel) -> bytes set
+std::map<std::tuple<int, const void*, int, int>, int> g_resident;         // (device, kernel, threads, bytes)
+}  // namespace
+
+cudaError_t ensure_smem_limit(const void* func, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_attr_mutex);
+  int& cur = g_smem_limit[{dev, func}];
+  if (cur >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
+
+cudaError_t device_resident_ctas(const void* func, int threads, int bytes, int* ctas) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    auto it = g_resident.find({dev, func, threads, bytes});
+    if (it != g_resident.end()) {
+      *ctas = it->second;
+      return cudaSuccess;
+    }
+  }
+  if ((e = ensure_smem_limit(func, bytes)) != cudaSuccess) return e;
+  int per_sm = 0, sms = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, static_cast<size_t>(bytes));
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  std::lock_guard<std::mutex> lock(g_attr_mutex);
+  g_resident[{dev, func, threads, bytes}] = per_sm * sms;
+  *ctas = per_sm * sms;
+  return cudaSuccess;
+}
 }  // namespace rsft
 
 extern "C" {

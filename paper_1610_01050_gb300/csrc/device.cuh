@@ -233,6 +233,14 @@ bool fold_tc_supported(const Geometry& g, const FoldSchedule& fs);
 cudaError_t launch_fold_tc(const Geometry& g, const FoldSchedule& fs, const DeviceTables& t, const float2* cube,
                            int loop0, int lg, float2* folded, int* err, int* copy_mode, cudaStream_t stream);
 
+// Process-wide launch attributes, safe from several host threads: raise a kernel's dynamic
+// shared-memory limit on the current device to at least `bytes` (never lowered, so a launch on
+// another thread that relied on a higher limit stays valid), and the number of CTAs of `threads`
+// threads with `bytes` of dynamic shared memory that fit on the whole current device (cached
+// per device, kernel and size).  Both take one mutex.
+cudaError_t ensure_smem_limit(const void* func, int bytes);
+cudaError_t device_resident_ctas(const void* func, int threads, int bytes, int* ctas);
+
 // Message returned by rsft_last_error() on this thread.
 void set_last_error(const char* msg);
 

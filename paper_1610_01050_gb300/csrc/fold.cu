@@ -479,26 +479,11 @@ __global__ void fold_reduce_kernel(const ReduceArgs a) {
 
 template <int LG, bool CHUNK>
 cudaError_t launch_fold_lg(const FoldArgs& args, int smem, cudaStream_t stream) {
-  static int cached_smem[64] = {0};
-  static int cached_grid[64] = {0};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  int resident = 0;
+  const cudaError_t e =
+      device_resident_ctas(reinterpret_cast<const void*>(fold_kernel<LG, CHUNK>), kThreads, smem, &resident);
   if (e != cudaSuccess) return e;
-  if (dev >= 64 || cached_smem[dev] != smem) {
-    e = cudaFuncSetAttribute(fold_kernel<LG, CHUNK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fold_kernel<LG, CHUNK>, kThreads, smem);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    if (dev < 64) {
-      cached_smem[dev] = smem;
-      cached_grid[dev] = per_sm * sms;
-    }
-  }
   const int units = args.fs.groups * args.fs.row_chunks * args.fs.col_chunks * args.nframes;
-  const int resident = dev < 64 ? cached_grid[dev] : 2 * 152;
   const int grid = units < resident ? units : resident;
   fold_kernel<LG, CHUNK><<<grid, kThreads, smem, stream>>>(args);
   return cudaGetLastError();
@@ -538,18 +523,18 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encode_tiled() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  // looked up once; the initialisation of a function-local static is thread-safe
+  static const EncodeTiledFn fn = [] {
     void* ptr = nullptr;
     cudaDriverEntryPointQueryResult q;
+    EncodeTiledFn f = nullptr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess && ptr)
-      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+      f = reinterpret_cast<EncodeTiledFn>(ptr);
     cudaGetLastError();
-  }
+    return f;
+  }();
   return fn;
 }
 

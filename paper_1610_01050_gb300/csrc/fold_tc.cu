@@ -500,18 +500,18 @@ using EncodeTiledFnTc = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32
                                      CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFnTc encode_tiled_tc() {
-  static EncodeTiledFnTc fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  // looked up once; the initialisation of a function-local static is thread-safe
+  static const EncodeTiledFnTc fn = [] {
     void* ptr = nullptr;
     cudaDriverEntryPointQueryResult q;
+    EncodeTiledFnTc f = nullptr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess && ptr)
-      fn = reinterpret_cast<EncodeTiledFnTc>(ptr);
+      f = reinterpret_cast<EncodeTiledFnTc>(ptr);
     cudaGetLastError();
-  }
+    return f;
+  }();
   return fn;
 }
 
@@ -551,24 +551,13 @@ int encode_tc_map(const Geometry& g, const FoldSchedule& fs, const float2* cube,
 
 template <int LG>
 cudaError_t launch_tc_lg(const TcArgs& args, int smem, cudaStream_t stream) {
-  static int cached_smem[64] = {0};
-  static int cached_sms[64] = {0};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(fold_tc_kernel<LG>), smem);
   if (e != cudaSuccess) return e;
-  if (dev >= 64 || cached_smem[dev] != smem) {
-    e = cudaFuncSetAttribute(fold_tc_kernel<LG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    int sms = 0;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 64) {
-      cached_smem[dev] = smem;
-      cached_sms[dev] = sms;
-    }
-  }
-  const int sms = dev < 64 ? cached_sms[dev] : 152;
-  const int grid = args.units < sms ? args.units : sms;
+  int dev = 0, sms = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int grid = args.units < sms ? args.units : sms;  // one CTA per SM (all of its tensor memory)
   fold_tc_kernel<LG><<<grid, kTcThreads, smem, stream>>>(args);
   return cudaGetLastError();
 }

@@ -482,7 +482,7 @@ cudaError_t launch_noise_floor(const Geometry& g, const float2* spectrum, float 
   args.keys_in_smem = g.total_b <= 32768 ? 1 : 0;
   const int smem = args.keys_in_smem ? static_cast<int>(g.total_b * 4) : 0;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(noise_floor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(noise_floor_kernel), smem);
     if (e != cudaSuccess) return e;
   }
   noise_floor_kernel<<<dim3(g.loops, nframes), kFloorThreads, smem, stream>>>(args);
@@ -524,15 +524,8 @@ cudaError_t launch_fft_cluster(const Geometry& g, const DeviceTables& t, const f
   int64_t twiddles = 0;
   for (int d = 0; d < g.ndim; ++d) twiddles += g.b[d] / 2;
   const int smem = static_cast<int>((E * (csize > 1 ? 2 : 1) + twiddles) * sizeof(float2));
-  static int set_smem[64] = {0};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(fft_cluster_kernel), smem > 48 * 1024 ? smem : 48 * 1024);
   if (e != cudaSuccess) return e;
-  if (dev >= 64 || set_smem[dev] < smem) {
-    e = cudaFuncSetAttribute(fft_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem > 48 * 1024 ? smem : 48 * 1024);
-    if (e != cudaSuccess) return e;
-    if (dev < 64) set_smem[dev] = smem;
-  }
   const int threads = E >= 2048 ? 512 : 256;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(g.loops * csize), static_cast<unsigned>(nframes));
@@ -565,7 +558,7 @@ cudaError_t launch_fft_pass(const Geometry& g, const FftPass& ps, const DeviceTa
   const int64_t slab = ps.outer_per_cta * ps.group * ps.width;
   const int smem = static_cast<int>(slab * sizeof(float2));
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(fft_pass_kernel), smem);
     if (e != cudaSuccess) return e;
   }
   const int64_t ctas = ps.ctas_per_loop * g.loops;

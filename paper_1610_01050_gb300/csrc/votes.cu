@@ -948,11 +948,9 @@ cudaError_t launch_stage2(const Geometry& g, int mu, Workspace& ws, uint64_t* lo
 
 template <int DV, int NP>
 cudaError_t small_rows_attr(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(vote_rows_small_kernel<0, DV, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
+  cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(vote_rows_small_kernel<0, DV, NP>), static_cast<int>(smem));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(vote_rows_small_kernel<1, DV, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(smem));
+    e = ensure_smem_limit(reinterpret_cast<const void*>(vote_rows_small_kernel<1, DV, NP>), static_cast<int>(smem));
   return e;
 }
 
@@ -1083,9 +1081,9 @@ cudaError_t launch_vote_rows(const Geometry& g, const VoteRowSchedule& vs, const
   const int staged = cnt_bytes + bit_bytes <= 112 * 1024 ? 1 : 0;
   const size_t smem = cnt_bytes + (staged ? bit_bytes : 0);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(vote_rows_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(vote_rows_kernel<0>), static_cast<int>(smem));
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(vote_rows_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+      e = ensure_smem_limit(reinterpret_cast<const void*>(vote_rows_kernel<1>), static_cast<int>(smem));
     if (e != cudaSuccess) return e;
   }
   vote_rows_kernel<0><<<blocks, kRowWarps * 32, smem, stream>>>(a, staged);
