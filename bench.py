@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--profile", type=int, default=0,
                     help="run this many plain executes of the workload and exit without a JSON line: the small, "
                          "fixed command that the ncu captures under profiles/ are taken on")
+    ap.add_argument("--profile-frames", type=int, default=0,
+                    help="with --profile: run that many rsft_execute_frames calls of this many frames instead")
     return ap.parse_args()
 
 
@@ -635,6 +637,42 @@ def mixed_batch(R, torch, ri, dev, ws, stream, n_frames=512, per_shape=2, lanes=
                     f"all {len(fseq)} graphs in one rsft_graph_launch_batch"}
 
 
+def frames_fold_roofline(R, torch, fplans, cubes, peak, groups=24, group=16, cap=BATCH_CAP):
+    """The fold as the frames form launches it (16 frames per launch): CUDA events around every
+    fold launch of `groups` rsft_execute_frames calls on the headline's two plans, each on its own
+    stream (as the recorded form runs them), so one group's fold overlaps the other's tail."""
+    dev = cubes[0].device
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = []
+    for s_ in streams:
+        with torch.cuda.stream(s_):
+            outs.append((torch.zeros(group * cap, dtype=torch.int64, device=dev),
+                         torch.zeros(group * cap, dtype=torch.complex64, device=dev),
+                         torch.zeros(group, dtype=torch.int64, device=dev)))
+    seq = [cubes[k % len(cubes)] for k in range(group)]
+    torch.cuda.synchronize()
+    for fp in fplans:
+        R.rsft_plan_timing(fp, True)
+    before = [R.rsft_plan_get(fp, R.RSFT_GET_FRAMES_FOLD) for fp in fplans]
+    for g in range(groups):
+        i = g % 2
+        loc, amp, cnt = outs[i]
+        R.rsft_execute_frames(fplans[i], seq, cnt, located=loc, amp=amp, stream=streams[i])
+    torch.cuda.synchronize()
+    after = [R.rsft_plan_get(fp, R.RSFT_GET_FRAMES_FOLD) for fp in fplans]
+    for fp in fplans:
+        R.rsft_plan_timing(fp, False)
+    ms = sum(a[0] - b[0] for a, b in zip(after, before))
+    launches = sum(a[2] - b[2] for a, b in zip(after, before))
+    frames = sum(a[1] - b[1] for a, b in zip(after, before))
+    per_launch_s = ms / max(1.0, launches) / 1e3
+    bytes_per_launch = int(R.rsft_plan_get(fplans[0], R.RSFT_GET_FOLD_BYTES)[0]) * (frames / max(1.0, launches))
+    achieved = bytes_per_launch / per_launch_s / 1e9
+    return {"achieved": achieved, "frac": achieved / peak, "launch_us": per_launch_s * 1e6,
+            "frames_per_launch": frames / max(1.0, launches), "launches_timed": int(launches),
+            "algorithmic_bytes_per_launch": int(bytes_per_launch)}
+
+
 def per_pass_roofline(R, torch, wl, nv, seed, cubes, stream, peak, steps, lpp=4):
     """The fold with `lpp` loops per pass over the cube (ceil(L / lpp) passes, each reading the
     cube): the HBM-bound form of the same step, against the one fused compute-bound pass."""
@@ -816,6 +854,8 @@ def run_ours(args):
     value = whole_job_rate(ws, n_timed, ms)
     plain_value = whole_job_rate(ws, n_timed, ms_plain)
 
+    # the fold as the frames form launches it (when that form is the headline's)
+    ffold = frames_fold_roofline(R, torch, fplans, cubes, measured_peak()[0]) if form == "frames" else None
     # roofline of the dominant kernel (the fold): algorithmic bytes / average launch time
     fold_bytes = int(R.rsft_plan_get(plan, R.RSFT_GET_FOLD_BYTES)[0])
     timed = max(1.0, stage[6])
@@ -886,6 +926,30 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl, host[0].numpy(), nv, seed)
 
+    roofline_plain = {"bound": "hbm", "kernel": "permute_window_fold (" + ("fold_tc_kernel: tcgen05 3xTF32"
+                      if tensor_fold else "fold_kernel: SIMT FP32") + "), one frame per launch", "achieved": achieved,
+                      "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                      "peak_source": f"{peak_kind} (copy bandwidth)", "traffic": traffic,
+                      "algorithmic_bytes_per_launch": fold_bytes, "launch_us": fold_s * 1e6,
+                      "dram_gbs": traffic / fold_s / 1e9 if traffic else None,
+                      "dram_note": "ncu DRAM bytes of one launch (traffic) over the same launch time: the "
+                                   "sector-level rate, beside the useful-byte rate (achieved); the launch time "
+                                   "from CUDA events of the plain executes"}
+    if isinstance(ffold, dict):
+        ftraffic = profile_traffic(args.workload + "_frames16", fold_source)
+        roofline = {"bound": "hbm", "kernel": "permute_window_fold (fold_kernel: SIMT FP32), "
+                    f"{ffold['frames_per_launch']:.0f} frames per launch as the headline's frames form runs it",
+                    "achieved": ffold["achieved"], "peak": peak, "unit": "GB/s", "frac": ffold["frac"],
+                    "peak_source": f"{peak_kind} (copy bandwidth)",
+                    "traffic": ftraffic,
+                    "algorithmic_bytes_per_launch": ffold["algorithmic_bytes_per_launch"],
+                    "launch_us": ffold["launch_us"], "launches_timed": ffold["launches_timed"],
+                    "dram_gbs": ftraffic / (ffold["launch_us"] / 1e6) / 1e9 if ftraffic else None,
+                    "dram_note": "traffic: ncu DRAM bytes of one 16-frame fold launch (profiles/, the same source); "
+                                 "launch time from CUDA events around each fold launch of rsft_execute_frames calls "
+                                 "on the headline's two plans and streams"}
+    else:
+        roofline = roofline_plain
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
@@ -913,13 +977,8 @@ def run_ours(args):
                           "note": "Pd: targets located within +-1 bin per dim; Pfa: located cells outside +-3-bin "
                                   "target boxes; the dense detector is run at the RSFT's measured Pfa"},
             "stages_us_per_frame": stages,
-            "roofline": {"bound": "hbm", "kernel": "permute_window_fold (" + ("fold_tc_kernel: tcgen05 3xTF32"
-                         if tensor_fold else "fold_kernel: SIMT FP32") + ")", "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_kind} (copy bandwidth)",
-                         "traffic": traffic, "algorithmic_bytes_per_launch": fold_bytes,
-                         "dram_gbs": traffic / fold_s / 1e9 if traffic else None,
-                         "dram_note": "ncu DRAM bytes of one launch (traffic) over the same launch time: the "
-                                      "sector-level rate, beside the useful-byte rate (achieved)"},
+            "roofline": roofline,
+            "roofline_one_frame": roofline_plain,
             "roofline_per_pass": per_pass,
             "e2e": {"value": e2e_val, "unit": "frames/s", "h2d_bytes_per_step": int(np.prod(wl.shape)) * 8,
                     "d2h_bytes_per_step": int(d2h / e2e_steps)},
@@ -965,8 +1024,17 @@ def run_profile(args):
     located = torch.zeros(cap, dtype=torch.int64, device="cuda")
     amp = torch.zeros(cap, dtype=torch.complex64, device="cuda")
     count = torch.zeros(1, dtype=torch.int64, device="cuda")
-    for k in range(args.profile):
-        R.rsft_execute_async(plan, cubes[k % len(cubes)], count, located=located, amp=amp)
+    if args.profile_frames > 0:
+        nf = args.profile_frames
+        seq = [cubes[k % len(cubes)] for k in range(nf)]
+        floc = torch.zeros(nf * cap, dtype=torch.int64, device="cuda")
+        famp = torch.zeros(nf * cap, dtype=torch.complex64, device="cuda")
+        fcnt = torch.zeros(nf, dtype=torch.int64, device="cuda")
+        for _ in range(args.profile):
+            R.rsft_execute_frames(plan, seq, fcnt, located=floc, amp=famp)
+    else:
+        for k in range(args.profile):
+            R.rsft_execute_async(plan, cubes[k % len(cubes)], count, located=located, amp=amp)
     torch.cuda.synchronize()
     plan.close()
 

@@ -211,10 +211,13 @@ enum {
                              * fold, 103 or 105 the same boxes into the tensor-core fold (whole
                              * 64-column rows, chosen by environment RSFT_FOLD=tc at plan
                              * creation), -1 none yet                                            */
-  RSFT_GET_GAMMA_LAST = 17  /* double [L]    thresholds the last execute on the plan's own
+  RSFT_GET_GAMMA_LAST = 17, /* double [L]    thresholds the last execute on the plan's own
                              * workspace compared with: the plan's gamma_l with known noise, the
                              * per-loop estimates (FP32, widened) in estimate mode.  Waits for the
                              * device; NaN before the first execute in estimate mode.          */
+  RSFT_GET_FRAMES_FOLD = 18 /* double [3]    with timing on: summed device milliseconds of the fold
+                             * launches of rsft_execute_frames calls (not of recorded graphs), the
+                             * frames they folded, and their number.  Waits for them.           */
 };
 rsft_status rsft_plan_get(const rsft_plan* plan, int32_t what, void* out, size_t bytes);
 

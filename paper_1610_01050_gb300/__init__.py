@@ -38,7 +38,7 @@ RSFT_GET_SIGMA, RSFT_GET_SIGMA_INV, RSFT_GET_GAMMA, RSFT_GET_BETA = 1, 2, 3, 4
 RSFT_GET_MU, RSFT_GET_PFA1, RSFT_GET_ETA_M, RSFT_GET_PD_BAR = 5, 6, 7, 8
 RSFT_GET_WINDOW, RSFT_GET_FLAT, RSFT_GET_WARNINGS, RSFT_GET_SNR_DB = 9, 10, 11, 12
 RSFT_GET_WORKSPACE_BYTES, RSFT_GET_STAGE_MS, RSFT_GET_FOLD_BYTES, RSFT_GET_FOLD_COPY = 13, 14, 15, 16
-RSFT_GET_GAMMA_LAST = 17
+RSFT_GET_GAMMA_LAST, RSFT_GET_FRAMES_FOLD = 17, 18
 RSFT_BUCKETS_FOLDED, RSFT_BUCKETS_SPECTRUM = 0, 1
 
 # Every C entry point declared in include/rsft.h.
@@ -338,7 +338,7 @@ _GET_SHAPES = {
     RSFT_GET_FLAT: ("float64", "2sn"), RSFT_GET_WARNINGS: ("int32", "1"),
     RSFT_GET_SNR_DB: ("float64", "1"), RSFT_GET_WORKSPACE_BYTES: ("int64", "1"),
     RSFT_GET_STAGE_MS: ("float64", "8"), RSFT_GET_FOLD_BYTES: ("int64", "1"), RSFT_GET_FOLD_COPY: ("int32", "1"),
-    RSFT_GET_GAMMA_LAST: ("float64", "l"),
+    RSFT_GET_GAMMA_LAST: ("float64", "l"), RSFT_GET_FRAMES_FOLD: ("float64", "3"),
 }
 
 
@@ -401,7 +401,7 @@ def rsft_plan_get(plan: Plan, what: int) -> np.ndarray:
     d = plan.desc
     L, D = int(d.loops), int(d.ndim)
     sn = sum(int(d.n[i]) for i in range(D))
-    count = {"ld": L * D, "l": L, "1": 1, "8": 8, "sn": sn, "2sn": 2 * sn}[kind]
+    count = {"ld": L * D, "l": L, "1": 1, "3": 3, "8": 8, "sn": sn, "2sn": 2 * sn}[kind]
     out = np.zeros(count, dtype=dt)
     _check(load_library().rsft_plan_get(plan.handle, int(what), _ptr(out), out.nbytes))
     if kind == "ld":

@@ -93,6 +93,14 @@ struct rsft_plan {
   std::vector<unsigned char> h_xres;        // residue index of each column of a 64-column chunk
   std::vector<cudaEvent_t> event_pool;
   std::vector<std::array<cudaEvent_t, 6>> pending;  // events of timed executes not yet summed
+  struct FramesTiming {
+    cudaEvent_t start, end;
+    int frames;
+  };
+  std::vector<FramesTiming> frames_pending;         // fold launches of timed rsft_execute_frames calls
+  double frames_fold_ms = 0.0;                      // summed device time of those fold launches
+  double frames_folded = 0.0;                       // frames they folded
+  double frames_fold_launches = 0.0;
   double stage_ms[6] = {0, 0, 0, 0, 0, 0};
   int64_t timed_executes = 0;
 };
@@ -643,6 +651,18 @@ void drain_timing(rsft_plan* p) {
       if (e) p->event_pool.push_back(e);
   }
   p->pending.clear();
+  for (auto& ft : p->frames_pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(ft.end) == cudaSuccess && cudaEventElapsedTime(&ms, ft.start, ft.end) == cudaSuccess) {
+      p->frames_fold_ms += ms;
+      p->frames_folded += ft.frames;
+      p->frames_fold_launches += 1.0;
+    }
+    cudaGetLastError();
+    p->event_pool.push_back(ft.start);
+    p->event_pool.push_back(ft.end);
+  }
+  p->frames_pending.clear();
 }
 
 int launches_per_execute(const rsft_plan* p) {
@@ -658,6 +678,11 @@ void release(rsft_plan* p) {
     DeviceGuard guard(p->device);
     cudaDeviceSynchronize();
     p->pending.clear();
+    for (auto& ft : p->frames_pending) {
+      if (ft.start) cudaEventDestroy(ft.start);
+      if (ft.end) cudaEventDestroy(ft.end);
+    }
+    p->frames_pending.clear();
     for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
     for (rsft_lane& ln : p->lanes) {
       if (ln.stream) cudaStreamDestroy(ln.stream);
@@ -968,7 +993,7 @@ rsft_status ensure_frames(rsft_plan* p) {
 // Frames [0, n) of one plan, kMaxFrames per launch of each stage: frame f reads d_cubes[f] and
 // writes d_located + f * max_located, d_amp + f * max_located and d_counts[f].
 rsft_status run_frames(rsft_plan* p, const void* const* d_cubes, int64_t n, cudaStream_t s, uint64_t* d_located,
-                       float2* d_amp, int64_t* d_counts) {
+                       float2* d_amp, int64_t* d_counts, bool timed) {
   const rsft::Geometry& g = p->geom;
   const int L = g.loops;
   const int64_t cap = p->host.desc.max_located;
@@ -983,9 +1008,19 @@ rsft_status run_frames(rsft_plan* p, const void* const* d_cubes, int64_t n, cuda
     if (e != cudaSuccess) return cuda_fail(e, "clear detections");
     const float2* cubes[rsft::kMaxFrames];
     for (int f = 0; f < nf; ++f) cubes[f] = static_cast<const float2*>(d_cubes[f0 + f]);
+    rsft_plan::FramesTiming ft{nullptr, nullptr, nf};
+    if (timed && p->timing) {
+      ft.start = take_event(p);
+      ft.end = take_event(p);
+      if (ft.start) cudaEventRecord(ft.start, s);
+    }
     e = rsft::launch_fold_frames(g, p->fold, p->tables, cubes, nf, static_cast<int64_t>(L) * g.total_b, 0, L,
                                  fw.folded, nullptr, p->ws.err_flag, &p->fold_copy_mode, s);
     if (e != cudaSuccess) return cuda_fail(e, "permute_window_fold (frames)");
+    if (ft.start && ft.end) {
+      cudaEventRecord(ft.end, s);
+      p->frames_pending.push_back(ft);
+    }
     e = rsft::launch_fft_cluster(g, p->tables, fw.folded, fw.spectrum, fw.det_bits, fw.det_count, words_b, !estimate,
                                  s, nf, fw.frame_bits);
     if (e != cudaSuccess) return cuda_fail(e, "bucket_fft/np_detect (frames)");
@@ -1046,7 +1081,7 @@ rsft_status rsft_execute_frames(rsft_plan* plan, const void* const* d_cubes, int
   if (!frames_together(plan))
     return run_frames_in_turn(plan, d_cubes, n_frames, s, d_located, static_cast<float2*>(d_amp), d_counts);
   if ((st = ensure_frames(plan)) != RSFT_OK) return st;
-  return run_frames(plan, d_cubes, n_frames, s, d_located, static_cast<float2*>(d_amp), d_counts);
+  return run_frames(plan, d_cubes, n_frames, s, d_located, static_cast<float2*>(d_amp), d_counts, true);
 }
 
 rsft_status rsft_plan_frames_together(const rsft_plan* plan, int32_t* together) {
@@ -1365,6 +1400,19 @@ rsft_status rsft_plan_get(const rsft_plan* plan, int32_t what, void* out, size_t
       if (e == cudaSuccess) e = cudaMemcpy(g.data(), plan->ws.gamma_used, static_cast<size_t>(L) * 4, cudaMemcpyDeviceToHost);
       if (e != cudaSuccess) return cuda_fail(e, "rsft_plan_get(GAMMA_LAST)");
       for (int l = 0; l < L; ++l) o[l] = static_cast<double>(g[l]);
+      return RSFT_OK;
+    }
+    case RSFT_GET_FRAMES_FOLD: {
+      if (!need(24)) break;
+      rsft_plan* mp = const_cast<rsft_plan*>(plan);
+      if (mp->has_device) {
+        DeviceGuard guard(mp->device);
+        drain_timing(mp);
+      }
+      double* o = static_cast<double*>(out);
+      o[0] = mp->frames_fold_ms;
+      o[1] = mp->frames_folded;
+      o[2] = mp->frames_fold_launches;
       return RSFT_OK;
     }
     case RSFT_GET_FOLD_COPY:
@@ -1711,7 +1759,7 @@ rsft_status rsft_graph_create_frames(rsft_plan* plan, const void* const* d_cubes
     return cuda_fail(e, "cudaStreamBeginCapture");
   }
   if (together) {
-    st = run_frames(plan, d_cubes, n_frames, cs, d_located, static_cast<float2*>(d_amp), d_counts);
+    st = run_frames(plan, d_cubes, n_frames, cs, d_located, static_cast<float2*>(d_amp), d_counts, false);
   } else {
     // recorded on lane 0's workspace (a recorded execute always clears its votes first)
     rsft_lane& ln = plan->lanes[0];
