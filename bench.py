@@ -639,10 +639,12 @@ def mixed_batch(R, torch, ri, dev, ws, stream, n_frames=512, per_shape=2, lanes=
 
 def frames_fold_roofline(R, torch, fplans, cubes, peak, groups=24, group=16, cap=BATCH_CAP):
     """The fold as the frames form launches it (16 frames per launch): CUDA events around every
-    fold launch of `groups` rsft_execute_frames calls on the headline's two plans, each on its own
-    stream (as the recorded form runs them), so one group's fold overlaps the other's tail."""
+    fold launch of `groups` rsft_execute_frames calls on the headline's two plans, all on one
+    stream, so each fold launch runs alone on the GPU (in the recorded form the two plans' groups
+    overlap, which shares the GPU between two folds and makes either launch look longer)."""
     dev = cubes[0].device
-    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    one = torch.cuda.Stream()
+    streams = [one, one]
     outs = []
     for s_ in streams:
         with torch.cuda.stream(s_):
@@ -947,7 +949,7 @@ def run_ours(args):
                     "dram_gbs": ftraffic / (ffold["launch_us"] / 1e6) / 1e9 if ftraffic else None,
                     "dram_note": "traffic: ncu DRAM bytes of one 16-frame fold launch (profiles/, the same source); "
                                  "launch time from CUDA events around each fold launch of rsft_execute_frames calls "
-                                 "on the headline's two plans and streams"}
+                                 "on the headline's two plans, one stream (each fold launch alone on the GPU)"}
     else:
         roofline = roofline_plain
     if rank == 0:
