@@ -215,9 +215,11 @@ enum {
                              * workspace compared with: the plan's gamma_l with known noise, the
                              * per-loop estimates (FP32, widened) in estimate mode.  Waits for the
                              * device; NaN before the first execute in estimate mode.          */
-  RSFT_GET_FRAMES_FOLD = 18 /* double [3]    with timing on: summed device milliseconds of the fold
+  RSFT_GET_FRAMES_FOLD = 18,/* double [3]    with timing on: summed device milliseconds of the fold
                              * launches of rsft_execute_frames calls (not of recorded graphs), the
                              * frames they folded, and their number.  Waits for them.           */
+  RSFT_GET_FFT_SHAPE = 19   /* int32 [2]     the bucket FFT's CTAs per loop (a thread-block cluster)
+                             * and threads per CTA; 0, 0 when it runs as shared-memory passes     */
 };
 rsft_status rsft_plan_get(const rsft_plan* plan, int32_t what, void* out, size_t bytes);
 
@@ -400,10 +402,19 @@ void rsft_graph_destroy(rsft_graph* graph);
  * events on `stream` -- and keeps the fastest, rebuilding the plan's fold tables.
  * d_cube: device, 16-byte aligned, the plan's N complex64 (only its timing matters).
  * *us_out (may be NULL): the winner's microseconds per fold launch; *chosen (may be NULL):
- * its rank among the candidates (0 = the model's choice).  Results of executes do not
- * depend on the schedule beyond FP32 summation order.  Synchronises `stream`; not to be
+ * its rank among the candidates (0 = the model's choice).  With the cluster FFT it then
+ * times every valid shape of the bucket FFT (CTAs per loop 1, 2, 4 or 8, i.e. buckets per
+ * CTA, and 256 or 512 threads per CTA) on the cube's buckets and keeps the fastest
+ * (RSFT_GET_FFT_SHAPE).  Results of executes do not depend on the schedule beyond FP32
+ * summation order; the FFT's shape does not change its arithmetic.  Synchronises `stream`; not to be
  * called while the plan executes on another stream.  The paper has no counterpart.
  * Errors: INVALID_ARG, UNSUPPORTED (no candidate could run), OOM, CUDA. */
+/* Shape of the bucket FFT's cluster launch: ctas_per_loop CTAs (1, 2, 4 or 8; each holds
+ * B / ctas_per_loop buckets of a loop) of `threads` threads (256 or 512); 0, 0 restores the
+ * default.  The arithmetic does not depend on the shape.  Errors: INVALID_ARG, UNSUPPORTED
+ * (shared-memory FFT passes, or a shape the bucket grid does not allow). */
+rsft_status rsft_plan_set_fft_shape(rsft_plan* plan, int32_t ctas_per_loop, int32_t threads);
+
 rsft_status rsft_plan_autotune(rsft_plan* plan, const void* d_cube, void* stream, int32_t candidates, int32_t reps,
                                double* us_out, int32_t* chosen);
 

@@ -38,7 +38,7 @@ RSFT_GET_SIGMA, RSFT_GET_SIGMA_INV, RSFT_GET_GAMMA, RSFT_GET_BETA = 1, 2, 3, 4
 RSFT_GET_MU, RSFT_GET_PFA1, RSFT_GET_ETA_M, RSFT_GET_PD_BAR = 5, 6, 7, 8
 RSFT_GET_WINDOW, RSFT_GET_FLAT, RSFT_GET_WARNINGS, RSFT_GET_SNR_DB = 9, 10, 11, 12
 RSFT_GET_WORKSPACE_BYTES, RSFT_GET_STAGE_MS, RSFT_GET_FOLD_BYTES, RSFT_GET_FOLD_COPY = 13, 14, 15, 16
-RSFT_GET_GAMMA_LAST, RSFT_GET_FRAMES_FOLD = 17, 18
+RSFT_GET_GAMMA_LAST, RSFT_GET_FRAMES_FOLD, RSFT_GET_FFT_SHAPE = 17, 18, 19
 RSFT_BUCKETS_FOLDED, RSFT_BUCKETS_SPECTRUM = 0, 1
 
 # Every C entry point declared in include/rsft.h.
@@ -51,7 +51,7 @@ C_SYMBOLS = (
     "rsft_bartlett_execute_async", "rsft_bartlett_get", "rsft_bartlett_copy_spectrum",
     "rsft_graph_create", "rsft_graph_launch", "rsft_graph_launch_batch", "rsft_graph_destroy", "rsft_plan_autotune",
     "rsft_plan_set_loops_per_pass", "rsft_check_wait_timeout", "rsft_execute_frames", "rsft_plan_frames_together",
-    "rsft_graph_create_frames",
+    "rsft_graph_create_frames", "rsft_plan_set_fft_shape",
 )
 RSFT_BARTLETT_GAMMA, RSFT_BARTLETT_GAIN, RSFT_BARTLETT_WINDOW, RSFT_BARTLETT_WORKSPACE_BYTES = 1, 2, 3, 4
 
@@ -124,6 +124,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rsft_graph_launch.argtypes = [c_void_p, c_void_p]
     lib.rsft_execute_frames.argtypes = [c_void_p, POINTER(c_void_p), c_int64, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.rsft_plan_frames_together.argtypes = [c_void_p, POINTER(c_int32)]
+    lib.rsft_plan_set_fft_shape.argtypes = [c_void_p, c_int32, c_int32]
     lib.rsft_graph_create_frames.argtypes = [c_void_p, POINTER(c_void_p), c_int64, c_void_p, c_void_p, c_void_p,
                                              POINTER(c_void_p)]
     lib.rsft_graph_launch_batch.argtypes = [POINTER(c_void_p), c_int64, c_void_p]
@@ -141,7 +142,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     for name in ("rsft_plan_create", "rsft_execute", "rsft_execute_async", "rsft_execute_host",
                  "rsft_plan_get", "rsft_plan_timing", "rsft_copy_buckets", "rsft_copy_detections",
                  "rsft_refine", "rsft_stage2_static", "rsft_execute_frames", "rsft_plan_frames_together",
-                 "rsft_graph_create_frames"):
+                 "rsft_graph_create_frames", "rsft_plan_set_fft_shape"):
         getattr(lib, name).restype = c_int32
     _lib = lib
     return lib
@@ -338,7 +339,7 @@ _GET_SHAPES = {
     RSFT_GET_FLAT: ("float64", "2sn"), RSFT_GET_WARNINGS: ("int32", "1"),
     RSFT_GET_SNR_DB: ("float64", "1"), RSFT_GET_WORKSPACE_BYTES: ("int64", "1"),
     RSFT_GET_STAGE_MS: ("float64", "8"), RSFT_GET_FOLD_BYTES: ("int64", "1"), RSFT_GET_FOLD_COPY: ("int32", "1"),
-    RSFT_GET_GAMMA_LAST: ("float64", "l"), RSFT_GET_FRAMES_FOLD: ("float64", "3"),
+    RSFT_GET_GAMMA_LAST: ("float64", "l"), RSFT_GET_FRAMES_FOLD: ("float64", "3"), RSFT_GET_FFT_SHAPE: ("int32", "2"),
 }
 
 
@@ -381,6 +382,11 @@ def rsft_execute_frames(plan: Plan, cubes, counts, located=None, amp=None, strea
                                               _dptr(located, "located"), _dptr(amp, "amp"), _dptr(counts, "counts")))
 
 
+def rsft_plan_set_fft_shape(plan: Plan, ctas_per_loop: int, threads: int) -> None:
+    """Bucket FFT cluster shape (CTAs per loop 1/2/4/8, threads 256/512); 0, 0 restores the default."""
+    _check(load_library().rsft_plan_set_fft_shape(plan.handle, int(ctas_per_loop), int(threads)))
+
+
 def rsft_plan_frames_together(plan: Plan) -> bool:
     """Whether rsft_execute_frames runs this plan's frames together (else one after another)."""
     out = c_int32(0)
@@ -401,7 +407,7 @@ def rsft_plan_get(plan: Plan, what: int) -> np.ndarray:
     d = plan.desc
     L, D = int(d.loops), int(d.ndim)
     sn = sum(int(d.n[i]) for i in range(D))
-    count = {"ld": L * D, "l": L, "1": 1, "3": 3, "8": 8, "sn": sn, "2sn": 2 * sn}[kind]
+    count = {"ld": L * D, "l": L, "1": 1, "2": 2, "3": 3, "8": 8, "sn": sn, "2sn": 2 * sn}[kind]
     out = np.zeros(count, dtype=dt)
     _check(load_library().rsft_plan_get(plan.handle, int(what), _ptr(out), out.nbytes))
     if kind == "ld":

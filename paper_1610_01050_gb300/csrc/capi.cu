@@ -84,6 +84,8 @@ struct rsft_plan {
                                     // 100 + rank on the tensor cores
   bool fold_tc = false;             // the fold runs on the tensor cores (fold_tc.cu)
   bool fft_cluster = false;         // the bucket FFT runs as one cluster launch (else shared-memory passes)
+  int fft_csize = 0;                // its CTAs per loop and threads per CTA (0: the default shape; set by
+  int fft_threads = 0;              // rsft_plan_autotune)
   rsft_frame_work frames{};         // rsft_execute_frames workspace
   int64_t partial_cap = 0;          // elements of every workspace's fold partial-sum buffer
   int loop_group = rsft::kMaxLoopGroup;  // loops folded per pass over the cube
@@ -752,7 +754,7 @@ rsft_status run_lane(rsft_plan* p, rsft::Workspace& ws, bool& votes_dirty, bool 
   const bool estimate = p->host.estimate_noise;
   if (p->fft_cluster) {
     e = rsft::launch_fft_cluster(g, p->tables, ws.folded, ws.spectrum, ws.det_bits, ws.det_count, ws.words_b,
-                                 !estimate, stream);
+                                 !estimate, stream, 1, 0, p->fft_csize, p->fft_threads);
     if (e != cudaSuccess) return cuda_fail(e, "bucket_fft/np_detect (cluster)");
   } else {
     for (size_t i = 0; i < p->passes.size(); ++i) {
@@ -1022,7 +1024,7 @@ rsft_status run_frames(rsft_plan* p, const void* const* d_cubes, int64_t n, cuda
       p->frames_pending.push_back(ft);
     }
     e = rsft::launch_fft_cluster(g, p->tables, fw.folded, fw.spectrum, fw.det_bits, fw.det_count, words_b, !estimate,
-                                 s, nf, fw.frame_bits);
+                                 s, nf, fw.frame_bits, p->fft_csize, p->fft_threads);
     if (e != cudaSuccess) return cuda_fail(e, "bucket_fft/np_detect (frames)");
     if (estimate) {
       e = rsft::launch_noise_floor(g, fw.spectrum, static_cast<float>(p->host.floor_factor), fw.gamma_used,
@@ -1402,6 +1404,15 @@ rsft_status rsft_plan_get(const rsft_plan* plan, int32_t what, void* out, size_t
       for (int l = 0; l < L; ++l) o[l] = static_cast<double>(g[l]);
       return RSFT_OK;
     }
+    case RSFT_GET_FFT_SHAPE: {
+      if (!need(8)) break;
+      int32_t* o = static_cast<int32_t*>(out);
+      const bool on = plan->has_device && plan->fft_cluster;
+      o[0] = on ? (plan->fft_csize > 0 ? plan->fft_csize : rsft::fft_cluster_size(plan->geom)) : 0;
+      const int64_t E = on && o[0] > 0 ? plan->geom.total_b / o[0] : 0;
+      o[1] = on ? (plan->fft_threads > 0 ? plan->fft_threads : (E >= 2048 ? 512 : 256)) : 0;
+      return RSFT_OK;
+    }
     case RSFT_GET_FRAMES_FOLD: {
       if (!need(24)) break;
       rsft_plan* mp = const_cast<rsft_plan*>(plan);
@@ -1602,6 +1613,23 @@ rsft_status rsft_plan_set_loops_per_pass(rsft_plan* plan, int32_t loops_per_pass
   return st;
 }
 
+rsft_status rsft_plan_set_fft_shape(rsft_plan* plan, int32_t ctas_per_loop, int32_t threads) {
+  if (!plan) return fail(RSFT_ERR_INVALID_ARG, "NULL plan");
+  if (!plan->has_device) return fail(RSFT_ERR_INVALID_ARG, "host-only plan");
+  if (ctas_per_loop == 0 && threads == 0) {
+    plan->fft_csize = 0;
+    plan->fft_threads = 0;
+    return RSFT_OK;
+  }
+  if (!plan->fft_cluster) return fail(RSFT_ERR_UNSUPPORTED, "this plan's bucket FFT runs as shared-memory passes");
+  if (!rsft::fft_cluster_valid(plan->geom, ctas_per_loop))
+    return fail(RSFT_ERR_UNSUPPORTED, "CTAs per loop must be 1, 2, 4 or 8 and fit the bucket grid");
+  if (threads != 256 && threads != 512) return fail(RSFT_ERR_INVALID_ARG, "threads must be 256 or 512");
+  plan->fft_csize = ctas_per_loop;
+  plan->fft_threads = threads;
+  return RSFT_OK;
+}
+
 rsft_status rsft_plan_autotune(rsft_plan* plan, const void* d_cube, void* stream, int32_t candidates, int32_t reps,
                                double* us_out, int32_t* chosen) {
   if (!plan || !d_cube) return fail(RSFT_ERR_INVALID_ARG, "NULL plan or cube");
@@ -1665,10 +1693,45 @@ rsft_status rsft_plan_autotune(rsft_plan* plan, const void* d_cube, void* stream
       best = static_cast<int>(i);
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   plan->fold = best >= 0 ? cands[best] : original;
   const rsft_status st2 = apply_fold_schedule(plan);
+  // the bucket FFT's shape: CTAs per loop (buckets per CTA) and threads per CTA, timed on the
+  // buckets of the cube under the chosen fold schedule
+  if (st == RSFT_OK && st2 == RSFT_OK && best >= 0 && plan->fft_cluster) {
+    st = fold_cube(plan, d_cube, s);
+    const rsft::Geometry& g = plan->geom;
+    double fft_best = 1e300;
+    int bc = 0, bt = 0;
+    for (int c = 1; c <= 8 && st == RSFT_OK; c <<= 1) {
+      if (!rsft::fft_cluster_valid(g, c)) continue;
+      for (int t : {256, 512}) {
+        auto launch = [&] {
+          return rsft::launch_fft_cluster(g, plan->tables, plan->ws.folded, plan->ws.spectrum, plan->ws.det_bits,
+                                          plan->ws.det_count, plan->ws.words_b, true, s, 1, 0, c, t);
+        };
+        e = launch();
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+          cudaGetLastError();  // a shape the device cannot schedule: skip it
+          continue;
+        }
+        if (ms < fft_best) {
+          fft_best = ms;
+          bc = c;
+          bt = t;
+        }
+      }
+    }
+    plan->fft_csize = bc;
+    plan->fft_threads = bt;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   if (st != RSFT_OK) return st;
   if (st2 != RSFT_OK) return st2;
   if (best < 0) return fail(RSFT_ERR_UNSUPPORTED, "no candidate fold schedule could run");

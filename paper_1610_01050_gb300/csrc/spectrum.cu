@@ -489,26 +489,32 @@ cudaError_t launch_noise_floor(const Geometry& g, const float2* spectrum, float 
   return cudaGetLastError();
 }
 
-int fft_cluster_size(const Geometry& g) {
+bool fft_cluster_valid(const Geometry& g, int c) {
   const int64_t B = g.total_b;
   const int64_t S = B / g.b[0];
-  if (B < 2 || B > (int64_t(1) << 20)) return 0;
-  int64_t c = B / 2048;  // about 2048 buckets per CTA
-  if (c < 1) c = 1;
-  while (c > 8 || c > g.b[0] || c > S) c >>= 1;
+  if (B < 2 || B > (int64_t(1) << 20) || c < 1 || c > 8 || (c & (c - 1))) return false;
   int64_t twiddles = 0;
   for (int d = 0; d < g.ndim; ++d) twiddles += g.b[d] / 2;
-  if (twiddles > 8192) return 0;
-  for (; c > 1; c >>= 1)
-    if (B / c <= 8192 && S / c >= 32) return static_cast<int>(c);  // two buffers of B / C; whole detection words
-  return B <= 16384 ? 1 : 0;                   // one CTA holds the loop in place (128 KiB)
+  if (twiddles > 8192 || c > g.b[0] || c > S) return false;
+  if (c == 1) return B <= 16384;                // one CTA holds the loop in place (128 KiB)
+  return B / c <= 8192 && S / c >= 32;          // two buffers of B / C; whole detection words per run
+}
+
+int fft_cluster_size(const Geometry& g) {
+  int64_t c = g.total_b / 2048;  // about 2048 buckets per CTA
+  if (c < 1) c = 1;
+  if (c > 8) c = 8;
+  for (; c >= 1; c >>= 1)
+    if (fft_cluster_valid(g, static_cast<int>(c))) return static_cast<int>(c);
+  return 0;
 }
 
 cudaError_t launch_fft_cluster(const Geometry& g, const DeviceTables& t, const float2* in, float2* out,
                                uint32_t* det_bits, uint32_t* det_count, int64_t words_b, bool detect,
-                               cudaStream_t stream, int nframes, int64_t frame_bits) {
-  const int csize = fft_cluster_size(g);
-  if (csize < 1) return cudaErrorInvalidConfiguration;
+                               cudaStream_t stream, int nframes, int64_t frame_bits, int csize_req, int threads_req) {
+  const int csize = csize_req > 0 ? csize_req : fft_cluster_size(g);
+  if (csize < 1 || !fft_cluster_valid(g, csize)) return cudaErrorInvalidConfiguration;
+  if (threads_req != 0 && threads_req != 256 && threads_req != 512) return cudaErrorInvalidValue;
   ClusterFftArgs args;
   args.g = g;
   args.t = t;
@@ -526,7 +532,7 @@ cudaError_t launch_fft_cluster(const Geometry& g, const DeviceTables& t, const f
   const int smem = static_cast<int>((E * (csize > 1 ? 2 : 1) + twiddles) * sizeof(float2));
   cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(fft_cluster_kernel), smem > 48 * 1024 ? smem : 48 * 1024);
   if (e != cudaSuccess) return e;
-  const int threads = E >= 2048 ? 512 : 256;
+  const int threads = threads_req > 0 ? threads_req : (E >= 2048 ? 512 : 256);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(g.loops * csize), static_cast<unsigned>(nframes));
   cfg.blockDim = dim3(threads);

@@ -171,3 +171,42 @@ def test_loops_per_pass_meet_oracle(lpp):
     g = gpu_run(d, cube_dev=x, plan=plan)
     rep = compare_full(g, O.rsft(op, cube.astype(np.complex128)), op)
     assert rep["located"] > 0
+
+
+FFT_SHAPES = [((1024, 256, 64), (64, 32, 8), 12), ((256, 512), (128, 128), 8), ((512, 256, 32), (32, 16, 2), 10)]
+
+
+@pytest.mark.parametrize("n,b,loops", FFT_SHAPES, ids=["radar", "2d_b16384", "3d_b1024"])
+def test_every_fft_cluster_shape_gives_the_same_spectrum(n, b, loops):
+    """The bucket FFT's cluster shape (CTAs per loop, threads per CTA) changes no arithmetic: every
+    valid shape gives the default shape's spectrum, detections and located list bit for bit; an
+    invalid shape is refused; the autotuner's choice is one of them."""
+    d = R.make_desc(n, b, loops, seed=33, p_fa1=0.01, mu=3, max_located=1 << 18)
+    tg = ri.draw_targets(n, 6, "offgrid", 33, (10.0, 20.0), int(np.prod(b)))
+    cube = ri.tone_cube(n, tg, 1.0, 33)
+    plan = R.rsft_plan_create(d)
+    ref = gpu_run(d, cube, plan=plan, want_votes=False)
+    tried = 0
+    for c in (1, 2, 4, 8):
+        for t in (256, 512):
+            try:
+                R.rsft_plan_set_fft_shape(plan, c, t)
+            except R.RsftError as e:
+                assert e.status == R.RSFT_ERR_UNSUPPORTED
+                continue
+            assert list(R.rsft_plan_get(plan, R.RSFT_GET_FFT_SHAPE)) == [c, t]
+            g = gpu_run(d, cube, plan=plan, want_votes=False)
+            np.testing.assert_array_equal(g["spectrum"], ref["spectrum"])
+            np.testing.assert_array_equal(g["detected"], ref["detected"])
+            np.testing.assert_array_equal(g["located"], ref["located"])
+            tried += 1
+    assert tried >= 2
+    with pytest.raises(R.RsftError):
+        R.rsft_plan_set_fft_shape(plan, 3, 256)
+    R.rsft_plan_set_fft_shape(plan, 0, 0)
+    x = torch.from_numpy(cube).cuda()
+    R.rsft_plan_autotune(plan, x, candidates=2, reps=3)
+    c, t = R.rsft_plan_get(plan, R.RSFT_GET_FFT_SHAPE)
+    assert c in (1, 2, 4, 8) and t in (256, 512)
+    g = gpu_run(d, cube, plan=plan, want_votes=False)
+    np.testing.assert_array_equal(g["located"], ref["located"])
