@@ -335,8 +335,10 @@ rsft_status build_fold_tables(rsft_plan* p, int group, rsft::DeviceTables& tabs)
     auto weight = [&](int l, int d, int64_t sd) {
       return h.wbar[d][(h.sigma_inv[l * D + d] * sd) & (h.n[d] - 1)] * h.w[d][sd];
     };
-    // layout [class group][row chunk][row][class in group][record]: a stage's rows are contiguous
+    // layout [class group][row chunk][stage][row slot][step][record]: a stage's records are
+    // contiguous, and a row slot's records of consecutive steps adjacent
     const int64_t R = fs.rows_per_chunk, C = fs.cps;
+    const int64_t spst = rsft::fold_stage_steps(fs), crow = fs.crow, rs = C * crow;
     const int64_t tunits = static_cast<int64_t>(fs.groups) * fs.row_chunks;
     const int full = std::min(group, L);
     const int64_t group_f4 = tunits * R * C * rsft::fold_record_f4(full);
@@ -358,7 +360,9 @@ rsft_status build_fold_tables(rsft_plan* p, int group, rsft::DeviceTables& tabs)
           cres /= h.b[d];
           sdig[d] = xd + h.b[d] * md;
         }
-        float* out = reinterpret_cast<float*>(&ft[tbase + static_cast<size_t>(e) * rec]);
+        const int64_t stage = r / (spst * crow), step = (r / crow) % spst, ro = (r % crow) * C + ci;
+        const int64_t at = tu * R * C + (stage * rs + ro) * spst + step;   // record index in the group
+        float* out = reinterpret_cast<float*>(&ft[tbase + static_cast<size_t>(at) * rec]);
         for (int l = 0; l < lg; ++l) {
           cplx wv(1.0, 0.0);
           for (int d = 0; d < fs.d_in; ++d) wv *= weight(l0 + l, d, sdig[d]);

@@ -59,6 +59,14 @@ __host__ __device__ __forceinline__ int fold_pair_of(int tid, unsigned lane_perm
   return q;
 }
 
+// Row steps (2 * kFoldConsumers elements each) per stage of the fold's shared-memory ring: every
+// whole stage of a unit is a run of this many steps (fewer when the unit's rows are fewer).
+constexpr int kFoldStepsPerStage = 8;
+__host__ __device__ __forceinline__ int fold_stage_steps(const FoldSchedule& fs) {
+  const int steps = fs.rows_per_chunk / fs.crow;
+  return steps < kFoldStepsPerStage ? steps : kFoldStepsPerStage;
+}
+
 // Fold row-table record of one (row, class) for a group of lg loops (float4 units): ceil(lg / 2)
 // float4 holding the pairs (d - c, c + d) of two loops each, then ceil(lg / 4) float4 holding c of
 // four loops each (w = c + jd the loop's row weight; entries past lg are zero).
@@ -100,7 +108,7 @@ struct DeviceTables {
   const float2* twiddle[kMaxDim];// [B_d / 2]: e^{-j 2 pi k / B_d}
   const float2* ginv[kMaxDim];   // [M_d]: 1 / G_d(-v) (dimension 0 also holds 1 / sum w)
   const unsigned short* slots_by_x; // [X][slots_per_x]: epilogue partial sums of each residue
-  const float4* ftable;          // fold row table [loop group][class group][row chunk][row][class][record]
+  const float4* ftable;          // fold row table [loop group][class group][row chunk][stage][row slot][step][record]
                                  // (fold_record_f4: (d-c, c+d) pairs, then c values)
   int64_t ftable_group_f4;       // float4 of the row table per full loop group
   int ftable_group;              // loops per group the row table was built for

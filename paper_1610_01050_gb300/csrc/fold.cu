@@ -51,7 +51,7 @@ constexpr int kThreads = kFoldConsumers;   // 256 threads, two columns each
 static_assert(kThreads == 256, "fold_pair_of places 8 thread bits");
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxRing = 8;                // shared-memory stages
-constexpr int kStepsPerStage = 8;          // row steps (2 * threads elements each) per stage
+constexpr int kStepsPerStage = kFoldStepsPerStage;  // row steps (2 * threads elements each) per stage
 constexpr int kStepElems = 2 * kThreads;
 constexpr int kStageBytes = kStepsPerStage * kStepElems * 8;
 constexpr int kSmemBudget = 110 * 1024;    // two CTAs per SM
@@ -70,7 +70,8 @@ struct FoldArgs {
   float2* folded;
   float2* partial;
   int* err;
-  const float4* table;    // this loop group's row table: [group][row chunk][row][class][record] (fold_record_f4)
+  const float4* table;    // this loop group's row table: [group][row chunk][stage][row slot][step][record]
+                          // (fold_record_f4 float4 a record; a row slot's records of one stage are adjacent)
   const float2* colw;     // this loop group's column weights: [col chunk][lg][W]
   int smem_colw;          // one column chunk: its weights staged in shared memory once
   int ring;               // stages in the ring
@@ -82,6 +83,20 @@ struct FoldArgs {
   unsigned short xdig[2048];                  // [X][4] inner residue digits
 };
 
+// Division by a launch constant: a shift and a mask when it is a power of two (all the fold's
+// counts are for power-of-two geometries), else the plain operators.
+struct Divisor {
+  int d, s;  // s = log2 d, or -1
+};
+__device__ __forceinline__ Divisor divisor(int d) {
+  Divisor v;
+  v.d = d;
+  v.s = (d & (d - 1)) == 0 ? __ffs(d) - 1 : -1;
+  return v;
+}
+__device__ __forceinline__ int quo(int x, Divisor v) { return v.s >= 0 ? x >> v.s : x / v.d; }
+__device__ __forceinline__ int rem(int x, Divisor v) { return v.s >= 0 ? x & (v.d - 1) : x % v.d; }
+
 // Stage geometry: a row step holds C classes x crow rows of W columns (rs = C crow rows);
 // spst steps form a stage, nst stages a unit.
 struct StageShape {
@@ -91,9 +106,8 @@ struct StageShape {
 __host__ __device__ __forceinline__ StageShape stage_shape(const FoldSchedule& fs, int lg) {
   StageShape s;
   s.rs = fs.cps * fs.crow;
-  const int steps = fs.rows_per_chunk / fs.crow;
-  s.spst = steps < kStepsPerStage ? steps : kStepsPerStage;
-  s.nst = steps / s.spst;
+  s.spst = fold_stage_steps(fs);
+  s.nst = fs.rows_per_chunk / fs.crow / s.spst;
   s.data_bytes = s.spst * s.rs * fs.width * 8;
   s.table_bytes = s.spst * s.rs * fold_record_f4(lg) * 16;
   return s;
@@ -140,7 +154,9 @@ __host__ __device__ __forceinline__ int fold_layout(const FoldSchedule& fs, int 
 // next unit's rows arrive during this unit's epilogue): the last warp to finish with stage i
 // (a shared-memory count per slot) issues stage i + ring into the same slot.  Each stage
 // brings its rows and their row-table slice.
-template <int LG, bool CHUNK>
+// FULL: every row step fills the 2 * threads elements and every stage has kStepsPerStage steps,
+// so the row-step strides are constants.
+template <int LG, bool CHUNK, bool FULL>
 __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant__ FoldArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int NP = (LG + 1) / 2;        // float4 of (d - c, c + d) pairs in a row record (two loops each)
@@ -183,25 +199,31 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
 
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_keep = policy_evict_last();
-  // Stage i of this CTA (one thread): unit blockIdx.x + (i / nst) grid, stage i % nst of it.
+  // Stage i of this CTA (one thread): unit blockIdx.x + (i / nst) grid, stage i % nst of it.  The
+  // issuing thread holds up its warp, and the ring's next refill waits for that warp: keep it short.
   auto issue = [&](int i) {
-    const int uf = static_cast<int>(blockIdx.x) + (i / nst) * static_cast<int>(gridDim.x);
-    const int f = uf / units_pf, u = uf - f * units_pf;  // frame, unit within the frame
+    // (formed here, not held in registers across the consumers' loop)
+    const Divisor dv_nst = divisor(nst), dv_upf = divisor(units_pf), dv_cc = divisor(fs.col_chunks),
+                  dv_rc = divisor(fs.row_chunks), dv_ch = divisor(chunks), dv_ring = divisor(ring);
+    const int uf = static_cast<int>(blockIdx.x) + quo(i, dv_nst) * static_cast<int>(gridDim.x);
+    const int f = quo(uf, dv_upf), u = uf - f * units_pf;  // frame, unit within the frame
     // the frame's tensor map and cube by constant indices (a dynamic index into the parameter
     // block would make the compiler copy it to local memory)
     const CUtensorMap* fmap = &a.tmap[0];
     const float2* fcube = a.cube[0];
+    if (a.nframes > 1) {
 #pragma unroll
-    for (int ff = 1; ff < kMaxFrames; ++ff)
-      if (ff == f) {
-        fmap = &a.tmap[ff];
-        fcube = a.cube[ff];
-      }
-    const int k = i % nst;
-    const int cc = u % fs.col_chunks;
-    const int rc = (u / fs.col_chunks) % fs.row_chunks;
-    const int cls0 = (u / chunks) * C;     // first class of the unit
-    const int slot = i % ring;
+      for (int ff = 1; ff < kMaxFrames; ++ff)
+        if (ff == f) {
+          fmap = &a.tmap[ff];
+          fcube = a.cube[ff];
+        }
+    }
+    const int k = rem(i, dv_nst);
+    const int cc = rem(u, dv_cc);
+    const int rc = rem(quo(u, dv_cc), dv_rc);
+    const int cls0 = quo(u, dv_ch) * C;     // first class of the unit
+    const int slot = rem(i, dv_ring);
     unsigned char* base = smem + slot * a.slot_bytes;
     float2* dst = reinterpret_cast<float2*>(base);
     mbar_arrive_expect_tx(full + slot, static_cast<uint32_t>(sh.data_bytes + sh.table_bytes));
@@ -302,17 +324,19 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
       if (ok && !mbar_try_wait(full + slot, parity) && !mbar_wait(full + slot, parity, abort_flag, a.err)) ok = false;
       if (ok && active) {
         const float4* src = reinterpret_cast<const float4*>(smem + slot * a.slot_bytes) + pq;
-        // this row slot's record in each row step: (d - c, c + d) pairs of two loops per float4, then
-        // c of four loops per float4
-        const float4* tr = reinterpret_cast<const float4*>(smem + slot * a.slot_bytes + kStageBytes) + ro * REC;
-#pragma unroll
+        // this row slot's records of the stage's steps, one after another: (d - c, c + d) pairs of
+        // two loops per float4, then c of four loops per float4
+        const float4* tr =
+            reinterpret_cast<const float4*>(smem + slot * a.slot_bytes + kStageBytes) + ro * (FULL ? kStepsPerStage : spst) * REC;
+        const int dstride = FULL ? kStepElems / 2 : RS * W / 2;  // float4 from one row step to the next
+#pragma unroll 2
         for (int step = 0; step < kStepsPerStage; ++step) {
-          if (step < spst) {
-            const float4 v = src[step * (RS * W / 2)];
+          if (FULL || step < spst) {
+            const float4 v = src[step * dstride];
             const float2 x0 = make_float2(v.x, v.y), x1 = make_float2(v.z, v.w);  // (a, b) of the columns
             const float s0 = v.x + v.y, s1 = v.z + v.w;                           // (a + b) of each column
             const float2 ss0 = make_float2(s0, s0), ss1 = make_float2(s1, s1);
-            const float4* rec = tr + step * RS * REC;
+            const float4* rec = tr + step * REC;
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
               const float4 w = rec[q];
@@ -477,16 +501,23 @@ __global__ void fold_reduce_kernel(const ReduceArgs a) {
   }
 }
 
-template <int LG, bool CHUNK>
-cudaError_t launch_fold_lg(const FoldArgs& args, int smem, cudaStream_t stream) {
+template <int LG, bool CHUNK, bool FULL>
+cudaError_t launch_fold_shape(const FoldArgs& args, int smem, cudaStream_t stream) {
   int resident = 0;
   const cudaError_t e =
-      device_resident_ctas(reinterpret_cast<const void*>(fold_kernel<LG, CHUNK>), kThreads, smem, &resident);
+      device_resident_ctas(reinterpret_cast<const void*>(fold_kernel<LG, CHUNK, FULL>), kThreads, smem, &resident);
   if (e != cudaSuccess) return e;
   const int units = args.fs.groups * args.fs.row_chunks * args.fs.col_chunks * args.nframes;
   const int grid = units < resident ? units : resident;
-  fold_kernel<LG, CHUNK><<<grid, kThreads, smem, stream>>>(args);
+  fold_kernel<LG, CHUNK, FULL><<<grid, kThreads, smem, stream>>>(args);
   return cudaGetLastError();
+}
+
+template <int LG, bool CHUNK>
+cudaError_t launch_fold_lg(const FoldArgs& args, int smem, cudaStream_t stream) {
+  const FoldSchedule& fs = args.fs;
+  const bool full = fs.cps * fs.crow * fs.width == kStepElems && fold_stage_steps(fs) == kStepsPerStage;
+  return full ? launch_fold_shape<LG, CHUNK, true>(args, smem, stream) : launch_fold_shape<LG, CHUNK, false>(args, smem, stream);
 }
 
 // One CTA waits, through the fold's bounded barrier wait, on a barrier that nothing
@@ -546,8 +577,7 @@ int encode_fold_map(const Geometry& g, const FoldSchedule& fs, const float2* cub
   if (fs.d_in < 1 || fs.d_in > 2 || fs.width > 256) return 0;
   EncodeTiledFn fn = encode_tiled();
   if (!fn) return 0;
-  const int steps = fs.rows_per_chunk / fs.crow;
-  const int nrows = (steps < kStepsPerStage ? steps : kStepsPerStage) * fs.crow;  // rows per class per stage
+  const int nrows = fold_stage_steps(fs) * fs.crow;  // rows per class per stage
   if (fs.cps > 256) return 0;
   cuuint64_t dims[5], strides[4];
   cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
