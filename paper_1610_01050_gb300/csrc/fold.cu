@@ -56,6 +56,30 @@ constexpr int kStepElems = 2 * kThreads;
 constexpr int kStageBytes = kStepsPerStage * kStepElems * 8;
 constexpr int kSmemBudget = 110 * 1024;    // two CTAs per SM
 
+// Division by a launch constant: a shift and a mask when it is a power of two (all the fold's
+// counts are for power-of-two geometries), else the plain operators.
+struct Divisor {
+  int d, s;  // s = log2 d, or -1
+};
+__host__ __device__ __forceinline__ Divisor divisor(int d) {
+  Divisor v;
+  v.d = d;
+  v.s = -1;
+  if (d > 0 && (d & (d - 1)) == 0) {
+    v.s = 0;
+    while ((1 << v.s) < d) ++v.s;
+  }
+  return v;
+}
+__device__ __forceinline__ int quo(int x, Divisor v) { return v.s >= 0 ? x >> v.s : x / v.d; }
+__device__ __forceinline__ int rem(int x, Divisor v) { return v.s >= 0 ? x & (v.d - 1) : x % v.d; }
+
+// The counts the stage issue divides by: stages per unit, units per frame, column chunks, row
+// chunks, chunks per class group, ring slots.
+struct IssueDivisors {
+  Divisor nst, upf, cc, rc, ch, ring;
+};
+
 struct FoldArgs {
   CUtensorMap tmap[kMaxFrames];  // per frame: rows of C classes as one box (tensor mode)
   int tensor_rank;        // 0: one 1-D bulk copy per row; 3 or 5: one tensor copy per stage
@@ -81,21 +105,8 @@ struct FoldArgs {
   int sinvb[kMaxLoopGroup * kMaxDim];        // sigma^{-1} mod B_d of the group's loops
   unsigned short slots[512];                  // [C X][slots_per_x] epilogue partial sums per (class, residue)
   unsigned short xdig[2048];                  // [X][4] inner residue digits
+  IssueDivisors dv;
 };
-
-// Division by a launch constant: a shift and a mask when it is a power of two (all the fold's
-// counts are for power-of-two geometries), else the plain operators.
-struct Divisor {
-  int d, s;  // s = log2 d, or -1
-};
-__device__ __forceinline__ Divisor divisor(int d) {
-  Divisor v;
-  v.d = d;
-  v.s = (d & (d - 1)) == 0 ? __ffs(d) - 1 : -1;
-  return v;
-}
-__device__ __forceinline__ int quo(int x, Divisor v) { return v.s >= 0 ? x >> v.s : x / v.d; }
-__device__ __forceinline__ int rem(int x, Divisor v) { return v.s >= 0 ? x & (v.d - 1) : x % v.d; }
 
 // Stage geometry: a row step holds C classes x crow rows of W columns (rs = C crow rows);
 // spst steps form a stage, nst stages a unit.
@@ -202,34 +213,22 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
   // Stage i of this CTA (one thread): unit blockIdx.x + (i / nst) grid, stage i % nst of it.  The
   // issuing thread holds up its warp, and the ring's next refill waits for that warp: keep it short.
   auto issue = [&](int i) {
-    // (formed here, not held in registers across the consumers' loop)
-    const Divisor dv_nst = divisor(nst), dv_upf = divisor(units_pf), dv_cc = divisor(fs.col_chunks),
-                  dv_rc = divisor(fs.row_chunks), dv_ch = divisor(chunks), dv_ring = divisor(ring);
-    const int uf = static_cast<int>(blockIdx.x) + quo(i, dv_nst) * static_cast<int>(gridDim.x);
-    const int f = quo(uf, dv_upf), u = uf - f * units_pf;  // frame, unit within the frame
-    // the frame's tensor map and cube by constant indices (a dynamic index into the parameter
-    // block would make the compiler copy it to local memory)
-    const CUtensorMap* fmap = &a.tmap[0];
-    const float2* fcube = a.cube[0];
-    if (a.nframes > 1) {
-#pragma unroll
-      for (int ff = 1; ff < kMaxFrames; ++ff)
-        if (ff == f) {
-          fmap = &a.tmap[ff];
-          fcube = a.cube[ff];
-        }
-    }
-    const int k = rem(i, dv_nst);
-    const int cc = rem(u, dv_cc);
-    const int rc = rem(quo(u, dv_cc), dv_rc);
-    const int cls0 = quo(u, dv_ch) * C;     // first class of the unit
-    const int slot = rem(i, dv_ring);
+    const IssueDivisors& dv = a.dv;
+    const int uf = static_cast<int>(blockIdx.x) + quo(i, dv.nst) * static_cast<int>(gridDim.x);
+    const int f = quo(uf, dv.upf), u = rem(uf, dv.upf);  // frame, unit within the frame
+    const CUtensorMap* fmap = &a.tmap[f];                 // (the parameter block's own copy)
+    const int k = rem(i, dv.nst);
+    const int cc = rem(u, dv.cc);
+    const int rc = rem(quo(u, dv.cc), dv.rc);
+    const int grp = quo(u, dv.ch);
+    const int cls0 = grp * C;     // first class of the unit
+    const int slot = rem(i, dv.ring);
     unsigned char* base = smem + slot * a.slot_bytes;
     float2* dst = reinterpret_cast<float2*>(base);
     mbar_arrive_expect_tx(full + slot, static_cast<uint32_t>(sh.data_bytes + sh.table_bytes));
     const int r0 = rc * R + k * spst * fs.crow;  // first row (within each class) of the stage
     bulk_g2s(base + kStageBytes,
-             a.table + ((static_cast<int64_t>(u / chunks) * fs.row_chunks + rc) * R + k * spst * fs.crow) * C * REC,
+             a.table + ((static_cast<int64_t>(grp) * fs.row_chunks + rc) * R + k * spst * fs.crow) * C * REC,
              static_cast<uint32_t>(sh.table_bytes), full + slot, pol_keep);
     if (a.tensor_rank == 3) {
       tensor_g2s_3d(dst, fmap, cc * W, cls0 & static_cast<int>(g.b[0] - 1), r0, full + slot, pol_stream);
@@ -255,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
             stride *= g.n[d];
           }
         }
-        bulk_g2s(dst + step * RS * W + ro * W, fcube + row * fs.row_len + static_cast<int64_t>(cc) * W,
+        bulk_g2s(dst + step * RS * W + ro * W, a.cube[f] + row * fs.row_len + static_cast<int64_t>(cc) * W,
                  static_cast<uint32_t>(W * 8), full + slot, pol_stream);
       }
     }
@@ -642,6 +641,15 @@ cudaError_t launch_fold_frames(const Geometry& g, const FoldSchedule& fs, const 
   for (int i = 0; i < fs.xcount * 4 && i < 2048; ++i) args.xdig[i] = t.h_xdig[i];
   const int smem = fold_layout(fs, lg, &args.ring, &args.slot_bytes, &args.colw_off, &args.red_off, &args.bar_off,
                                &args.lch);
+  {
+    const int chunks = fs.row_chunks * fs.col_chunks;
+    args.dv.nst = divisor(stage_shape(fs, lg).nst);
+    args.dv.upf = divisor(fs.groups * chunks);
+    args.dv.cc = divisor(fs.col_chunks);
+    args.dv.rc = divisor(fs.row_chunks);
+    args.dv.ch = divisor(chunks);
+    args.dv.ring = divisor(args.ring);
+  }
   // the epilogue partials of at most 6 loops always fit: multi-pass kernels only above that
   const bool chunk = args.lch < lg;
   switch (lg) {
