@@ -185,7 +185,7 @@ bool choose_vote_rows(const rsft::Geometry& g, rsft::VoteRowSchedule& vs) {
     }
     // the kernel keeps a [L][N_d] bucket-offset table (u16) of each row dimension in shared memory
     int64_t kb_words = 0;
-    for (int d = 0; best >= 0 && d < vs.d_v; ++d) kb_words += static_cast<int64_t>(g.loops) * g.n[d];
+    for (int d = 0; best >= 0 && d < vs.d_v; ++d) kb_words += static_cast<int64_t>((g.loops + 7) & ~7) * g.n[d];
     if (best >= 0 && vs.n_in >= 16 && kb_words <= 49152 && g.total_b <= 65536 &&
         rsft::vote_rows_small_smem(g, vs, (g.total_b + 31) / 32) <= 200 * 1024) {
       vs.small = 1;
@@ -592,12 +592,15 @@ rsft_status build_device(rsft_plan* p) {
     if ((st = upload(p, &mp, masks)) != RSFT_OK) return st;
     p->tables.rowmask = mp;
     // bucket-plane offsets of the row dimensions: ((sigma i mod N_d) >> log M_d) << b_shift_d (< B <= 65536)
+    // per dimension [N_d][Lp]: the offsets of all loops of one index together, padded to eight
+    const int Lp = (L + 7) & ~7;
     std::vector<uint16_t> kb;
     for (int d = 0; d < vs.d_v; ++d)
-      for (int l = 0; l < L; ++l)
-        for (int64_t i = 0; i < h.n[d]; ++i)
-          kb.push_back(static_cast<uint16_t>((((h.sigma[l * D + d] * i) & (h.n[d] - 1)) >> p->geom.log_m[d])
-                                             << p->geom.b_shift[d]));
+      for (int64_t i = 0; i < h.n[d]; ++i)
+        for (int l = 0; l < Lp; ++l)
+          kb.push_back(l < L ? static_cast<uint16_t>((((h.sigma[l * D + d] * i) & (h.n[d] - 1)) >> p->geom.log_m[d])
+                                                     << p->geom.b_shift[d])
+                             : static_cast<uint16_t>(0));
     while (kb.empty() || kb.size() % 8 != 0) kb.push_back(0u);  // whole 16-byte units for the bulk copy
     uint16_t* kp = nullptr;
     if ((st = upload(p, &kp, kb)) != RSFT_OK) return st;

@@ -119,7 +119,7 @@ struct DeviceTables {
   const unsigned short* x_digits;   // [X][4]: inner residue digit per inner dimension
   const uint64_t* rowmask;          // rows <= 64: per loop, the candidate mask of every detection pattern of a
                                     // plane ([L][2^b_in], b_in <= 8) or of each inner bucket ([L][b_in])
-  const uint16_t* kb16;             // per row dimension d < d_v: [L][N_d] bucket offset (Def. 3) of index i_d
+  const uint16_t* kb16;             // per row dimension d < d_v: [N_d][L rounded up to 8] bucket offset (Def. 3) of index i_d
   const unsigned char* h_xres;      // host: residue index of each column of a 64-column chunk
 };
 

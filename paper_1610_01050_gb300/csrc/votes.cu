@@ -648,10 +648,14 @@ __host__ __device__ __forceinline__ uint32_t round16(uint64_t v) { return static
 // of every detection pattern of a plane ([L][2^B_in]); otherwise one mask per bucket.
 __host__ __device__ __forceinline__ bool pattern_table(int b_in) { return b_in <= 8; }
 
+// Bucket-offset tables of the row dimensions: per index i_d the offsets of all loops, padded
+// to whole 16-byte groups of eight ([N_d][kb_loops_padded(L)] u16 per dimension).
+__host__ __device__ __forceinline__ int kb_loops_padded(int loops) { return (loops + 7) & ~7; }
+
 __host__ __device__ inline SmallRowLayout small_row_layout(const Geometry& g, int d_v, int b_in, int64_t words_b) {
   SmallRowLayout s{};
   int64_t kb_words = 0;
-  for (int d = 0; d < d_v; ++d) kb_words += static_cast<int64_t>(g.loops) * g.n[d];
+  for (int d = 0; d < d_v; ++d) kb_words += static_cast<int64_t>(kb_loops_padded(g.loops)) * g.n[d];
   s.kb_bytes = round16(static_cast<uint64_t>(kb_words) * 2);
   s.cand_bytes = round16(static_cast<uint64_t>(g.loops) * (pattern_table(b_in) ? (1 << b_in) : b_in) * 8);
   s.bit_bytes = round16(static_cast<uint64_t>(g.loops) * words_b * 4);
@@ -664,7 +668,7 @@ __host__ __device__ inline SmallRowLayout small_row_layout(const Geometry& g, in
 
 // The tables a row count reads (shared memory, or global memory in the emit kernel).
 struct RowTables {
-  const uint16_t* kb;      // per row dimension d < d_v: [L][N_d] bucket offset of index i_d
+  const uint16_t* kb;      // per row dimension d < d_v: [N_d][kb_loops_padded(L)] bucket offset of index i_d
   const uint64_t* cand;    // [L][2^B_in] pattern unions, or [L][B_in] per-bucket masks
   const uint32_t* bits;    // [L][words_b] detection bitmaps
 };
@@ -690,12 +694,13 @@ __device__ __forceinline__ void count_row(const RowArgs& a, const RowTables& t, 
       idx[d] = static_cast<int>(static_cast<uint32_t>(r) & static_cast<uint32_t>(g.n[d] - 1));
       r >>= g.log_n[d];
     }
+    const int Lp = kb_loops_padded(L);
     int off = 0;
 #pragma unroll
     for (int d = 0; d < DV; ++d) {
-      kp[d] = t.kb + off + idx[d];
-      kn[d] = static_cast<int>(g.n[d]);
-      off += L * kn[d];
+      kp[d] = t.kb + off + idx[d] * Lp;
+      kn[d] = 1;
+      off += Lp * static_cast<int>(g.n[d]);
     }
   }
 #pragma unroll
@@ -731,11 +736,116 @@ __device__ __forceinline__ void count_row(const RowArgs& a, const RowTables& t, 
   }
 }
 
-// Locations of the row with votes > mu, bit-sliced.
+// Loads from the shared-memory window by 32-bit address.  They read tables that no thread
+// writes after the kernel's copy barrier; every address they take derives from a base formed
+// after that barrier (shared_base), so the compiler cannot move them above it.
+__device__ __forceinline__ uint32_t lds_u16(uint32_t addr) {
+  unsigned short v;
+  asm("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
+  uint32_t v;
+  asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ uint64_t lds_u64(uint32_t addr) {
+  uint64_t v;
+  asm("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ uint32_t shared_base(const void* p) {
+  uint32_t v;
+  asm volatile("mov.u32 %0, %1;" : "=r"(v) : "r"(smem_u32(p)));
+  return v;
+}
+
+// count_row on tables staged in shared memory (window addresses of the bucket-offset tables,
+// the candidate table and the detection bitmaps): the same counts.  The offsets of eight loops
+// come with one 16-byte load per row dimension and are summed two at a time in 32-bit words
+// (an offset sum stays below B <= 65536, so the halves never carry into each other); each loop
+// then costs one bitmap load and a few integer operations unless its plane holds a detection.
+template <int DV, int NP>
+__device__ __forceinline__ void count_row_smem(const RowArgs& a, uint32_t s_kb, uint32_t s_cand, uint32_t s_bits,
+                                               int64_t row, uint64_t* c) {
+  const Geometry& g = a.g;
+  const int L = g.loops;
+  const uint32_t Lp = static_cast<uint32_t>(kb_loops_padded(L));
+  const bool wide = a.b_in > 32;
+  const uint32_t pat_mask = a.b_in < 32 ? ((1u << a.b_in) - 1u) : 0xffffffffu;
+  const bool table = pattern_table(a.b_in);
+  uint32_t ka[DV > 0 ? DV : 1];
+  {
+    uint64_t r = static_cast<uint64_t>(row);
+    uint32_t idx[DV > 0 ? DV : 1];
+#pragma unroll
+    for (int d = DV - 1; d >= 0; --d) {
+      idx[d] = static_cast<uint32_t>(r) & static_cast<uint32_t>(g.n[d] - 1);
+      r >>= g.log_n[d];
+    }
+    uint32_t off = 0;
+#pragma unroll
+    for (int d = 0; d < DV; ++d) {
+      ka[d] = s_kb + 2u * (off + idx[d] * Lp);
+      off += static_cast<uint32_t>(g.n[d]) * Lp;
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < 8; ++p) c[p] = 0ull;
+  const uint32_t wstep = 32u * static_cast<uint32_t>(a.words_b);  // bits of one loop's bitmap
+  const uint32_t cstep = 8u * static_cast<uint32_t>(table ? (1 << a.b_in) : a.b_in);
+  uint32_t boff = 0u;                                              // first bit of loop l's bitmap
+  for (int l0 = 0; l0 < L; l0 += 8) {
+    uint32_t kw[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int d = 0; d < DV; ++d) {
+      uint32_t t0, t1, t2, t3;
+      asm("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(t0), "=r"(t1), "=r"(t2), "=r"(t3) : "r"(ka[d] + 2u * l0));
+      kw[0] += t0;
+      kw[1] += t1;
+      kw[2] += t2;
+      kw[3] += t3;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (l0 + j < L) {
+        const uint32_t kb = ((kw[j >> 1] >> (16 * (j & 1))) & 0xffffu) + boff;
+        const uint32_t wa = s_bits + ((kb >> 5) << 2);
+        const uint32_t plo = (lds_u32(wa) >> (kb & 31u)) & pat_mask;
+        const uint32_t phi = wide ? lds_u32(wa + 4u) : 0u;
+        if (plo | phi) {
+          const uint32_t sc = s_cand + static_cast<uint32_t>(l0 + j) * cstep;
+          uint64_t m;
+          if (table) {
+            m = lds_u64(sc + (plo << 3));
+          } else {
+            m = 0ull;
+            uint64_t pat = static_cast<uint64_t>(plo) | (static_cast<uint64_t>(phi) << 32);
+            while (pat) {
+              m |= lds_u64(sc + (static_cast<uint32_t>(__ffsll(static_cast<long long>(pat)) - 1) << 3));
+              pat &= pat - 1;
+            }
+          }
+#pragma unroll
+          for (int p = 0; p < NP; ++p) {
+            const uint64_t tt = c[p] & m;
+            c[p] ^= m;
+            m = tt;
+          }
+        }
+      }
+      boff += wstep;
+    }
+  }
+}
+
+// Locations of the row with votes > mu, bit-sliced (NP counter planes; votes < 2^NP).
+template <int NP>
 __device__ __forceinline__ uint64_t above_mu(const RowArgs& a, const uint64_t* c) {
+  if (a.mu >> NP) return 0ull;  // more votes than NP planes can hold
   uint64_t eq = ~0ull, gt = 0ull;
 #pragma unroll
-  for (int p = 7; p >= 0; --p) {
+  for (int p = NP - 1; p >= 0; --p) {
     if ((a.mu >> p) & 1) {
       eq &= c[p];
     } else {
@@ -806,10 +916,8 @@ __global__ void __launch_bounds__(kSmallWarps * 32) vote_rows_small_kernel(const
   if (!mbar_wait_bounded(bar, 0u, a.err)) return;  // no block-wide barriers below
   const int64_t gw = static_cast<int64_t>(blockIdx.x) * kSmallWarps + wid;
   if (gw >= a.warps) return;
-  RowTables t;
-  t.kb = reinterpret_cast<const uint16_t*>(smem_small + lay.kb_off);
-  t.cand = reinterpret_cast<const uint64_t*>(smem_small + lay.cand_off);
-  t.bits = reinterpret_cast<const uint32_t*>(smem_small + lay.bit_off);
+  const uint32_t sbase = shared_base(smem_small);   // (after the copy barrier)
+  const uint32_t s_kb = sbase + lay.kb_off, s_cand = sbase + lay.cand_off, s_bits = sbase + lay.bit_off;
   const int64_t row0 = gw * a.rows_per_warp;
   ulonglong2* list = fp.row_list + row0;
   uint64_t pos = PASS == 1 ? a.warp_offset[gw] : 0ull;
@@ -820,8 +928,8 @@ __global__ void __launch_bounds__(kSmallWarps * 32) vote_rows_small_kernel(const
     uint64_t c[8];
     uint64_t gt = 0ull;
     if (valid) {
-      count_row<DV, NP>(a, t, row, c);
-      gt = above_mu(a, c);
+      count_row_smem<DV, NP>(a, s_kb, s_cand, s_bits, row, c);
+      gt = above_mu<NP>(a, c);
     }
     if (PASS == 0) {
       hits += static_cast<uint32_t>(__popcll(gt));
