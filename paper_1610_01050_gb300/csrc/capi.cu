@@ -708,14 +708,30 @@ void release(rsft_plan* p) {
 
 // One fold launch of loops [l0, l0 + lg): the tensor-core fold where the plan has one, else
 // the SIMT fold (and its partial-sum reduction when the schedule chunks rows or columns).
+// One fold launch of loops [l0, l0 + lg).  `clear`: the SIMT fold also zeroes the detection
+// bitmaps and counts (the first launch of an execute); the tensor-core fold leaves that to a memset.
 cudaError_t fold_group(rsft_plan* p, const rsft::DeviceTables& ft, bool tensor_cores, const void* cube, int l0,
-                       int lg, rsft::Workspace& ws, cudaStream_t stream) {
+                       int lg, rsft::Workspace& ws, cudaStream_t stream, bool clear = false) {
   const rsft::Geometry& g = p->geom;
-  if (tensor_cores)
+  if (tensor_cores) {
+    cudaError_t e = cudaSuccess;
+    if (clear) {
+      e = cudaMemsetAsync(ws.det_bits, 0, static_cast<size_t>(g.loops) * ws.words_b * 4, stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(ws.det_count, 0, static_cast<size_t>(g.loops) * 4, stream);
+      if (e != cudaSuccess) return e;
+    }
     return rsft::launch_fold_tc(g, p->fold, ft, static_cast<const float2*>(cube), l0, lg, ws.folded, ws.err_flag,
                                 &p->fold_copy_mode, stream);
+  }
+  rsft::FoldClear fc;
+  if (clear) {
+    fc.a = ws.det_bits;
+    fc.na = static_cast<int64_t>(g.loops) * ws.words_b;
+    fc.b = ws.det_count;
+    fc.nb = g.loops;
+  }
   cudaError_t e = rsft::launch_fold(g, p->fold, ft, static_cast<const float2*>(cube), l0, lg, ws.folded, ws.partial,
-                                    ws.err_flag, &p->fold_copy_mode, stream);
+                                    ws.err_flag, &p->fold_copy_mode, stream, fc);
   if (e == cudaSuccess && !p->fold.direct) e = rsft::launch_fold_reduce(g, p->fold, ft, l0, lg, ws.partial, ws.folded, stream);
   return e;
 }
@@ -743,9 +759,6 @@ rsft_status run_lane(rsft_plan* p, rsft::Workspace& ws, bool& votes_dirty, bool 
     e = cudaMemsetAsync(ws.votes, 0, static_cast<size_t>(ws.vote_words) * 4, stream);
     if (e != cudaSuccess) return cuda_fail(e, "clear votes");
   }
-  e = cudaMemsetAsync(ws.det_bits, 0, static_cast<size_t>(g.loops) * ws.words_b * 4, stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ws.det_count, 0, static_cast<size_t>(g.loops) * 4, stream);
-  if (e != cudaSuccess) return cuda_fail(e, "clear detections");
   mark(0);
   // segment mode: loop l folds its own segment (one loop per launch); otherwise every loop
   // group folds the same cube in one pass
@@ -754,7 +767,7 @@ rsft_status run_lane(rsft_plan* p, rsft::Workspace& ws, bool& votes_dirty, bool 
   for (int l0 = 0; l0 < g.loops; l0 += group) {
     const int lg = std::min(group, g.loops - l0);
     const void* cube = d_segments ? d_segments[l0] : d_cube;
-    e = fold_group(p, ft, p->fold_tc && !d_segments, cube, l0, lg, ws, stream);
+    e = fold_group(p, ft, p->fold_tc && !d_segments, cube, l0, lg, ws, stream, l0 == 0);
     if (e != cudaSuccess) return cuda_fail(e, "permute_window_fold");
   }
   mark(1);
@@ -1012,9 +1025,11 @@ rsft_status run_frames(rsft_plan* p, const void* const* d_cubes, int64_t n, cuda
   cudaError_t e = cudaSuccess;
   for (int64_t f0 = 0; f0 < n; f0 += rsft::kMaxFrames) {
     const int nf = static_cast<int>(std::min<int64_t>(rsft::kMaxFrames, n - f0));
-    e = cudaMemsetAsync(fw.det_bits, 0, static_cast<size_t>(nf) * fw.frame_bits * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(fw.det_count, 0, static_cast<size_t>(nf) * L * 4, s);
-    if (e != cudaSuccess) return cuda_fail(e, "clear detections");
+    rsft::FoldClear fc;  // the fold zeroes the group's detection bitmaps and counts
+    fc.a = fw.det_bits;
+    fc.na = static_cast<int64_t>(nf) * fw.frame_bits;
+    fc.b = fw.det_count;
+    fc.nb = static_cast<int64_t>(nf) * L;
     const float2* cubes[rsft::kMaxFrames];
     for (int f = 0; f < nf; ++f) cubes[f] = static_cast<const float2*>(d_cubes[f0 + f]);
     rsft_plan::FramesTiming ft{nullptr, nullptr, nf};
@@ -1024,7 +1039,7 @@ rsft_status run_frames(rsft_plan* p, const void* const* d_cubes, int64_t n, cuda
       if (ft.start) cudaEventRecord(ft.start, s);
     }
     e = rsft::launch_fold_frames(g, p->fold, p->tables, cubes, nf, static_cast<int64_t>(L) * g.total_b, 0, L,
-                                 fw.folded, nullptr, p->ws.err_flag, &p->fold_copy_mode, s);
+                                 fw.folded, nullptr, p->ws.err_flag, &p->fold_copy_mode, s, fc);
     if (e != cudaSuccess) return cuda_fail(e, "permute_window_fold (frames)");
     if (ft.start && ft.end) {
       cudaEventRecord(ft.end, s);

@@ -183,14 +183,23 @@ cudaError_t launch_refine_step(const RefineGeom& rg, const DeviceTables& t, cons
 // Exclusive scan of n u32 counts into offsets[0..n] (offsets[n] = total), total also to *total.
 cudaError_t launch_count_scan(const uint32_t* counts, int64_t n, uint64_t* offsets, int64_t* total,
                               cudaStream_t stream);
+// Two word ranges the fold zeroes on its way (the detection bitmaps and counts that the bucket
+// FFT then fills), so an execute needs no separate clearing launches.
+struct FoldClear {
+  uint32_t* a = nullptr;
+  int64_t na = 0;
+  uint32_t* b = nullptr;
+  int64_t nb = 0;
+};
 cudaError_t launch_fold(const Geometry& g, const FoldSchedule& fs, const DeviceTables& t,
                         const float2* cube, int loop0, int lg, float2* folded, float2* partial, int* err,
-                        int* copy_mode, cudaStream_t stream);
+                        int* copy_mode, cudaStream_t stream, const FoldClear& clear = FoldClear{});
 // The fold of `nframes` cubes of one plan in one persistent launch (direct schedules): frame f's
 // buckets go to folded + f * folded_stride.
 cudaError_t launch_fold_frames(const Geometry& g, const FoldSchedule& fs, const DeviceTables& t,
                                const float2* const* cubes, int nframes, int64_t folded_stride, int loop0, int lg,
-                               float2* folded, float2* partial, int* err, int* copy_mode, cudaStream_t stream);
+                               float2* folded, float2* partial, int* err, int* copy_mode, cudaStream_t stream,
+                               const FoldClear& clear = FoldClear{});
 cudaError_t launch_fold_reduce(const Geometry& g, const FoldSchedule& fs, const DeviceTables& t,
                                int loop0, int lg, const float2* partial, float2* folded,
                                cudaStream_t stream);

@@ -106,6 +106,7 @@ struct FoldArgs {
   unsigned short slots[512];                  // [C X][slots_per_x] epilogue partial sums per (class, residue)
   unsigned short xdig[2048];                  // [X][4] inner residue digits
   IssueDivisors dv;
+  FoldClear clear;        // words zeroed by the grid before its work (detection bitmaps and counts)
 };
 
 // Stage geometry: a row step holds C classes x crow rows of W columns (rs = C crow rows);
@@ -197,6 +198,12 @@ __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant
   int* released = reinterpret_cast<int*>(cbar + 1);  // [ring] warps done with the slot's stage
   volatile int* abort_flag = released + kMaxRing;
 
+  {
+    // the next stage's detection bitmaps and counts start from zero
+    const int64_t nthreads = static_cast<int64_t>(gridDim.x) * kThreads;
+    for (int64_t w = static_cast<int64_t>(blockIdx.x) * kThreads + tid; w < a.clear.na; w += nthreads) a.clear.a[w] = 0u;
+    for (int64_t w = static_cast<int64_t>(blockIdx.x) * kThreads + tid; w < a.clear.nb; w += nthreads) a.clear.b[w] = 0u;
+  }
   if (tid == 0) {
     for (int i = 0; i < ring; ++i) {
       mbar_init(full + i, 1);
@@ -617,7 +624,8 @@ int encode_fold_map(const Geometry& g, const FoldSchedule& fs, const float2* cub
 
 cudaError_t launch_fold_frames(const Geometry& g, const FoldSchedule& fs, const DeviceTables& t,
                                const float2* const* cubes, int nframes, int64_t folded_stride, int loop0, int lg,
-                               float2* folded, float2* partial, int* err, int* copy_mode, cudaStream_t stream) {
+                               float2* folded, float2* partial, int* err, int* copy_mode, cudaStream_t stream,
+                               const FoldClear& clear) {
   if (nframes < 1 || nframes > kMaxFrames || (nframes > 1 && !fs.direct)) return cudaErrorInvalidValue;
   thread_local FoldArgs args;  // large (parameter tables); filled, then copied by the launch
   args.tensor_rank = encode_fold_map(g, fs, cubes[0], &args.tmap[0]);
@@ -627,6 +635,7 @@ cudaError_t launch_fold_frames(const Geometry& g, const FoldSchedule& fs, const 
   for (int f = 0; f < kMaxFrames; ++f) args.cube[f] = cubes[f < nframes ? f : 0];
   args.nframes = nframes;
   args.folded_stride = folded_stride;
+  args.clear = clear;
   args.g = g;
   args.fs = fs;
   args.loop0 = loop0;
@@ -683,8 +692,8 @@ cudaError_t launch_fold_frames(const Geometry& g, const FoldSchedule& fs, const 
 
 cudaError_t launch_fold(const Geometry& g, const FoldSchedule& fs, const DeviceTables& t,
                         const float2* cube, int loop0, int lg, float2* folded, float2* partial, int* err,
-                        int* copy_mode, cudaStream_t stream) {
-  return launch_fold_frames(g, fs, t, &cube, 1, 0, loop0, lg, folded, partial, err, copy_mode, stream);
+                        int* copy_mode, cudaStream_t stream, const FoldClear& clear) {
+  return launch_fold_frames(g, fs, t, &cube, 1, 0, loop0, lg, folded, partial, err, copy_mode, stream, clear);
 }
 
 cudaError_t launch_fold_reduce(const Geometry& g, const FoldSchedule& fs, const DeviceTables& t,
