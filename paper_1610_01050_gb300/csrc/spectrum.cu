@@ -196,13 +196,64 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
 }
 
 // All decimation-in-time stages of dimension d (size n = 2^ln, element stride 2^lst) of an
-// E-element shared-memory buffer whose input along d is in bit-reversed order, two radix-2
-// stages per pass between barriers where two remain (a radix-2^2 butterfly on four elements
-// spaced h apart: stage h pairs (a0, a1) and (a2, a3) with W_2h^p, stage 2h pairs (b0, b2) with
-// W_4h^p and (b1, b3) with W_4h^(p + h) = -j W_4h^p), else one.  tw[k] = e^{-j 2 pi k / n}.
+// E-element shared-memory buffer whose input along d is in bit-reversed order, several radix-2
+// stages per pass between barriers: three while three or more remain (except four, taken as
+// two and two), then two, then one.  A radix-2^3 butterfly on eight elements spaced h apart:
+// stage h pairs (a0, a1), (a2, a3), ... with W_2h^p; stage 2h pairs (b0, b2), (b4, b6) with
+// W_4h^p and (b1, b3), (b5, b7) with W_4h^(p + h) = -j W_4h^p; stage 4h pairs (c_k, c_k+4) with
+// W_8h^(p + k h) = W_8h^p W_8^k.  A radix-2^2 butterfly is its first two stages on four
+// elements.  tw[k] = e^{-j 2 pi k / n}.
 __device__ __forceinline__ void dit_dimension(float2* buf, uint32_t E, int ln, int lst, const float2* __restrict__ tw) {
   const uint32_t smask = (1u << lst) - 1u;
+  const float r2 = 0.70710678118654752f;  // 1 / sqrt 2
   int lh = 0;
+  for (; lh + 2 < ln && ln - lh != 4; lh += 3) {
+    const uint32_t eighth = E >> 3;
+    for (uint32_t qi = threadIdx.x; qi < eighth; qi += blockDim.x) {
+      const uint32_t low = qi & smask;
+      const uint32_t t = qi >> lst;
+      const uint32_t b = t & ((1u << (ln - 3)) - 1u);
+      const uint32_t line = t >> (ln - 3);
+      const uint32_t pos = b & ((1u << lh) - 1u);
+      const uint32_t grp = b >> lh;
+      const uint32_t i0 = (((line << ln) + (grp << (lh + 3)) + pos) << lst) + low;
+      const uint32_t hs = 1u << (lh + lst);
+      const float2 w1 = tw[pos << (ln - 1 - lh)];  // W_2h^pos
+      const float2 w2 = tw[pos << (ln - 2 - lh)];  // W_4h^pos
+      const float2 w3 = tw[pos << (ln - 3 - lh)];  // W_8h^pos
+      float2 v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = buf[i0 + k * hs];
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) {  // stage h
+        const float2 y = cmulf(w1, v[k + 1]);
+        v[k + 1] = make_float2(v[k].x - y.x, v[k].y - y.y);
+        v[k] = make_float2(v[k].x + y.x, v[k].y + y.y);
+      }
+#pragma unroll
+      for (int k = 0; k < 8; k += 4) {  // stage 2h
+        const float2 y0 = cmulf(w2, v[k + 2]);
+        const float2 u1 = cmulf(w2, v[k + 3]);
+        const float2 y1 = make_float2(u1.y, -u1.x);  // -j W_4h^pos
+        v[k + 2] = make_float2(v[k].x - y0.x, v[k].y - y0.y);
+        v[k] = make_float2(v[k].x + y0.x, v[k].y + y0.y);
+        v[k + 3] = make_float2(v[k + 1].x - y1.x, v[k + 1].y - y1.y);
+        v[k + 1] = make_float2(v[k + 1].x + y1.x, v[k + 1].y + y1.y);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {  // stage 4h: W_8h^pos W_8^k
+        const float2 u = cmulf(w3, v[k + 4]);
+        float2 y;
+        if (k == 0) y = u;
+        else if (k == 1) y = make_float2((u.x + u.y) * r2, (u.y - u.x) * r2);
+        else if (k == 2) y = make_float2(u.y, -u.x);
+        else y = make_float2((u.y - u.x) * r2, -(u.x + u.y) * r2);
+        buf[i0 + k * hs] = make_float2(v[k].x + y.x, v[k].y + y.y);
+        buf[i0 + (k + 4) * hs] = make_float2(v[k].x - y.x, v[k].y - y.y);
+      }
+    }
+    __syncthreads();
+  }
   for (; lh + 1 < ln; lh += 2) {
     const uint32_t quarter = E >> 2;
     for (uint32_t qi = threadIdx.x; qi < quarter; qi += blockDim.x) {
