@@ -674,11 +674,15 @@ void drain_timing(rsft_plan* p) {
   p->frames_pending.clear();
 }
 
+// Kernels one execute with a located list and amplitudes launches (no full vote array): the
+// fold (and its reduce for chunked schedules) per loop group, the FFT, the noise floor in
+// estimate mode, the votes and second stage (small rows: count and emit; wide rows: count, scan
+// and write; scatter mode: scatter, count, scan and write), the median.
 int launches_per_execute(const rsft_plan* p) {
   const int groups = (p->geom.loops + p->loop_group - 1) / p->loop_group;
   return groups * (p->fold.direct ? 1 : 2) + (p->fft_cluster ? 1 : static_cast<int>(p->passes.size())) +
          (p->host.estimate_noise ? 1 : 0) +
-         (p->rows_mode ? 3 : 4) + 1;
+         (p->rows_mode ? (p->rows.small ? 2 : 3) : 4) + 1;
 }
 
 void release(rsft_plan* p) {
