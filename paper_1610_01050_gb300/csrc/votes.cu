@@ -462,6 +462,7 @@ __device__ __forceinline__ FramePtrs frame_ptrs(const RowArgs& a) {
 }
 
 constexpr int kRowWarps = 8;
+static_assert(kRowWarps % 4 == 0, "the emit kernel reads the warp counts four at a time");
 
 // First bucket index of the B_in-bucket plane that row `row` maps to in loop l.
 __device__ __forceinline__ int64_t plane_of(const RowArgs& a, int l, int64_t row) {
@@ -739,11 +740,6 @@ __device__ __forceinline__ void count_row(const RowArgs& a, const RowTables& t, 
 // Loads from the shared-memory window by 32-bit address.  They read tables that no thread
 // writes after the kernel's copy barrier; every address they take derives from a base formed
 // after that barrier (shared_base), so the compiler cannot move them above it.
-__device__ __forceinline__ uint32_t lds_u16(uint32_t addr) {
-  unsigned short v;
-  asm("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
-  return v;
-}
 __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
   uint32_t v;
   asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
@@ -974,8 +970,18 @@ __global__ void __launch_bounds__(kRowWarps * 32) emit_rows_kernel(const RowArgs
   const unsigned int n = live ? fp.warp_rows[gw] : 0u;
   if (lane == 0) wcnt[wid] = live ? fp.warp_count[gw] : 0u;
   unsigned long long s = 0ull;
+  if ((reinterpret_cast<uintptr_t>(fp.warp_count) & 15u) == 0) {
+    // four counts a load (first is a multiple of kRowWarps = 8, the counts 16-byte aligned)
+    const uint4* wc4 = reinterpret_cast<const uint4*>(fp.warp_count);
+#pragma unroll 4
+    for (int64_t w = threadIdx.x; w < (first >> 2); w += kRowWarps * 32) {
+      const uint4 v = wc4[w];
+      s += static_cast<unsigned long long>(v.x) + v.y + v.z + v.w;
+    }
+  } else {
 #pragma unroll 8
-  for (int64_t w = threadIdx.x; w < first; w += kRowWarps * 32) s += fp.warp_count[w];
+    for (int64_t w = threadIdx.x; w < first; w += kRowWarps * 32) s += fp.warp_count[w];
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) red[wid] = s;
