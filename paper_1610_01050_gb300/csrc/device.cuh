@@ -6,6 +6,31 @@
 
 namespace rsft {
 
+// Programmatic dependent launch along an execute's chain of kernels (fold, FFT, vote count,
+// emit, median): a kernel launched with launch_chained may be scheduled while the kernel before
+// it on the stream is still finishing.  Every chained kernel calls chain_wait() before it reads
+// or writes anything (it returns once the previous grid has completed and its memory is
+// visible), then chain_release() so that its own successor can start launching; launched
+// without the attribute, both are no-ops.
+__device__ __forceinline__ void chain_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void chain_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                           Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
 constexpr int kMaxDim = 4;
 constexpr int kMaxLoopGroup = 16;    // loops folded per pass over the cube
 constexpr int kFoldConsumers = 256;  // fold consumer threads per CTA (two columns each)

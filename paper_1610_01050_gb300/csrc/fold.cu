@@ -171,6 +171,8 @@ __host__ __device__ __forceinline__ int fold_layout(const FoldSchedule& fs, int 
 template <int LG, bool CHUNK, bool FULL>
 __global__ void __launch_bounds__(kThreads, 2) fold_kernel(const __grid_constant__ FoldArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
+  chain_wait();
+  chain_release();
   constexpr int NP = (LG + 1) / 2;        // float4 of (d - c, c + d) pairs in a row record (two loops each)
   constexpr int NC = (LG + 3) / 4;        // float4 of c values (four loops each)
   constexpr int REC = NP + NC;
@@ -515,8 +517,7 @@ cudaError_t launch_fold_shape(const FoldArgs& args, int smem, cudaStream_t strea
   if (e != cudaSuccess) return e;
   const int units = args.fs.groups * args.fs.row_chunks * args.fs.col_chunks * args.nframes;
   const int grid = units < resident ? units : resident;
-  fold_kernel<LG, CHUNK, FULL><<<grid, kThreads, smem, stream>>>(args);
-  return cudaGetLastError();
+  return launch_chained(fold_kernel<LG, CHUNK, FULL>, dim3(grid), dim3(kThreads), static_cast<size_t>(smem), stream, args);
 }
 
 // The constant-stride form up to 12 loops per group: there it is 4-8% faster (radar cube, the

@@ -343,6 +343,8 @@ __device__ __forceinline__ void store_block(const ClusterFftArgs& a, int l, cons
 __global__ void __launch_bounds__(512) fft_cluster_kernel(const ClusterFftArgs a) {
   extern __shared__ __align__(16) float2 sbuf[];
   __shared__ uint32_t hits;
+  chain_wait();
+  chain_release();
   const Geometry& g = a.g;
   const int C = a.csize;
   const int l = static_cast<int>(blockIdx.x) / C;
@@ -589,13 +591,15 @@ cudaError_t launch_fft_cluster(const Geometry& g, const DeviceTables& t, const f
   cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = static_cast<size_t>(smem);
   cfg.stream = stream;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = static_cast<unsigned>(csize);
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // chained (chain_wait first)
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, fft_cluster_kernel, args);
 }
 

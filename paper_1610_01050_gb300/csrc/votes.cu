@@ -279,6 +279,8 @@ constexpr int kMedianWarps = 4;
 
 // One warp per located index; per-loop values in shared memory, median by rank.
 __global__ void __launch_bounds__(kMedianWarps * 32) median_kernel(const MedianArgs a) {
+  chain_wait();
+  chain_release();
   const MedianFrame mf = median_frame(a);
   __shared__ float vre[kMedianWarps][256];
   __shared__ float vim[kMedianWarps][256];
@@ -339,6 +341,8 @@ __global__ void __launch_bounds__(kMedianWarps * 32) median_kernel(const MedianA
 // values stay in registers and the ranks come from shuffles within the group.
 template <int G>
 __global__ void __launch_bounds__(kMedianWarps * 32) median_group_kernel(const MedianArgs a) {
+  chain_wait();
+  chain_release();
   const MedianFrame mf = median_frame(a);
   const Geometry& g = a.g;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -893,6 +897,8 @@ constexpr int kSmallWarps = 16;
 template <int PASS, int DV, int NP>
 __global__ void __launch_bounds__(kSmallWarps * 32) vote_rows_small_kernel(const RowArgs a) {
   extern __shared__ __align__(16) unsigned char smem_small[];
+  chain_wait();
+  chain_release();
   const FramePtrs fp = frame_ptrs(a);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const SmallRowLayout lay = small_row_layout(a.g, a.d_v, a.b_in, a.words_b);
@@ -955,6 +961,8 @@ __global__ void __launch_bounds__(kSmallWarps * 32) vote_rows_small_kernel(const
 // the global tables.
 template <int DV, int NP>
 __global__ void __launch_bounds__(kRowWarps * 32) emit_rows_kernel(const RowArgs a, RowTables gt_tables) {
+  chain_wait();
+  chain_release();
   const FramePtrs fp = frame_ptrs(a);
   gt_tables.bits = fp.det_bits;
   __shared__ unsigned long long red[kRowWarps];
@@ -1086,20 +1094,17 @@ template <int DV, int NP>
 cudaError_t small_rows_run(const RowArgs& a, const RowTables& gtab, size_t smem, bool full, cudaStream_t stream,
                            int nframes) {
   const dim3 blocks(static_cast<unsigned>((a.warps + kSmallWarps - 1) / kSmallWarps), static_cast<unsigned>(nframes));
-  vote_rows_small_kernel<0, DV, NP><<<blocks, kSmallWarps * 32, smem, stream>>>(a);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_chained(vote_rows_small_kernel<0, DV, NP>, blocks, dim3(kSmallWarps * 32), smem, stream, a);
   if (e != cudaSuccess) return e;
   if (full) {
     // the full vote array: scan the warp counts, recount and write every row
     stage2_scan_kernel<<<1, 1024, 0, stream>>>(a.warp_count, a.warps, const_cast<uint64_t*>(a.warp_offset), a.d_count);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    vote_rows_small_kernel<1, DV, NP><<<blocks, kSmallWarps * 32, smem, stream>>>(a);
-    return cudaGetLastError();
+    return launch_chained(vote_rows_small_kernel<1, DV, NP>, blocks, dim3(kSmallWarps * 32), smem, stream, a);
   }
   const dim3 eblocks(static_cast<unsigned>((a.warps + kRowWarps - 1) / kRowWarps), static_cast<unsigned>(nframes));
-  emit_rows_kernel<DV, NP><<<eblocks, kRowWarps * 32, 0, stream>>>(a, gtab);
-  return cudaGetLastError();
+  return launch_chained(emit_rows_kernel<DV, NP>, eblocks, dim3(kRowWarps * 32), 0, stream, a, gtab);
 }
 
 size_t vote_rows_small_smem(const Geometry& g, const VoteRowSchedule& vs, int64_t words_b) {
@@ -1231,14 +1236,14 @@ cudaError_t launch_median(const Geometry& g, const DeviceTables& t, const float2
     if (gb > 152 * 8) gb = 152 * 8;
     if (gb < 1) gb = 1;
     const dim3 gu(static_cast<unsigned>(gb), static_cast<unsigned>(nframes));
-    if (per_warp == 8) median_group_kernel<4><<<gu, kMedianWarps * 32, 0, stream>>>(args);
-    else if (per_warp == 4) median_group_kernel<8><<<gu, kMedianWarps * 32, 0, stream>>>(args);
-    else if (per_warp == 2) median_group_kernel<16><<<gu, kMedianWarps * 32, 0, stream>>>(args);
-    else median_group_kernel<32><<<gu, kMedianWarps * 32, 0, stream>>>(args);
-    return cudaGetLastError();
+    const dim3 blk(kMedianWarps * 32);
+    if (per_warp == 8) return launch_chained(median_group_kernel<4>, gu, blk, 0, stream, args);
+    if (per_warp == 4) return launch_chained(median_group_kernel<8>, gu, blk, 0, stream, args);
+    if (per_warp == 2) return launch_chained(median_group_kernel<16>, gu, blk, 0, stream, args);
+    return launch_chained(median_group_kernel<32>, gu, blk, 0, stream, args);
   }
-  median_kernel<<<dim3(static_cast<unsigned>(blocks), static_cast<unsigned>(nframes)), kMedianWarps * 32, 0, stream>>>(args);
-  return cudaGetLastError();
+  return launch_chained(median_kernel, dim3(static_cast<unsigned>(blocks), static_cast<unsigned>(nframes)),
+                        dim3(kMedianWarps * 32), 0, stream, args);
 }
 
 }  // namespace rsft
