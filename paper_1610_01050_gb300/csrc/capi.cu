@@ -1020,6 +1020,7 @@ rsft_status ensure_frames(rsft_plan* p) {
 // writes d_located + f * max_located, d_amp + f * max_located and d_counts[f].
 rsft_status run_frames(rsft_plan* p, const void* const* d_cubes, int64_t n, cudaStream_t s, uint64_t* d_located,
                        float2* d_amp, int64_t* d_counts, bool timed) {
+  const rsft::ChainLaunches unchained(false);  // frame groups of two plans share the GPU
   const rsft::Geometry& g = p->geom;
   const int L = g.loops;
   const int64_t cap = p->host.desc.max_located;

@@ -599,7 +599,7 @@ cudaError_t launch_fft_cluster(const Geometry& g, const DeviceTables& t, const f
   attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // chained (chain_wait first)
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 2;
+  cfg.numAttrs = t_chain_launches ? 2 : 1;
   return cudaLaunchKernelEx(&cfg, fft_cluster_kernel, args);
 }
 
