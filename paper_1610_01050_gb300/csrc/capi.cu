@@ -681,7 +681,7 @@ void drain_timing(rsft_plan* p) {
 int launches_per_execute(const rsft_plan* p) {
   const int groups = (p->geom.loops + p->loop_group - 1) / p->loop_group;
   return groups * (p->fold.direct ? 1 : 2) + (p->fft_cluster ? 1 : static_cast<int>(p->passes.size())) +
-         (p->host.estimate_noise ? 1 : 0) +
+         (p->host.estimate_noise && !p->fft_cluster ? 1 : 0) +
          (p->rows_mode ? (p->rows.small ? 2 : 3) : 4) + 1;
 }
 
@@ -777,8 +777,10 @@ rsft_status run_lane(rsft_plan* p, rsft::Workspace& ws, bool& votes_dirty, bool 
   mark(1);
   const bool estimate = p->host.estimate_noise;
   if (p->fft_cluster) {
+    // (estimate mode: each loop's noise floor is selected inside the cluster that holds its buckets)
     e = rsft::launch_fft_cluster(g, p->tables, ws.folded, ws.spectrum, ws.det_bits, ws.det_count, ws.words_b,
-                                 !estimate, stream, 1, 0, p->fft_csize, p->fft_threads);
+                                 !estimate, stream, 1, 0, p->fft_csize, p->fft_threads,
+                                 estimate ? ws.gamma_used : nullptr, static_cast<float>(p->host.floor_factor));
     if (e != cudaSuccess) return cuda_fail(e, "bucket_fft/np_detect (cluster)");
   } else {
     for (size_t i = 0; i < p->passes.size(); ++i) {
@@ -787,7 +789,7 @@ rsft_status run_lane(rsft_plan* p, rsft::Workspace& ws, bool& votes_dirty, bool 
       if (e != cudaSuccess) return cuda_fail(e, "bucket_fft/np_detect");
     }
   }
-  if (estimate) {
+  if (estimate && !p->fft_cluster) {
     // noise floor of each loop from its own bucket powers, then the detection against it
     e = rsft::launch_noise_floor(g, ws.spectrum, static_cast<float>(p->host.floor_factor), ws.gamma_used,
                                  ws.det_bits, ws.det_count, ws.words_b, stream);
@@ -1054,9 +1056,10 @@ rsft_status run_frames(rsft_plan* p, const void* const* d_cubes, int64_t n, cuda
     // fixes a shape: 16-frame groups of the radar cube 44.0 -> 43.1 us a frame, the batched shapes
     // equal or faster; the arithmetic does not depend on the shape
     e = rsft::launch_fft_cluster(g, p->tables, fw.folded, fw.spectrum, fw.det_bits, fw.det_count, words_b, !estimate,
-                                 s, nf, fw.frame_bits, p->fft_csize, p->fft_threads ? p->fft_threads : 256);
+                                 s, nf, fw.frame_bits, p->fft_csize, p->fft_threads ? p->fft_threads : 256,
+                                 estimate ? fw.gamma_used : nullptr, static_cast<float>(p->host.floor_factor));
     if (e != cudaSuccess) return cuda_fail(e, "bucket_fft/np_detect (frames)");
-    if (estimate) {
+    if (estimate && !p->fft_cluster) {
       e = rsft::launch_noise_floor(g, fw.spectrum, static_cast<float>(p->host.floor_factor), fw.gamma_used,
                                    fw.det_bits, fw.det_count, words_b, s, nf, fw.frame_bits);
       if (e != cudaSuccess) return cuda_fail(e, "np_detect noise floor (frames)");

@@ -250,10 +250,12 @@ bool fft_cluster_valid(const Geometry& g, int csize);
 // With nframes > 1 the arrays hold frames one after another ([frame][L][B] buckets, [frame][L] counts,
 // frame_bits detection words per frame).  csize / threads 0 take the default shape (about 2048
 // buckets per CTA; 512 threads from 2048 buckets per CTA, else 256).
+// gamma_out non-null: estimate mode fused in (each loop's threshold from its own lower-median bucket
+// power times floor_factor, written to gamma_out[frame][l], then its detections); detect must be false.
 cudaError_t launch_fft_cluster(const Geometry& g, const DeviceTables& t, const float2* in, float2* out,
                                uint32_t* det_bits, uint32_t* det_count, int64_t words_b, bool detect,
                                cudaStream_t stream, int nframes = 1, int64_t frame_bits = 0, int csize = 0,
-                               int threads = 0);
+                               int threads = 0, float* gamma_out = nullptr, float floor_factor = 0.f);
 // Estimate mode of the first stage: per loop, gamma_l = lowermedian(|f-hat_l|^2) * factor (written to
 // gamma_out[l]) and the loop's detection bitmap and count against it.
 cudaError_t launch_noise_floor(const Geometry& g, const float2* spectrum, float factor, float* gamma_out,

@@ -174,6 +174,8 @@ struct ClusterFftArgs {
   int csize;             // C: CTAs per loop (a cluster)
   int detect;
   int64_t frame_bits;    // frames (blockIdx.y): detection words between consecutive frames
+  float* gamma_out;      // non-null: estimate mode, gamma_l from the loop's own bucket powers ([frames][L])
+  float floor_factor;    // -ln Pfa1-bar / ln 2 (estimate mode)
 };
 
 // Reverse the bits of each dimension's digit of a row-major index over dimensions [d0, D).
@@ -307,7 +309,9 @@ __device__ __forceinline__ void dit_dimension(float2* buf, uint32_t E, int ln, i
 // ((e >> lq) << lS) + col0 + (e & (2^lq - 1)) of loop l.  Rows of at least 32 elements keep a
 // warp's 32 consecutive elements on one aligned detection word.
 __device__ __forceinline__ void store_block(const ClusterFftArgs& a, int l, const float2* src, uint32_t E, int lq,
-                                            int lS, uint32_t col0, float gamma, uint32_t* hits) {
+                                            int lS, uint32_t col0, float gamma, uint32_t* hits, bool store = true,
+                                            bool detect_now = false) {
+  const bool detect = detect_now || a.detect;
   const int64_t f = blockIdx.y;
   float2* dst = a.out + (f * a.g.loops + l) * a.g.total_b;
   uint32_t* bits = a.det_bits + f * a.frame_bits + static_cast<int64_t>(l) * a.words_b;
@@ -319,10 +323,10 @@ __device__ __forceinline__ void store_block(const ClusterFftArgs& a, int l, cons
     bool hit = false;
     if (e < E) {
       const float2 v = src[e];
-      dst[k] = v;
-      hit = a.detect && bucket_power(v) > gamma;
+      if (store) dst[k] = v;
+      hit = detect && bucket_power(v) > gamma;
     }
-    if (!a.detect) continue;
+    if (!detect) continue;
     const unsigned ballot = __ballot_sync(0xffffffffu, hit);
     if (lane == 0 && ballot) {
       const uint32_t kw = k;                 // bucket of lane 0
@@ -338,6 +342,85 @@ __device__ __forceinline__ void store_block(const ClusterFftArgs& a, int l, cons
       atomicAdd(hits, static_cast<uint32_t>(__popc(ballot)));
     }
   }
+}
+
+// Lower median (rank floor((B - 1) / 2)) of the power bit patterns of a loop's B buckets, held
+// E apiece in the shared memory of the C CTAs of a cluster: four passes over 8-bit digits, most
+// significant first (non-negative floats order as their bit patterns); each CTA histograms its
+// own elements whose high digits match the prefix, then every CTA sums the C histograms through
+// distributed shared memory (hist holds 512 words: the CTA's own bins, then the cluster's
+// totals) and takes the same digit.  Returns the selected pattern.
+__device__ __forceinline__ uint32_t cluster_lower_median(const float2* buf, uint32_t E, uint32_t B, int C,
+                                                         uint32_t* hist, uint32_t* pick) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t prefix = 0u, rank = (B - 1u) / 2u;
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 24 - 8 * pass;
+    const uint32_t hi_mask = pass == 0 ? 0u : (0xFFFFFFFFu << (shift + 8));
+    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    for (uint32_t e0 = 0; e0 < E; e0 += blockDim.x) {
+      const uint32_t e = e0 + threadIdx.x;
+      bool take = false;
+      uint32_t digit = 0u;
+      if (e < E) {
+        const uint32_t key = __float_as_uint(bucket_power(buf[e]));
+        take = (key & hi_mask) == prefix;
+        digit = (key >> shift) & 255u;
+      }
+      const unsigned active = __ballot_sync(0xffffffffu, take);
+      if (take) {
+        const unsigned peers = __match_any_sync(active, digit);
+        if (lane == __ffs(peers) - 1) atomicAdd(&hist[digit], static_cast<uint32_t>(__popc(peers)));
+      }
+    }
+    if (C > 1) {
+      cluster.sync();  // every CTA's histogram is complete
+      // thread b sums bin b over the cluster (C independent remote loads), into this CTA's totals
+      for (uint32_t b = threadIdx.x; b < 256; b += blockDim.x) {
+        uint32_t t = 0u;
+        for (int r = 0; r < C; ++r) t += cluster.map_shared_rank(hist, r)[b];
+        hist[256 + b] = t;
+      }
+      cluster.sync();  // the histograms are read before anyone moves on (the next pass clears them)
+    } else {
+      __syncthreads();
+    }
+    const uint32_t* tot = C > 1 ? hist + 256 : hist;
+    if (warp == 0) {
+      // lane q holds bins [8q, 8q + 8): find the bin where the running count passes rank
+      uint32_t c[8], sum = 0u;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        c[j] = tot[lane * 8 + j];
+        sum += c[j];
+      }
+      uint32_t incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const uint32_t excl = incl - sum;
+      if (excl <= rank && rank < incl) {
+        uint32_t run = excl;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (run <= rank && rank < run + c[j]) {
+            pick[0] = static_cast<uint32_t>(lane * 8 + j);
+            pick[1] = run;
+          }
+          run += c[j];
+        }
+      }
+    }
+    __syncthreads();  // pick[] is written
+    prefix |= pick[0] << shift;
+    rank -= pick[1];
+    __syncthreads();  // pick[] is rewritten by the next pass
+  }
+  return prefix;
 }
 
 __global__ void __launch_bounds__(512) fft_cluster_kernel(const ClusterFftArgs a) {
@@ -378,9 +461,17 @@ __global__ void __launch_bounds__(512) fft_cluster_kernel(const ClusterFftArgs a
     if (g.log_b[d] > 0)
       dit_dimension(sbuf, E, g.log_b[d], g.b_shift[d], tws[d]);
   const float gamma = a.detect ? a.t.gamma[l] : 0.f;
+  __shared__ uint32_t sel_hist[512];
+  __shared__ uint32_t sel_pick[2];
   if (C == 1) {
     const int lB = 31 - __clz(B);                // the loop as one row: bucket k = e
     store_block(a, l, sbuf, B, lB, lB, 0u, gamma, &hits);
+    if (a.gamma_out) {
+      // estimate mode: the noise floor from this loop's own bucket powers, then its detections
+      const float gl = __uint_as_float(cluster_lower_median(sbuf, B, B, 1, sel_hist, sel_pick)) * a.floor_factor;
+      if (threadIdx.x == 0) a.gamma_out[static_cast<int64_t>(blockIdx.y) * g.loops + l] = gl;
+      store_block(a, l, sbuf, B, lB, lB, 0u, gl, &hits, false, true);
+    }
   } else {
     // phase 2: columns [c Q, (c + 1) Q) of every row of dimension 0, from the cluster's shared memory
     cg::cluster_group cluster = cg::this_cluster();
@@ -400,8 +491,14 @@ __global__ void __launch_bounds__(512) fft_cluster_kernel(const ClusterFftArgs a
     cluster.sync();                              // no CTA leaves while others still read its rows
     if (lb0 > 0) dit_dimension(gbuf, E, lb0, lq, tws[0]);
     store_block(a, l, gbuf, E, lq, lS, c * Q, gamma, &hits);
+    if (a.gamma_out) {
+      // estimate mode: the noise floor from the cluster's bucket powers, then this CTA's detections
+      const float gl = __uint_as_float(cluster_lower_median(gbuf, E, B, C, sel_hist, sel_pick)) * a.floor_factor;
+      if (c == 0 && threadIdx.x == 0) a.gamma_out[static_cast<int64_t>(blockIdx.y) * g.loops + l] = gl;
+      store_block(a, l, gbuf, E, lq, lS, c * Q, gl, &hits, false, true);
+    }
   }
-  if (a.detect) {
+  if (a.detect || a.gamma_out) {
     __syncthreads();
     if (threadIdx.x == 0 && hits) atomicAdd(a.det_count + static_cast<int64_t>(blockIdx.y) * g.loops + l, hits);
   }
@@ -564,7 +661,8 @@ int fft_cluster_size(const Geometry& g) {
 
 cudaError_t launch_fft_cluster(const Geometry& g, const DeviceTables& t, const float2* in, float2* out,
                                uint32_t* det_bits, uint32_t* det_count, int64_t words_b, bool detect,
-                               cudaStream_t stream, int nframes, int64_t frame_bits, int csize_req, int threads_req) {
+                               cudaStream_t stream, int nframes, int64_t frame_bits, int csize_req, int threads_req,
+                               float* gamma_out, float floor_factor) {
   const int csize = csize_req > 0 ? csize_req : fft_cluster_size(g);
   if (csize < 1 || !fft_cluster_valid(g, csize)) return cudaErrorInvalidConfiguration;
   if (threads_req != 0 && threads_req != 256 && threads_req != 512) return cudaErrorInvalidValue;
@@ -579,6 +677,8 @@ cudaError_t launch_fft_cluster(const Geometry& g, const DeviceTables& t, const f
   args.csize = csize;
   args.detect = detect ? 1 : 0;
   args.frame_bits = frame_bits;
+  args.gamma_out = gamma_out;
+  args.floor_factor = floor_factor;
   const int64_t E = g.total_b / csize;
   int64_t twiddles = 0;
   for (int d = 0; d < g.ndim; ++d) twiddles += g.b[d] / 2;
