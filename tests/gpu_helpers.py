@@ -112,6 +112,17 @@ def check_noise_floor(g, ref, op):
         assert abs(m_gpu - m_ref) <= np.max(np.abs(pg - pr)) + 4e-7 * m_ref, (l, m_gpu, m_ref)
     rel = np.abs(gg / gr - 1)
     assert np.all(rel <= GAMMA_TOL), rel
+    # exactly: each threshold is the rank-floor((B - 1) / 2) power of the GPU's own FP32 spectrum
+    # (power = fma(re, re, re(im * im)): re^2 is exact in FP64, the FP32 product im * im is rounded,
+    # one final rounding to FP32) times the plan's factor, multiplied in FP32
+    pfa1 = float(R.rsft_plan_get(g["plan"], R.RSFT_GET_PFA1)[0])
+    f32 = np.float32(-np.log(pfa1) / np.log(2.0))
+    for l in range(op.loops):
+        sp = np.asarray(g["spectrum"][l]).reshape(-1)
+        x, y = sp.real.astype(np.float32), sp.imag.astype(np.float32)
+        pw = (x.astype(np.float64) * x.astype(np.float64) + (y * y).astype(np.float64)).astype(np.float32)
+        m = np.sort(pw)[(pw.size - 1) // 2]
+        assert np.float32(gg[l]) == np.float32(m) * f32, (l, gg[l], m, f32)
     return BAND + rel
 
 
