@@ -167,7 +167,11 @@ rsft_status rsft_execute(rsft_plan* plan, const void* d_cube, void* stream,
 /*
  * As rsft_execute, but does not wait: the located count (int64, possibly
  * above max_located) is written to device memory *d_n_located in stream
- * order, and capacity overflow is not reported as an error.
+ * order, and capacity overflow is not reported as an error.  The execute's
+ * kernels are launched as a programmatic-dependent chain: each may be
+ * scheduled while the kernel before it on `stream` is finishing, but reads and
+ * writes nothing until that kernel has completed, so stream order with respect
+ * to the caller's kernels, copies and events is unchanged.
  */
 rsft_status rsft_execute_async(rsft_plan* plan, const void* d_cube, void* stream,
                                uint64_t* d_located, uint8_t* d_located_votes,

@@ -665,6 +665,7 @@ cudaError_t launch_fft_cluster(const Geometry& g, const DeviceTables& t, const f
                                float* gamma_out, float floor_factor) {
   const int csize = csize_req > 0 ? csize_req : fft_cluster_size(g);
   if (csize < 1 || !fft_cluster_valid(g, csize)) return cudaErrorInvalidConfiguration;
+  if (gamma_out && detect) return cudaErrorInvalidValue;  // one detection per launch: known or estimated
   if (threads_req != 0 && threads_req != 256 && threads_req != 512) return cudaErrorInvalidValue;
   ClusterFftArgs args;
   args.g = g;
