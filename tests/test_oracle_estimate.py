@@ -147,7 +147,7 @@ def test_binomial_design_solves_its_laws():
     assert O.binomial_vote_tail(12, pd, mu) == pytest.approx(0.9, rel=1e-9)
     hit = min(1.0, pd)
     assert O.binomial_vote_tail(12, d["rho"] * hit + (1 - d["rho"]) * q, mu) == pytest.approx(1e-6, rel=1e-6)
-    # the paper's Normal design of the same system, judged by the binomial law, misses P_fa by orders
+    # the paper's Normal design of the same system, evaluated with the binomial law, misses P_fa by orders
     nd = O.optimal_thresholds(12, 16384, 32, 2.34 ** 3, 0.9, 1e-6)
     true_pfa = O.binomial_vote_tail(12, d["rho"] * min(1.0, nd["pd_bar"]) + (1 - d["rho"]) * nd["pfa1"], nd["mu"])
     assert true_pfa > 100 * 1e-6
