@@ -426,8 +426,6 @@ __device__ __forceinline__ uint32_t cluster_lower_median(const float2* buf, uint
 __global__ void __launch_bounds__(512) fft_cluster_kernel(const ClusterFftArgs a) {
   extern __shared__ __align__(16) float2 sbuf[];
   __shared__ uint32_t hits;
-  chain_wait();
-  chain_release();
   const Geometry& g = a.g;
   const int C = a.csize;
   const int l = static_cast<int>(blockIdx.x) / C;
@@ -454,6 +452,9 @@ __global__ void __launch_bounds__(512) fft_cluster_kernel(const ClusterFftArgs a
       }
     }
   }
+  // (the twiddles are the plan's: staged while the previous kernel of the chain finishes)
+  chain_wait();
+  chain_release();
   // phase 1: rows [c E / S, (c + 1) E / S) of the loop, bit-reversed along dimensions d_first..D-1
   for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) sbuf[digit_reverse(e, g, d_first)] = src[e];
   __syncthreads();

@@ -897,8 +897,6 @@ constexpr int kSmallWarps = 16;
 template <int PASS, int DV, int NP>
 __global__ void __launch_bounds__(kSmallWarps * 32) vote_rows_small_kernel(const RowArgs a) {
   extern __shared__ __align__(16) unsigned char smem_small[];
-  chain_wait();
-  chain_release();
   const FramePtrs fp = frame_ptrs(a);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const SmallRowLayout lay = small_row_layout(a.g, a.d_v, a.b_in, a.words_b);
@@ -909,12 +907,16 @@ __global__ void __launch_bounds__(kSmallWarps * 32) vote_rows_small_kernel(const
   }
   __syncthreads();
   if (threadIdx.x == 0) {
+    // the plan's offset and candidate tables (written at plan creation) load while the previous
+    // kernel of the chain finishes; the detection bitmaps only after it has
     const uint64_t pol = policy_evict_last();
     mbar_arrive_expect_tx(bar, lay.kb_bytes + lay.cand_bytes + lay.bit_bytes);
     if (lay.kb_bytes) bulk_g2s(smem_small + lay.kb_off, a.t.kb16, lay.kb_bytes, bar, pol);  // none when d_v == 0
     bulk_g2s(smem_small + lay.cand_off, a.t.rowmask, lay.cand_bytes, bar, pol);
-    bulk_g2s(smem_small + lay.bit_off, fp.det_bits, lay.bit_bytes, bar, pol);
   }
+  chain_wait();
+  chain_release();
+  if (threadIdx.x == 0) bulk_g2s(smem_small + lay.bit_off, fp.det_bits, lay.bit_bytes, bar, policy_evict_last());
   if (!mbar_wait_bounded(bar, 0u, a.err)) return;  // no block-wide barriers below
   const int64_t gw = static_cast<int64_t>(blockIdx.x) * kSmallWarps + wid;
   if (gw >= a.warps) return;
